@@ -1,0 +1,227 @@
+/*
+ * zc.h -- C ABI of the GB300 error-bounded float codec and its collective
+ * steps (gZCCL, arXiv 2308.05199).
+ *
+ * The library implements the GPU-side hot path of compression-accelerated
+ * collectives: an error-bounded lossy compressor for FP32/BF16 buffers
+ * (Sec. 3.3.2 adapts such a compressor for collectives), its decompressor, the
+ * fused decompress -> sum -> recompress step each ring reduce-scatter round
+ * runs on the received chunk (Sec. 3.2.3, 3.3.1 "GPU reduction kernel",
+ * 3.3.3), and the per-destination pack of the compressed Scatter
+ * (Sec. 3.3.4).  Every call is asynchronous on the given CUDA stream, takes
+ * caller-owned device buffers, and never allocates: the paper's adapter
+ * replaces per-call temporary allocations and unified-memory offset buffers
+ * with one preallocated, reused device buffer (Sec. 3.3.2), here the
+ * "workspace".
+ *
+ * Method (the paper does not print the compressor's internals; these are
+ * this library's definitions, shared with its CPU oracle):
+ *   q_i = the integer nearest to x_i / (2 eb), ties to even (exact);
+ *   blocks of L = 16, 32, 64 or 128 elements, each delta-coded by a 1-D
+ *   Lorenzo predictor (d_i = q_i - q_{i-1}, the block head predicted from 0);
+ *   each block stored at a fixed bit width w = bit length of max |d|: a sign
+ *   plane, then magnitude planes 0 .. w-1, L bits each;
+ *   block payloads placed back to back at offsets given by a prefix sum of
+ *   their sizes (computed on the device in one pass, decoupled look-back).
+ * Reconstruction is x^ = fl32(q * 2eb): |x - q 2eb| <= eb exactly, and the
+ * FP32 value adds at most half an FP32 ulp of x^ (BF16 output: half a BF16
+ * ulp).
+ *
+ * Stream layout (little-endian, every stream a multiple of 16 bytes):
+ *   [0,4) "ZCv1"  [4] dtype  [5] log2 L  [6] flags (bit 0: raw)  [7] 0
+ *   [8,16) n  [16,20) eb (f32)  [20,24) nb = ceil(n / L)  [24,32) payload bytes
+ *   [32, 32 + pad16(nb))          one width byte per block, zero padded
+ *   [32 + pad16(nb), ... )        block payloads, zero padded to 16 bytes
+ * A raw stream (flag bit 0) holds the n elements verbatim after the header.
+ *
+ * Error channels.
+ *   - Argument errors are returned at once: a NULL pointer, a bad dtype or
+ *     block size, a non-positive or non-finite bound, a workspace or output
+ *     capacity that is too small for the header, a misaligned buffer.
+ *     Nothing is launched then.
+ *   - Data errors are only known on the device.  The first one is recorded in
+ *     the workspace's status word (first error wins) and read back with
+ *     zc_get_device_status().  Output content is unspecified after a data
+ *     error, but no kernel ever writes outside [d_out, d_out + out_cap).
+ *
+ * Workspace.  One workspace per stream in flight (two calls that run at the
+ * same time must not share one: Sec. 3.3.4 gives every stream its own
+ * temporary buffers for the same reason).  Size it with zc_workspace_bytes(),
+ * zero it once with zc_workspace_init(); after that no call needs it cleared
+ * again: the look-back flags carry a launch generation number.
+ *
+ * Alignment.  Stream buffers (d_out, d_cmp*) must be 16-byte aligned; FP32
+ * arrays 4-byte, BF16 arrays 2-byte aligned.
+ */
+#ifndef ZC_H
+#define ZC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t without the CUDA headers; 0 is the legacy default stream. */
+typedef struct CUstream_st* zc_stream_t;
+
+typedef enum {
+    ZC_OK = 0,
+    ZC_ERR_ARG = 1,       /* bad argument (returned at once)                  */
+    ZC_ERR_RANGE = 2,     /* |x / 2eb| rounds beyond 2^22                      */
+    ZC_ERR_NONFINITE = 3, /* NaN or Inf in the input                           */
+    ZC_ERR_CAPACITY = 4,  /* output buffer too small                           */
+    ZC_ERR_FORMAT = 5,    /* malformed or mismatched input stream              */
+    ZC_ERR_TIMEOUT = 6,   /* a device-side wait gave up (see zc_set_wait_limit)*/
+    ZC_ERR_CUDA = 7,      /* a CUDA runtime call failed                        */
+    ZC_ERR_WORKSPACE = 8  /* workspace too small or not initialised            */
+} zc_status;
+
+typedef enum { ZC_F32 = 0, ZC_BF16 = 1 } zc_dtype;
+typedef enum { ZC_EB_ABS = 0, ZC_EB_REL = 1 } zc_eb_mode;
+
+#define ZC_HEADER_BYTES 32
+#define ZC_MAX_WIDTH 24
+
+/* Upper bound of the stream length for n elements at block size `block`
+ * (every block at the largest width, 24): size d_out with it.  Sizing rule
+ * only; no CUDA call. */
+size_t zc_max_compressed_bytes(uint64_t n, int block);
+
+/* Exact length of a raw stream of n elements of `dtype`. */
+size_t zc_raw_stream_bytes(uint64_t n, int dtype);
+
+/* Workspace bytes for calls on up to `n_total` elements spread over up to
+ * `n_items` items (1 for single calls, P for batched ring steps and scatter
+ * packs, M for batched compression).  Host-side arithmetic only. */
+size_t zc_workspace_bytes(uint64_t n_total, int n_items);
+
+/* Zero the workspace (cudaMemsetAsync) and stamp it as initialised.  Call
+ * once after allocating it, on the stream that will use it. */
+int zc_workspace_init(void* d_ws, size_t ws_bytes, zc_stream_t s);
+
+/* Smallest and largest element of d_in[0..n) into d_minmax[0..1] (device
+ * FP32).  Non-finite input sets ZC_ERR_NONFINITE.  Used to fix one relative
+ * bound across several buffers (the ring takes one absolute bound for all its
+ * steps). */
+int zc_minmax(const void* d_in, uint64_t n, int dtype, float* d_minmax, void* d_ws,
+              size_t ws_bytes, zc_stream_t s);
+
+/* Compress d_in[0..n) (FP32 or BF16) into a stream at d_out.
+ *   eb_mode ZC_EB_ABS: eb = eb_value.
+ *   eb_mode ZC_EB_REL: eb = eb_value * (max - min) over the input in FP64
+ *     (max(|max|, 1) when max == min), resolved on the device by one extra
+ *     read of the input (value-range relative bound); the FP32 bound used is
+ *     written into the stream header.
+ *   block: 16, 32, 64 or 128.
+ *   *d_out_bytes (device u64) receives the stream length.
+ * The paper's Sec. 3.3.2 removes the offset buffer in unified memory and the
+ * per-call allocations of the compressor it adapts; here offsets stay in the
+ * workspace and nothing is read back to the host. */
+int zc_compress(const void* d_in, uint64_t n, int dtype, int eb_mode, double eb_value, int block,
+                void* d_out, size_t out_cap, uint64_t* d_out_bytes, void* d_ws, size_t ws_bytes,
+                zc_stream_t s);
+
+/* Decompress a stream of n elements into d_out as FP32 or BF16 (RNE of the
+ * FP32 reconstruction).  The stream's own header gives L and eb; a header
+ * that does not match n, a width above 24 or a block that would read past
+ * cmp_cap sets ZC_ERR_FORMAT.  Raw streams are copied (converted if
+ * out_dtype differs). */
+int zc_decompress(const void* d_cmp, size_t cmp_cap, void* d_out, uint64_t n, int out_dtype,
+                  void* d_ws, size_t ws_bytes, zc_stream_t s);
+
+/* One ring reduce-scatter step on one chunk (Sec. 3.2.3, 3.3.3): decode the
+ * received stream d_cmp_in, add d_local (FP32, one rounding, decoded + local),
+ * and re-encode the sum with the fixed absolute bound eb_abs at block size
+ * `block` into d_cmp_out.  Without a received stream (d_cmp_in NULL) the
+ * step is the ring's initial compression of d_local.  d_sum_out (nullable)
+ * receives the FP32 sum; d_cmp_out may be NULL when only the sum is wanted
+ * (the ring's last step).  Decompression, reduction and recompression run in
+ * one kernel pass over the chunk (Sec. 3.3.1 moves the reduction to the GPU;
+ * here it is fused with both codec passes). */
+int zc_reduce_step(const void* d_cmp_in, size_t cmp_in_cap, const float* d_local, uint64_t n,
+                   double eb_abs, int block, void* d_cmp_out, size_t out_cap,
+                   uint64_t* d_out_bytes, float* d_sum_out, void* d_ws, size_t ws_bytes,
+                   zc_stream_t s);
+
+/* One ring step for all P simulated ranks in one launch.  Item r describes
+ * rank r's chunk at this step (pointers as in zc_reduce_step, all device
+ * pointers; cmp_in NULL for the initial compression). */
+typedef struct {
+    const void* cmp_in;      /* received stream or NULL                       */
+    const float* local;      /* this rank's copy of the chunk (FP32)          */
+    void* cmp_out;           /* output stream or NULL                         */
+    float* sum_out;          /* FP32 sum or NULL                              */
+    uint64_t* out_bytes;     /* device u64: output stream length              */
+    uint64_t n;              /* chunk elements                                */
+    uint64_t cmp_in_cap;     /* bytes readable at cmp_in                      */
+    uint64_t out_cap;        /* bytes writable at cmp_out                     */
+} zc_reduce_item;
+
+/* A work-descriptor table in device memory, built once at set-up time (for
+ * example one per ring step, for the whole ring) and launched any number of
+ * times, also from a captured CUDA graph. */
+typedef struct {
+    int n_items;             /* descriptors in the table                      */
+    int rows;                /* tile height the table was built for           */
+    int block;               /* block size L                                  */
+    uint64_t total_tiles;    /* tiles of all items together                   */
+    const void* d_table;     /* the caller's device memory holding the table  */
+} zc_plan;
+
+/* Device bytes of a descriptor table for n_items items. */
+size_t zc_plan_table_bytes(int n_items);
+
+/* Build the table for one ring step over P ranks: validates every item,
+ * splits the items into tiles and copies the table to d_table with a
+ * synchronous cudaMemcpy (set-up time, not per step). */
+int zc_plan_reduce(zc_plan* plan, int P, const zc_reduce_item* h_items, double eb_abs, int block,
+                   void* d_table, size_t table_bytes);
+
+/* Launch the planned ring step: all P ranks' decompress -> add -> recompress
+ * in one kernel launch (the ring's per-round codec work of Sec. 3.2.3 for
+ * every rank at once). */
+int zc_reduce_step_batch(const zc_plan* plan, void* d_ws, size_t ws_bytes, zc_stream_t s);
+
+/* Scatter pack (Sec. 3.3.4, compressed binomial-tree Scatter/Scatterv): the
+ * root compresses segment p = d_in[h_displs[p] .. h_displs[p] + h_counts[p])
+ * into a complete stream of its own, for p = 0 .. P-1, and the streams are
+ * written back to back into d_out in one launch.  d_seg_off (device, P + 1
+ * u64) receives the offset of each stream and the total length.  A relative
+ * bound is resolved over all segments together.  P <= 1024. */
+int zc_scatter_pack(const void* d_in, int dtype, int P, const uint64_t* h_counts,
+                    const uint64_t* h_displs, int eb_mode, double eb_value, int block,
+                    void* d_out, size_t out_cap, uint64_t* d_seg_off, void* d_ws,
+                    size_t ws_bytes, zc_stream_t s);
+
+/* Block until s is idle, then read the workspace status word (a zc_status)
+ * and the index (element or tile) where the first error was seen. */
+int zc_get_device_status(const void* d_ws, zc_stream_t s, int* status, uint64_t* detail);
+
+/* Reset the status word (asynchronous on s). */
+int zc_clear_device_status(void* d_ws, zc_stream_t s);
+
+/* Every device-side wait (the look-back for a predecessor tile's offset) gives
+ * up after this many nanoseconds, records ZC_ERR_TIMEOUT and returns.
+ * Default 1 s; process-wide; applies to launches issued afterwards. */
+void zc_set_wait_limit_ns(uint64_t ns);
+
+/* Test hook: the tile with this index (within the next launches) does not
+ * publish its offset, so that its successors' waits run out and report
+ * ZC_ERR_TIMEOUT.  -1 (default) disables it. */
+void zc_debug_withhold_tile(int64_t tile);
+
+/* Tile geometry of the next launches: rows of 32 elements per warp (4, 8 or
+ * 16; a tile is 8 warps x rows x 32 elements).  Returns ZC_ERR_ARG for other
+ * values.  Changes no stream byte. */
+int zc_set_rows_per_warp(int rows);
+
+/* Library version string. */
+const char* zc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ZC_H */

@@ -1,0 +1,480 @@
+// zc_api.cu -- the C ABI declared in include/zc.h: argument checks, workspace
+// carving, tile planning and kernel launches.  No call allocates memory, reads
+// device memory back (except zc_get_device_status and the setup-time plan
+// builder) or synchronises the stream.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "zc_launch.h"
+
+using namespace zc;
+
+namespace {
+
+int g_rows = 8;
+unsigned long long g_wait_ns = 1000000000ull;
+long long g_withhold = -1;
+
+inline uint64_t pad16(uint64_t v) { return (v + 15u) & ~(uint64_t)15u; }
+
+int log2_block(int block)
+{
+    switch (block) {
+    case 16: return 4;
+    case 32: return 5;
+    case 64: return 6;
+    case 128: return 7;
+    default: return -1;
+    }
+}
+
+inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+inline bool dtype_ok(int t) { return t == ZC_F32 || t == ZC_BF16; }
+inline uint64_t tile_elems(int rows) { return (uint64_t)NTHREADS * rows; }
+inline uint64_t tiles_for(uint64_t n, int rows)
+{
+    const uint64_t t = (n + tile_elems(rows) - 1) / tile_elems(rows);
+    return t ? t : 1;
+}
+
+// Host copy of the FP32 bound: eb, 2 eb and the rounded reciprocal of 2 eb.
+int qparams(double eb_abs, float* eb, float* two, float* inv)
+{
+    if (!(eb_abs > 0.0) || !std::isfinite(eb_abs)) return ZC_ERR_ARG;
+    const float e = (float)eb_abs;
+    if (!std::isnormal(e) || e <= 0.0f) return ZC_ERR_ARG;
+    volatile float t = e;
+    t = t + e;
+    if (!std::isfinite((float)t)) return ZC_ERR_ARG;
+    *eb = e;
+    *two = t;
+    *inv = (float)(0.5 / (double)e);
+    return ZC_OK;
+}
+
+struct WsView {
+    Ctl* ctl;
+    float2* partial;
+    Chain chA, chB;
+    unsigned long long* seg_flag;
+    uint64_t cap;  // tiles (and items) the workspace can hold
+};
+
+int ws_view(void* ws, size_t bytes, WsView& v)
+{
+    if (ws == nullptr || !aligned(ws, 16)) return ZC_ERR_ARG;
+    const uint64_t fixed = WS_CTL_BYTES + WS_RANGE_BYTES;
+    if (bytes < fixed + 7 * 8 * 4) return ZC_ERR_WORKSPACE;
+    const uint64_t cap = (bytes - fixed) / (7 * 8);
+    unsigned long long* base = (unsigned long long*)((char*)ws + fixed);
+    v.ctl = (Ctl*)ws;
+    v.partial = (float2*)((char*)ws + WS_CTL_BYTES);
+    v.chA = Chain{base, base + cap, base + 2 * cap};
+    v.chB = Chain{base + 3 * cap, base + 4 * cap, base + 5 * cap};
+    v.seg_flag = base + 6 * cap;
+    v.cap = cap;
+    return ZC_OK;
+}
+
+Launch base_launch(const WsView& w)
+{
+    Launch P;
+    std::memset(&P, 0, sizeof(P));
+    P.ctl = w.ctl;
+    P.chA = w.chA;
+    P.chB = w.chB;
+    P.seg_flag = w.seg_flag;
+    P.expect_log2L = -1;
+    P.wc.limit_ns = g_wait_ns;
+    P.wc.withhold = g_withhold;
+    return P;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? ZC_OK : ZC_ERR_CUDA; }
+
+unsigned range_grid(uint64_t n)
+{
+    uint64_t g = (n + 256 * 32 - 1) / (256 * 32);
+    if (g < 1) g = 1;
+    if (g > 1216) g = 1216;  // 8 CTAs per SM on 152 SMs
+    return (unsigned)g;
+}
+
+cudaError_t launch_compress_any(int lg, int rows, int dt, const Launch& P, unsigned grid,
+                                cudaStream_t s)
+{
+    switch (lg) {
+    case 4: return launch_compress_l16(rows, dt, P, grid, s);
+    case 5: return launch_compress_l32(rows, dt, P, grid, s);
+    case 6: return launch_compress_l64(rows, dt, P, grid, s);
+    default: return launch_compress_l128(rows, dt, P, grid, s);
+    }
+}
+
+cudaError_t launch_reduce_any(int lg, int rows, const Launch& P, unsigned grid, cudaStream_t s)
+{
+    switch (lg) {
+    case 4: return launch_reduce_l16(rows, P, grid, s);
+    case 5: return launch_reduce_l32(rows, P, grid, s);
+    case 6: return launch_reduce_l64(rows, P, grid, s);
+    default: return launch_reduce_l128(rows, P, grid, s);
+    }
+}
+
+cudaError_t launch_scatter_any(int lg, int rows, int dt, const Launch& P, const ScatterParams& S,
+                               unsigned grid, cudaStream_t s)
+{
+    switch (lg) {
+    case 4: return launch_scatter_l16(rows, dt, P, S, grid, s);
+    case 5: return launch_scatter_l32(rows, dt, P, S, grid, s);
+    case 6: return launch_scatter_l64(rows, dt, P, S, grid, s);
+    default: return launch_scatter_l128(rows, dt, P, S, grid, s);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* zc_version(void) { return "zc 0.1 (sm_103a)"; }
+
+size_t zc_max_compressed_bytes(uint64_t n, int block)
+{
+    const int lg = log2_block(block);
+    if (lg < 0) return 0;
+    const uint64_t L = 1ull << lg;
+    const uint64_t nb = (n + L - 1) / L;
+    return 32 + pad16(nb) + pad16(nb * (ZC_MAX_WIDTH + 1) * (L / 8));
+}
+
+size_t zc_raw_stream_bytes(uint64_t n, int dtype)
+{
+    if (!dtype_ok(dtype)) return 0;
+    return 32 + pad16(n * (dtype == ZC_F32 ? 4 : 2));
+}
+
+size_t zc_workspace_bytes(uint64_t n_total, int n_items)
+{
+    if (n_items < 1) n_items = 1;
+    const uint64_t tiles = n_total / (NTHREADS * MIN_ROWS) + 2ull * (uint64_t)n_items + 2;
+    const uint64_t b = WS_CTL_BYTES + WS_RANGE_BYTES + tiles * 7 * 8;
+    return (b + 255) & ~(uint64_t)255;
+}
+
+int zc_workspace_init(void* d_ws, size_t ws_bytes, zc_stream_t s)
+{
+    WsView w;
+    int st = ws_view(d_ws, ws_bytes, w);
+    if (st) return st;
+    if (cudaMemsetAsync(d_ws, 0, ws_bytes, (cudaStream_t)s) != cudaSuccess) return ZC_ERR_CUDA;
+    return cuda_status(launch_ws_init(w.ctl, (cudaStream_t)s));
+}
+
+int zc_minmax(const void* d_in, uint64_t n, int dtype, float* d_minmax, void* d_ws,
+              size_t ws_bytes, zc_stream_t s)
+{
+    if ((n > 0 && d_in == nullptr) || !dtype_ok(dtype) || d_minmax == nullptr) return ZC_ERR_ARG;
+    WsView w;
+    int st = ws_view(d_ws, ws_bytes, w);
+    if (st) return st;
+    RangeLaunch R;
+    std::memset(&R, 0, sizeof(R));
+    R.ctl = w.ctl;
+    R.partial = w.partial;
+    R.minmax_out = d_minmax;
+    R.one = RangeSeg{d_in, n};
+    R.total = n;
+    R.rel = 0.0;
+    R.dtype = dtype;
+    return cuda_status(launch_range(R, range_grid(n), (cudaStream_t)s));
+}
+
+int zc_compress(const void* d_in, uint64_t n, int dtype, int eb_mode, double eb_value, int block,
+                void* d_out, size_t out_cap, uint64_t* d_out_bytes, void* d_ws, size_t ws_bytes,
+                zc_stream_t s)
+{
+    const int lg = log2_block(block);
+    if (lg < 0 || !dtype_ok(dtype) || (n > 0 && d_in == nullptr) || d_out == nullptr ||
+        !aligned(d_out, 16) || d_out_bytes == nullptr || !aligned(d_in, dtype == ZC_F32 ? 4 : 2))
+        return ZC_ERR_ARG;
+    if (eb_mode != ZC_EB_ABS && eb_mode != ZC_EB_REL) return ZC_ERR_ARG;
+    if (!(eb_value > 0.0) || !std::isfinite(eb_value)) return ZC_ERR_ARG;
+    const uint64_t nb = (n + (1ull << lg) - 1) >> lg;
+    if (nb > 0xffffffffull) return ZC_ERR_ARG;
+    if (out_cap < 32 + pad16(nb)) return ZC_ERR_CAPACITY;
+    WsView w;
+    int st = ws_view(d_ws, ws_bytes, w);
+    if (st) return st;
+    const int rows = g_rows;
+    const uint64_t tiles = tiles_for(n, rows);
+    if (tiles > w.cap || tiles > 0x7fffffffull) return ZC_ERR_WORKSPACE;
+    Launch P = base_launch(w);
+    Item& it = P.one;
+    it.x = d_in;
+    it.out = (uint8_t*)d_out;
+    it.out_bytes = (unsigned long long*)d_out_bytes;
+    it.n = n;
+    it.out_cap = out_cap;
+    it.tile_begin = 0;
+    it.ntiles = (unsigned)tiles;
+    it.x_dtype = dtype;
+    it.out_dtype = dtype;
+    if (eb_mode == ZC_EB_ABS) {
+        st = qparams(eb_value, &it.eb, &it.two_eb, &it.inv);
+        if (st) return st;
+    } else {
+        RangeLaunch R;
+        std::memset(&R, 0, sizeof(R));
+        R.ctl = w.ctl;
+        R.partial = w.partial;
+        R.one = RangeSeg{d_in, n};
+        R.total = n;
+        R.rel = eb_value;
+        R.dtype = dtype;
+        if (launch_range(R, range_grid(n), (cudaStream_t)s) != cudaSuccess) return ZC_ERR_CUDA;
+        P.eb_from_ctl = 1;
+    }
+    P.n_items = 1;
+    P.total_tiles = (unsigned)tiles;
+    return cuda_status(launch_compress_any(lg, rows, dtype, P, (unsigned)tiles, (cudaStream_t)s));
+}
+
+int zc_decompress(const void* d_cmp, size_t cmp_cap, void* d_out, uint64_t n, int out_dtype,
+                  void* d_ws, size_t ws_bytes, zc_stream_t s)
+{
+    if (d_cmp == nullptr || !aligned(d_cmp, 16) || cmp_cap < 32 || (n > 0 && d_out == nullptr) ||
+        !dtype_ok(out_dtype) || !aligned(d_out, out_dtype == ZC_F32 ? 4 : 2))
+        return ZC_ERR_ARG;
+    WsView w;
+    int st = ws_view(d_ws, ws_bytes, w);
+    if (st) return st;
+    const int rows = g_rows;
+    const uint64_t tiles = tiles_for(n, rows);
+    if (tiles > w.cap || tiles > 0x7fffffffull) return ZC_ERR_WORKSPACE;
+    Launch P = base_launch(w);
+    Item& it = P.one;
+    it.cin = (const uint8_t*)d_cmp;
+    it.cin_cap = cmp_cap;
+    it.raw_out = d_out;
+    it.n = n;
+    it.tile_begin = 0;
+    it.ntiles = (unsigned)tiles;
+    it.out_dtype = out_dtype;
+    P.n_items = 1;
+    P.total_tiles = (unsigned)tiles;
+    return cuda_status(launch_decompress(rows, P, (unsigned)tiles, (cudaStream_t)s));
+}
+
+int zc_reduce_step(const void* d_cmp_in, size_t cmp_in_cap, const float* d_local, uint64_t n,
+                   double eb_abs, int block, void* d_cmp_out, size_t out_cap,
+                   uint64_t* d_out_bytes, float* d_sum_out, void* d_ws, size_t ws_bytes,
+                   zc_stream_t s)
+{
+    const int lg = log2_block(block);
+    if (lg < 0 || (n > 0 && d_local == nullptr) || !aligned(d_local, 4)) return ZC_ERR_ARG;
+    if (d_cmp_out == nullptr && d_sum_out == nullptr) return ZC_ERR_ARG;
+    if (d_cmp_in != nullptr && (!aligned(d_cmp_in, 16) || cmp_in_cap < 32)) return ZC_ERR_ARG;
+    if (d_cmp_out != nullptr && (!aligned(d_cmp_out, 16) || d_out_bytes == nullptr))
+        return ZC_ERR_ARG;
+    if (!aligned(d_sum_out, 4)) return ZC_ERR_ARG;
+    const uint64_t nb = (n + (1ull << lg) - 1) >> lg;
+    if (d_cmp_out != nullptr && out_cap < 32 + pad16(nb)) return ZC_ERR_CAPACITY;
+    WsView w;
+    int st = ws_view(d_ws, ws_bytes, w);
+    if (st) return st;
+    const int rows = g_rows;
+    const uint64_t tiles = tiles_for(n, rows);
+    if (tiles > w.cap || tiles > 0x7fffffffull) return ZC_ERR_WORKSPACE;
+    Launch P = base_launch(w);
+    Item& it = P.one;
+    st = qparams(eb_abs, &it.eb, &it.two_eb, &it.inv);
+    if (st) return st;
+    it.x = d_local;
+    it.cin = (const uint8_t*)d_cmp_in;
+    it.cin_cap = cmp_in_cap;
+    it.out = (uint8_t*)d_cmp_out;
+    it.out_cap = out_cap;
+    it.out_bytes = (unsigned long long*)d_out_bytes;
+    it.raw_out = d_sum_out;
+    it.n = n;
+    it.tile_begin = 0;
+    it.ntiles = (unsigned)tiles;
+    it.x_dtype = ZC_F32;
+    it.out_dtype = ZC_F32;
+    P.n_items = 1;
+    P.total_tiles = (unsigned)tiles;
+    return cuda_status(launch_reduce_any(lg, rows, P, (unsigned)tiles, (cudaStream_t)s));
+}
+
+size_t zc_plan_table_bytes(int n_items)
+{
+    return n_items > 0 ? sizeof(Item) * (size_t)n_items : 0;
+}
+
+int zc_plan_reduce(zc_plan* plan, int P, const zc_reduce_item* h_items, double eb_abs, int block,
+                   void* d_table, size_t table_bytes)
+{
+    const int lg = log2_block(block);
+    if (plan == nullptr || P < 1 || h_items == nullptr || lg < 0 || d_table == nullptr ||
+        !aligned(d_table, 16) || table_bytes < zc_plan_table_bytes(P))
+        return ZC_ERR_ARG;
+    float eb, two, inv;
+    int st = qparams(eb_abs, &eb, &two, &inv);
+    if (st) return st;
+    const int rows = g_rows;
+    std::vector<Item> items((size_t)P);
+    uint64_t tile = 0;
+    for (int r = 0; r < P; ++r) {
+        const zc_reduce_item& h = h_items[r];
+        const uint64_t nb = (h.n + (1ull << lg) - 1) >> lg;
+        if ((h.n > 0 && h.local == nullptr) || (h.cmp_out == nullptr && h.sum_out == nullptr))
+            return ZC_ERR_ARG;
+        if (h.cmp_in != nullptr && (!aligned(h.cmp_in, 16) || h.cmp_in_cap < 32)) return ZC_ERR_ARG;
+        if (h.cmp_out != nullptr && (!aligned(h.cmp_out, 16) || h.out_bytes == nullptr))
+            return ZC_ERR_ARG;
+        if (h.cmp_out != nullptr && h.out_cap < 32 + pad16(nb)) return ZC_ERR_CAPACITY;
+        Item& it = items[r];
+        std::memset(&it, 0, sizeof(it));
+        it.x = h.local;
+        it.cin = (const uint8_t*)h.cmp_in;
+        it.cin_cap = h.cmp_in_cap;
+        it.out = (uint8_t*)h.cmp_out;
+        it.out_cap = h.out_cap;
+        it.out_bytes = (unsigned long long*)h.out_bytes;
+        it.raw_out = h.sum_out;
+        it.n = h.n;
+        it.eb = eb;
+        it.two_eb = two;
+        it.inv = inv;
+        it.tile_begin = (unsigned)tile;
+        it.ntiles = (unsigned)tiles_for(h.n, rows);
+        it.x_dtype = ZC_F32;
+        it.out_dtype = ZC_F32;
+        tile += it.ntiles;
+    }
+    if (tile > 0x7fffffffull) return ZC_ERR_ARG;
+    if (cudaMemcpy(d_table, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return ZC_ERR_CUDA;
+    plan->n_items = P;
+    plan->rows = rows;
+    plan->block = block;
+    plan->total_tiles = tile;
+    plan->d_table = d_table;
+    return ZC_OK;
+}
+
+int zc_reduce_step_batch(const zc_plan* plan, void* d_ws, size_t ws_bytes, zc_stream_t s)
+{
+    if (plan == nullptr || plan->d_table == nullptr || plan->n_items < 1) return ZC_ERR_ARG;
+    const int lg = log2_block(plan->block);
+    if (lg < 0) return ZC_ERR_ARG;
+    WsView w;
+    int st = ws_view(d_ws, ws_bytes, w);
+    if (st) return st;
+    if (plan->total_tiles > w.cap) return ZC_ERR_WORKSPACE;
+    Launch P = base_launch(w);
+    P.items = (const Item*)plan->d_table;
+    P.n_items = (unsigned)plan->n_items;
+    P.total_tiles = (unsigned)plan->total_tiles;
+    return cuda_status(launch_reduce_any(lg, plan->rows, P, (unsigned)plan->total_tiles, (cudaStream_t)s));
+}
+
+int zc_scatter_pack(const void* d_in, int dtype, int P, const uint64_t* h_counts,
+                    const uint64_t* h_displs, int eb_mode, double eb_value, int block,
+                    void* d_out, size_t out_cap, uint64_t* d_seg_off, void* d_ws,
+                    size_t ws_bytes, zc_stream_t s)
+{
+    const int lg = log2_block(block);
+    if (lg < 0 || !dtype_ok(dtype) || P < 1 || P > SCATTER_MAX || h_counts == nullptr ||
+        h_displs == nullptr || d_out == nullptr || !aligned(d_out, 16) || d_seg_off == nullptr ||
+        !aligned(d_in, dtype == ZC_F32 ? 4 : 2))
+        return ZC_ERR_ARG;
+    if (eb_mode != ZC_EB_ABS && eb_mode != ZC_EB_REL) return ZC_ERR_ARG;
+    if (!(eb_value > 0.0) || !std::isfinite(eb_value)) return ZC_ERR_ARG;
+    WsView w;
+    int st = ws_view(d_ws, ws_bytes, w);
+    if (st) return st;
+    const int rows = g_rows;
+    static ScatterParams S;  // host staging of the by-value parameter block
+    uint64_t tile = 0, total_n = 0, min_cap = 0;
+    std::vector<const void*> ptrs((size_t)P);
+    std::vector<unsigned long long> cnts((size_t)P);
+    const uint64_t es = dtype == ZC_F32 ? 4 : 2;
+    for (int p = 0; p < P; ++p) {
+        if (h_counts[p] > 0 && d_in == nullptr) return ZC_ERR_ARG;
+        const uint64_t nb = (h_counts[p] + (1ull << lg) - 1) >> lg;
+        if (nb > 0xffffffffull) return ZC_ERR_ARG;
+        S.tile_begin[p] = (unsigned)tile;
+        S.displ[p] = h_displs[p];
+        S.count[p] = h_counts[p];
+        tile += tiles_for(h_counts[p], rows);
+        total_n += h_counts[p];
+        min_cap += 32 + pad16(nb);
+        ptrs[p] = (const uint8_t*)d_in + h_displs[p] * es;
+        cnts[p] = h_counts[p];
+    }
+    S.tile_begin[P] = (unsigned)tile;
+    if (out_cap < min_cap) return ZC_ERR_CAPACITY;
+    if (tile > w.cap || (uint64_t)P + 1 > w.cap || tile > 0x7fffffffull) return ZC_ERR_WORKSPACE;
+    Launch L = base_launch(w);
+    Item& it = L.one;
+    it.x = d_in;
+    it.out = (uint8_t*)d_out;
+    it.out_cap = out_cap;
+    it.x_dtype = dtype;
+    it.out_dtype = dtype;
+    if (eb_mode == ZC_EB_ABS) {
+        st = qparams(eb_value, &it.eb, &it.two_eb, &it.inv);
+        if (st) return st;
+    } else {
+        RangeLaunch R;
+        std::memset(&R, 0, sizeof(R));
+        R.ctl = w.ctl;
+        R.partial = w.partial;
+        R.total = total_n;
+        R.rel = eb_value;
+        R.dtype = dtype;
+        if (launch_range_multi(R, ptrs.data(), cnts.data(), (unsigned)P, range_grid(total_n),
+                               (cudaStream_t)s) != cudaSuccess)
+            return ZC_ERR_CUDA;
+        L.eb_from_ctl = 1;
+    }
+    L.packed = 1;
+    L.seg_off = (unsigned long long*)d_seg_off;
+    L.n_items = (unsigned)P;
+    L.total_tiles = (unsigned)tile;
+    return cuda_status(launch_scatter_any(lg, rows, dtype, L, S, (unsigned)tile, (cudaStream_t)s));
+}
+
+int zc_get_device_status(const void* d_ws, zc_stream_t s, int* status, uint64_t* detail)
+{
+    if (d_ws == nullptr || status == nullptr) return ZC_ERR_ARG;
+    Ctl c;
+    if (cudaMemcpyAsync(&c, d_ws, sizeof(Ctl), cudaMemcpyDeviceToHost, (cudaStream_t)s) != cudaSuccess)
+        return ZC_ERR_CUDA;
+    if (cudaStreamSynchronize((cudaStream_t)s) != cudaSuccess) return ZC_ERR_CUDA;
+    *status = (int)c.status;
+    if (detail) *detail = c.detail;
+    return ZC_OK;
+}
+
+int zc_clear_device_status(void* d_ws, zc_stream_t s)
+{
+    if (d_ws == nullptr) return ZC_ERR_ARG;
+    return cudaMemsetAsync(d_ws, 0, 4, (cudaStream_t)s) == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
+}
+
+void zc_set_wait_limit_ns(uint64_t ns) { g_wait_ns = ns ? ns : 1; }
+
+void zc_debug_withhold_tile(int64_t tile) { g_withhold = tile; }
+
+int zc_set_rows_per_warp(int rows)
+{
+    if (rows != 4 && rows != 8 && rows != 16) return ZC_ERR_ARG;
+    g_rows = rows;
+    return ZC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,351 @@
+// zc_device.cuh -- device building blocks of the codec kernels.
+//
+// Control block, status word, memory-ordering helpers, the bounded
+// decoupled look-back that turns per-tile byte counts into stream offsets in
+// one pass, the warp bit-matrix transpose that builds bit planes, and the
+// exact prequantizer.  Everything here is sm_103a CUDA; nothing is shared with
+// the CPU oracle.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "zc.h"
+
+namespace zc {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int NWARPS = 8;                  // warps per CTA
+constexpr int NTHREADS = NWARPS * 32;      // threads per CTA
+constexpr int MIN_ROWS = 4;                // smallest rows-per-warp: tile = 1024 elements
+constexpr unsigned WS_MAGIC = 0x5a435753u; // "ZCWS"
+constexpr int RANGE_SLOTS = 4096;          // partial min/max slots of the range kernel
+constexpr uint64_t WS_CTL_BYTES = 256;
+constexpr uint64_t WS_RANGE_BYTES = RANGE_SLOTS * 8;
+constexpr uint64_t WS_TILE_WORDS = 6;      // u64 words per tile: 2 look-back chains x 3
+constexpr int QMAX = 1 << 22;              // largest |q|
+
+// Workspace control block (first 256 bytes of the workspace).
+struct Ctl {
+    unsigned status;          // first data error, 0 = none
+    unsigned magic;           // WS_MAGIC once zc_workspace_init ran
+    unsigned long long detail;
+    unsigned ticket;          // tile ticket; wraps to 0 at the end of every launch
+    unsigned done;            // finished CTAs; wraps to 0 at the end of every launch
+    unsigned epoch;           // launch generation stamped on look-back flags
+    unsigned range_done;      // finished CTAs of the range kernel
+    float eb, two_eb, inv;    // bound resolved on the device (relative mode)
+    float mn, mx;             // extremes seen by the range kernel
+    unsigned eb_ok;           // 1 when eb/two_eb/inv above are usable
+};
+static_assert(sizeof(Ctl) <= WS_CTL_BYTES, "control block too large");
+
+// ---- memory-ordering helpers -------------------------------------------
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_volatile_u32(const unsigned* p)
+{
+    return *(const volatile unsigned*)p;
+}
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// First error wins; `detail` records where it was seen.
+__device__ __forceinline__ void fail(Ctl* c, unsigned code, unsigned long long detail)
+{
+    if (atomicCAS(&c->status, 0u, code) == 0u) c->detail = detail;
+}
+
+// Normal (not zero, subnormal, infinite or NaN) FP32 value.
+__device__ __forceinline__ bool is_normal(float f)
+{
+    const unsigned e = (__float_as_uint(f) >> 23) & 0xffu;
+    return e != 0u && e != 0xffu;
+}
+
+__device__ __forceinline__ unsigned long long ceil16(unsigned long long v)
+{
+    return (v + 15ull) & ~15ull;
+}
+
+// ---- warp bit-matrix transpose -----------------------------------------
+// Lane i holds word u_i; afterwards lane k holds the word whose bit i is bit k
+// of u_i.  Five butterfly stages; each exchanges the off-diagonal sub-blocks
+// of the current block size with one shuffle, one funnel rotate and one
+// bit-select.  The transpose is its own inverse.
+__device__ __forceinline__ uint32_t transpose32(uint32_t u, int lane)
+{
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int j = 16 >> s;
+        const uint32_t m = s == 0 ? 0x0000ffffu
+                         : s == 1 ? 0x00ff00ffu
+                         : s == 2 ? 0x0f0f0f0fu
+                         : s == 3 ? 0x33333333u
+                                  : 0x55555555u;
+        const bool lo = (lane & j) == 0;
+        const uint32_t p = __shfl_xor_sync(FULL, u, j);
+        const uint32_t sh = __funnelshift_l(p, p, lo ? j : 32 - j);
+        const uint32_t keep = lo ? m : ~m;
+        u = (u & keep) | (sh & ~keep);
+    }
+    return u;
+}
+
+// ---- prequantization ------------------------------------------------------
+// q = the integer nearest to x / two_eb, ties to even, exactly.
+// Fast path: v = x * inv rounds (at most two roundings) to within |v| 2^-22.9
+// of the exact quotient; if v is farther than |v| 2^-20 from a half-integer,
+// rint(v) is the exact answer.  rint uses the 1.5 * 2^23 magic add (exact for
+// |v| < 2^22; the fast test already fails for |v| >= 2^19).
+// Slow path (near a tie, large |v|, non-finite): q0 = rint(v), then the
+// residual r = x - q0 * two_eb, rounded once by an FMA, decides exactly
+// whether q0 or its neighbour is nearest (the residual is a multiple of
+// ulp(eb) near |r| = eb, so rounding cannot move it across eb).
+// Returns 0 or a zc_status code.
+__device__ __forceinline__ int quantize(float x, float eb, float two_eb, float inv, int& q)
+{
+    const float v = __fmul_rn(x, inv);
+    const float t = __fadd_rn(v, 12582912.0f);
+    const float r = __fsub_rn(t, 12582912.0f);
+    const float f = fabsf(__fsub_rn(v, r));
+    if (__fmaf_rn(fabsf(v), 9.5367431640625e-07f, f) < 0.5f) {  // |v| * 2^-20
+        q = __float_as_int(t) - 0x4b400000;
+        return 0;
+    }
+    q = 0;
+    if (!isfinite(x)) return ZC_ERR_NONFINITE;
+    if (!(fabsf(v) <= 4194308.0f)) return ZC_ERR_RANGE;
+    int q0 = __float2int_rn(v);
+    const float res = __fmaf_rn(-__int2float_rn(q0), two_eb, x);
+    const float ares = fabsf(res);
+    const int step = res > 0.0f ? 1 : -1;
+    if (ares > eb) q0 += step;
+    else if (ares == eb && (q0 & 1)) q0 += step;
+    if (q0 > QMAX || q0 < -QMAX) return ZC_ERR_RANGE;
+    q = q0;
+    return 0;
+}
+
+// ---- decoupled look-back over tile byte counts ---------------------------
+// A chain of tiles computes, in one pass, the byte position where each tile's
+// payload starts.  Tile t contributes a transform X -> X + a, or, when it ends
+// a stream (h), X -> ceil16(X + a) + b (the stream is padded to 16 bytes).
+// Transforms compose associatively, so a tile sums its predecessors'
+// published aggregates until it meets a published inclusive prefix.
+struct Xf {
+    unsigned long long a, b;
+    bool h;
+};
+__device__ __forceinline__ Xf xf_id() { return Xf{0ull, 0ull, false}; }
+// apply f first, then s
+__device__ __forceinline__ Xf xf_compose(const Xf& f, const Xf& s)
+{
+    Xf r;
+    if (!s.h) {
+        r.h = f.h;
+        r.a = f.h ? f.a : f.a + s.a;
+        r.b = f.h ? f.b + s.a : 0ull;
+    } else if (!f.h) {
+        r.h = true;
+        r.a = f.a + s.a;
+        r.b = s.b;
+    } else {
+        r.h = true;
+        r.a = f.a;
+        r.b = ceil16(f.b + s.a) + s.b;
+    }
+    return r;
+}
+__device__ __forceinline__ unsigned long long xf_apply(const Xf& f, unsigned long long x)
+{
+    return f.h ? ceil16(x + f.a) + f.b : x + f.a;
+}
+__device__ __forceinline__ Xf xf_shfl_up(const Xf& f, int off)
+{
+    Xf o;
+    o.a = __shfl_up_sync(FULL, f.a, off);
+    o.b = __shfl_up_sync(FULL, f.b, off);
+    o.h = __shfl_up_sync(FULL, (int)f.h, off) != 0;
+    return o;
+}
+__device__ __forceinline__ Xf xf_shfl(const Xf& f, int src)
+{
+    Xf o;
+    o.a = __shfl_sync(FULL, f.a, src);
+    o.b = __shfl_sync(FULL, f.b, src);
+    o.h = __shfl_sync(FULL, (int)f.h, src) != 0;
+    return o;
+}
+
+// Flag word of a tile: [63:32] epoch, [31:30] state, [29] h, [28] big,
+// [27:0] aggregate (when not big; else the aggregate is in the value word).
+constexpr unsigned ST_AGG = 1u, ST_PREFIX = 2u;
+constexpr unsigned long long AGG_INLINE_MAX = (1ull << 28) - 1;
+
+struct Chain {
+    unsigned long long* flag;   // per tile
+    unsigned long long* aggw;   // per tile: aggregate when too large for the flag
+    unsigned long long* pref;   // per tile: inclusive prefix
+};
+
+__device__ __forceinline__ unsigned long long make_flag(unsigned E, unsigned st, bool h,
+                                                        unsigned long long agg)
+{
+    const bool big = agg > AGG_INLINE_MAX;
+    return ((unsigned long long)E << 32) | ((unsigned long long)st << 30) |
+           ((unsigned long long)h << 29) | ((unsigned long long)big << 28) |
+           (big ? 0ull : agg);
+}
+
+struct WaitCfg {
+    unsigned long long limit_ns;
+    long long withhold;  // tile that never publishes (test hook), -1 = none
+};
+
+// Run by one full warp.  g: this tile's slot; g0: first slot of its chain
+// (whose exclusive value is 0).  Publishes g's aggregate, looks back, publishes
+// g's inclusive prefix, and returns g's exclusive value.  On a wait that runs
+// out, sets *timed_out and returns 0 (the tile then writes nothing).
+__device__ __forceinline__ unsigned long long lookback(const Chain& ch, unsigned g, unsigned g0,
+                                       unsigned long long agg, bool h, unsigned E,
+                                       const WaitCfg& wc, Ctl* ctl, bool* timed_out)
+{
+    const int lane = threadIdx.x & 31;
+    const bool publish = (long long)g != wc.withhold;
+    const Xf self{agg, 0ull, h};
+    *timed_out = false;
+    if (g == g0) {
+        if (lane == 0 && publish) {
+            st_relaxed(ch.pref + g, xf_apply(self, 0ull));
+            if (agg > AGG_INLINE_MAX) st_relaxed(ch.aggw + g, agg);
+            st_release(ch.flag + g, make_flag(E, ST_PREFIX, h, agg));
+        }
+        return 0ull;
+    }
+    if (lane == 0 && publish) {
+        if (agg > AGG_INLINE_MAX) st_relaxed(ch.aggw + g, agg);
+        st_release(ch.flag + g, make_flag(E, ST_AGG, h, agg));
+    }
+    Xf acc = xf_id();
+    long long hi = (long long)g - 1;
+    unsigned long long excl = 0ull;
+    while (true) {
+        const long long j = hi - 31 + lane;
+        const bool virt = j < (long long)g0;
+        unsigned long long f = 0ull;
+        bool valid = virt;
+        if (!virt) {
+            f = ld_acquire(ch.flag + j);
+            valid = (unsigned)(f >> 32) == E && ((f >> 30) & 3u) != 0u;
+        }
+        const unsigned long long t0 = globaltimer();
+        unsigned ns = 32;
+        bool expired = false;
+        while (!__all_sync(FULL, valid)) {
+            // the decision to give up is taken by the whole warp at once
+            expired = __any_sync(FULL, globaltimer() - t0 > wc.limit_ns);
+            if (expired) break;
+            __nanosleep(ns);
+            ns = ns < 2048 ? ns * 2 : ns;
+            if (!valid) {
+                f = ld_acquire(ch.flag + j);
+                valid = (unsigned)(f >> 32) == E && ((f >> 30) & 3u) != 0u;
+            }
+        }
+        if (expired) {
+            *timed_out = true;
+            if (lane == 0) fail(ctl, ZC_ERR_TIMEOUT, g);
+            excl = 0ull;
+            break;
+        }
+        const bool is_pref = virt || ((f >> 30) & 3u) == ST_PREFIX;
+        const unsigned pmask = __ballot_sync(FULL, is_pref);
+        Xf t = xf_id();
+        if (!virt) {
+            t.h = (f >> 29) & 1u;
+            t.a = ((f >> 28) & 1u) ? ld_relaxed(ch.aggw + j) : (f & AGG_INLINE_MAX);
+        }
+        const int p = pmask ? 31 - __clz(pmask) : -1;
+        if (lane <= p) t = xf_id();
+        // inclusive composition over lanes: lane 31 ends with T_{p+1} o ... o T_31
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const Xf o = xf_shfl_up(t, off);
+            if (lane >= off) t = xf_compose(o, t);
+        }
+        const Xf w = xf_shfl(t, 31);
+        acc = xf_compose(w, acc);
+        if (p >= 0) {
+            unsigned long long pv = 0ull;
+            if (lane == p && !virt) pv = ld_relaxed(ch.pref + j);
+            pv = __shfl_sync(FULL, pv, p);
+            excl = xf_apply(acc, pv);
+            break;
+        }
+        hi -= 32;
+    }
+    if (lane == 0 && publish) {
+        st_relaxed(ch.pref + g, xf_apply(self, excl));
+        st_release(ch.flag + g, make_flag(E, ST_PREFIX, h, agg));
+    }
+    return excl;
+}
+
+// Bounded wait for a value published with st_release on `flag` (epoch E in
+// the high word, nonzero low word); returns false if the wait ran out.
+__device__ __forceinline__ bool wait_flag(const unsigned long long* flag, unsigned E,
+                                          unsigned long long limit_ns)
+{
+    unsigned long long t0 = 0ull;
+    unsigned ns = 32;
+    while (true) {
+        const unsigned long long f = ld_acquire(flag);
+        if ((unsigned)(f >> 32) == E && (unsigned)f != 0u) return true;
+        const unsigned long long now = globaltimer();
+        if (t0 == 0ull) t0 = now;
+        else if (now - t0 > limit_ns) return false;
+        __nanosleep(ns);
+        ns = ns < 2048 ? ns * 2 : ns;
+    }
+}
+
+// ---- element access -------------------------------------------------------
+
+__device__ __forceinline__ float bf16_to_f32(uint16_t b)
+{
+    return __uint_as_float((uint32_t)b << 16);
+}
+// Round to nearest even; the reconstruction is finite.
+__device__ __forceinline__ uint16_t f32_to_bf16(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)((u >> 16) | ((u & 0x7fffffu) ? 0x40u : 0u));
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+}  // namespace zc

@@ -1,0 +1,46 @@
+// zc_launch.h -- host-side launch entry points of the kernel translation units.
+#pragma once
+
+#include "zc_codec.cuh"
+
+namespace zc {
+
+// One translation unit per block size instantiates the compress and ring-step
+// kernels for every tile height; these pick the instantiation at run time.
+cudaError_t launch_compress_l16(int rows, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_compress_l32(int rows, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_compress_l64(int rows, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_compress_l128(int rows, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_reduce_l16(int rows, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_reduce_l32(int rows, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_reduce_l64(int rows, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_reduce_l128(int rows, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_decompress(int rows, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_scatter_l16(int rows, int x_dtype, const Launch& P, const ScatterParams& S, unsigned grid, cudaStream_t s);
+cudaError_t launch_scatter_l32(int rows, int x_dtype, const Launch& P, const ScatterParams& S, unsigned grid, cudaStream_t s);
+cudaError_t launch_scatter_l64(int rows, int x_dtype, const Launch& P, const ScatterParams& S, unsigned grid, cudaStream_t s);
+cudaError_t launch_scatter_l128(int rows, int x_dtype, const Launch& P, const ScatterParams& S, unsigned grid, cudaStream_t s);
+
+// Range: extremes of the listed segments, then (rel > 0) the bound they imply.
+struct RangeSeg {
+    const void* x;
+    unsigned long long n;
+};
+constexpr int RANGE_MAX_SEGS = 1024;
+struct RangeLaunch {
+    Ctl* ctl;
+    float2* partial;        // RANGE_SLOTS slots
+    float* minmax_out;      // optional: device float[2]
+    RangeSeg one;           // the input (single-segment launches)
+    unsigned n_segs;
+    unsigned long long total;
+    double rel;             // > 0: resolve eb = rel * range into ctl
+    int dtype;
+};
+cudaError_t launch_range(const RangeLaunch& R, unsigned grid, cudaStream_t s);
+cudaError_t launch_range_multi(const RangeLaunch& R, const void* const* ptrs,
+                               const unsigned long long* counts, unsigned nseg, unsigned grid,
+                               cudaStream_t s);
+cudaError_t launch_ws_init(Ctl* ctl, cudaStream_t s);
+
+}  // namespace zc

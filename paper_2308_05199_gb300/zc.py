@@ -1,0 +1,308 @@
+"""ctypes binding of libzc.so (include/zc.h): argument marshalling only.
+
+Every function named ``zc_*`` here calls the C entry point of the same name
+with raw device pointers; all work runs in the library's CUDA kernels.  PyTorch
+supplies device memory and streams.  The library must have been built
+(``paper_2308_05199_gb300.build``); if it is missing, the first call raises --
+there is no fallback.
+
+The helpers below the raw bindings (``Workspace``, ``compress``, ...) only
+allocate torch tensors and forward to the raw calls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+OK, ERR_ARG, ERR_RANGE, ERR_NONFINITE, ERR_CAPACITY, ERR_FORMAT, ERR_TIMEOUT, ERR_CUDA, \
+    ERR_WORKSPACE = range(9)
+F32, BF16 = 0, 1
+EB_ABS, EB_REL = 0, 1
+HEADER = 32
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ZcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__("%s returned zc status %d" % (where, status))
+        self.status = status
+
+
+class ZcReduceItem(ctypes.Structure):
+    _fields_ = [("cmp_in", ctypes.c_void_p), ("local", ctypes.c_void_p),
+                ("cmp_out", ctypes.c_void_p), ("sum_out", ctypes.c_void_p),
+                ("out_bytes", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("cmp_in_cap", ctypes.c_uint64), ("out_cap", ctypes.c_uint64)]
+
+
+class ZcPlan(ctypes.Structure):
+    _fields_ = [("n_items", ctypes.c_int), ("rows", ctypes.c_int), ("block", ctypes.c_int),
+                ("total_tiles", ctypes.c_uint64), ("d_table", ctypes.c_void_p)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libzc.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError("libzc.so is not built (%s); run "
+                                   "paper_2308_05199_gb300.build.build()" % path)
+            L = ctypes.CDLL(path)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+def _declare(L):
+    c = ctypes
+    vp, u64, sz, i32, dbl = c.c_void_p, c.c_uint64, c.c_size_t, c.c_int, c.c_double
+    sig = {
+        "zc_max_compressed_bytes": (sz, [u64, i32]),
+        "zc_raw_stream_bytes": (sz, [u64, i32]),
+        "zc_workspace_bytes": (sz, [u64, i32]),
+        "zc_workspace_init": (i32, [vp, sz, vp]),
+        "zc_minmax": (i32, [vp, u64, i32, vp, vp, sz, vp]),
+        "zc_compress": (i32, [vp, u64, i32, i32, dbl, i32, vp, sz, vp, vp, sz, vp]),
+        "zc_decompress": (i32, [vp, sz, vp, u64, i32, vp, sz, vp]),
+        "zc_reduce_step": (i32, [vp, sz, vp, u64, dbl, i32, vp, sz, vp, vp, vp, sz, vp]),
+        "zc_plan_table_bytes": (sz, [i32]),
+        "zc_plan_reduce": (i32, [c.POINTER(ZcPlan), i32, c.POINTER(ZcReduceItem), dbl, i32, vp,
+                                 sz]),
+        "zc_reduce_step_batch": (i32, [c.POINTER(ZcPlan), vp, sz, vp]),
+        "zc_scatter_pack": (i32, [vp, i32, i32, vp, vp, i32, dbl, i32, vp, sz, vp, vp, sz, vp]),
+        "zc_get_device_status": (i32, [vp, vp, c.POINTER(c.c_int), c.POINTER(u64)]),
+        "zc_clear_device_status": (i32, [vp, vp]),
+        "zc_set_wait_limit_ns": (None, [u64]),
+        "zc_debug_withhold_tile": (None, [c.c_int64]),
+        "zc_set_rows_per_warp": (i32, [i32]),
+        "zc_version": (c.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def exported_names():
+    return ["zc_max_compressed_bytes", "zc_raw_stream_bytes", "zc_workspace_bytes",
+            "zc_workspace_init", "zc_minmax", "zc_compress", "zc_decompress", "zc_reduce_step",
+            "zc_plan_table_bytes", "zc_plan_reduce", "zc_reduce_step_batch", "zc_scatter_pack",
+            "zc_get_device_status", "zc_clear_device_status", "zc_set_wait_limit_ns",
+            "zc_debug_withhold_tile", "zc_set_rows_per_warp", "zc_version"]
+
+
+def _check(st: int, where: str):
+    if st != OK:
+        raise ZcError(st, where)
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.bfloat16:
+        return BF16
+    raise TypeError("zc takes float32 or bfloat16 tensors, got %s" % t.dtype)
+
+
+# ---- raw bindings (same names as the C ABI) --------------------------------
+
+def zc_max_compressed_bytes(n: int, block: int) -> int:
+    return lib().zc_max_compressed_bytes(n, block)
+
+
+def zc_raw_stream_bytes(n: int, dtype: int) -> int:
+    return lib().zc_raw_stream_bytes(n, dtype)
+
+
+def zc_workspace_bytes(n_total: int, n_items: int = 1) -> int:
+    return lib().zc_workspace_bytes(n_total, n_items)
+
+
+def zc_workspace_init(d_ws: int, ws_bytes: int, stream: int) -> int:
+    return lib().zc_workspace_init(d_ws, ws_bytes, stream)
+
+
+def zc_minmax(d_in, n, dtype, d_minmax, d_ws, ws_bytes, stream) -> int:
+    return lib().zc_minmax(d_in, n, dtype, d_minmax, d_ws, ws_bytes, stream)
+
+
+def zc_compress(d_in, n, dtype, eb_mode, eb_value, block, d_out, out_cap, d_out_bytes, d_ws,
+                ws_bytes, stream) -> int:
+    return lib().zc_compress(d_in, n, dtype, eb_mode, eb_value, block, d_out, out_cap,
+                             d_out_bytes, d_ws, ws_bytes, stream)
+
+
+def zc_decompress(d_cmp, cmp_cap, d_out, n, out_dtype, d_ws, ws_bytes, stream) -> int:
+    return lib().zc_decompress(d_cmp, cmp_cap, d_out, n, out_dtype, d_ws, ws_bytes, stream)
+
+
+def zc_reduce_step(d_cmp_in, cmp_in_cap, d_local, n, eb_abs, block, d_cmp_out, out_cap,
+                   d_out_bytes, d_sum_out, d_ws, ws_bytes, stream) -> int:
+    return lib().zc_reduce_step(d_cmp_in, cmp_in_cap, d_local, n, eb_abs, block, d_cmp_out,
+                                out_cap, d_out_bytes, d_sum_out, d_ws, ws_bytes, stream)
+
+
+def zc_plan_table_bytes(n_items: int) -> int:
+    return lib().zc_plan_table_bytes(n_items)
+
+
+def zc_plan_reduce(plan, P, h_items, eb_abs, block, d_table, table_bytes) -> int:
+    return lib().zc_plan_reduce(ctypes.byref(plan), P, h_items, eb_abs, block, d_table,
+                                table_bytes)
+
+
+def zc_reduce_step_batch(plan, d_ws, ws_bytes, stream) -> int:
+    return lib().zc_reduce_step_batch(ctypes.byref(plan), d_ws, ws_bytes, stream)
+
+
+def zc_scatter_pack(d_in, dtype, P, h_counts, h_displs, eb_mode, eb_value, block, d_out,
+                    out_cap, d_seg_off, d_ws, ws_bytes, stream) -> int:
+    return lib().zc_scatter_pack(d_in, dtype, P, h_counts, h_displs, eb_mode, eb_value, block,
+                                 d_out, out_cap, d_seg_off, d_ws, ws_bytes, stream)
+
+
+def zc_get_device_status(d_ws, stream):
+    st, detail = ctypes.c_int(0), ctypes.c_uint64(0)
+    r = lib().zc_get_device_status(d_ws, stream, ctypes.byref(st), ctypes.byref(detail))
+    _check(r, "zc_get_device_status")
+    return st.value, detail.value
+
+
+def zc_clear_device_status(d_ws, stream) -> int:
+    return lib().zc_clear_device_status(d_ws, stream)
+
+
+def zc_set_wait_limit_ns(ns: int):
+    lib().zc_set_wait_limit_ns(int(ns))
+
+
+def zc_debug_withhold_tile(tile: int):
+    lib().zc_debug_withhold_tile(int(tile))
+
+
+def zc_set_rows_per_warp(rows: int) -> int:
+    return lib().zc_set_rows_per_warp(rows)
+
+
+def zc_version() -> str:
+    return lib().zc_version().decode()
+
+
+# ---- tensor helpers ----------------------------------------------------------
+
+class Workspace:
+    """Device workspace sized for ``n_total`` elements over ``n_items`` items."""
+
+    def __init__(self, n_total: int, n_items: int = 1, device="cuda", stream=None):
+        self.nbytes = zc_workspace_bytes(n_total, n_items)
+        self.buf = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+        _check(zc_workspace_init(self.buf.data_ptr(), self.nbytes, _stream(stream)),
+               "zc_workspace_init")
+
+    @property
+    def ptr(self) -> int:
+        return self.buf.data_ptr()
+
+    def status(self, stream=None):
+        return zc_get_device_status(self.ptr, _stream(stream))
+
+    def clear(self, stream=None):
+        _check(zc_clear_device_status(self.ptr, _stream(stream)), "zc_clear_device_status")
+
+
+def empty_stream_buffer(n: int, block: int, device="cuda") -> torch.Tensor:
+    return torch.empty(zc_max_compressed_bytes(n, block), dtype=torch.uint8, device=device)
+
+
+def compress(x: torch.Tensor, eb: float, block: int = 32, mode: int = EB_ABS,
+             ws: Workspace | None = None, out: torch.Tensor | None = None,
+             out_bytes: torch.Tensor | None = None, stream=None):
+    """Compress a contiguous FP32/BF16 tensor; returns (stream buffer, u64 length tensor)."""
+    x = x.contiguous()
+    n = x.numel()
+    ws = ws or Workspace(n, 1, x.device, stream)
+    out = out if out is not None else empty_stream_buffer(n, block, x.device)
+    out_bytes = out_bytes if out_bytes is not None else torch.zeros(1, dtype=torch.int64,
+                                                                    device=x.device)
+    _check(zc_compress(x.data_ptr(), n, dtype_code(x), mode, float(eb), block, out.data_ptr(),
+                       out.numel(), out_bytes.data_ptr(), ws.ptr, ws.nbytes, _stream(stream)),
+           "zc_compress")
+    return out, out_bytes
+
+
+def decompress(cmp: torch.Tensor, n: int, out_dtype=torch.float32, ws: Workspace | None = None,
+               out: torch.Tensor | None = None, cmp_cap: int | None = None, stream=None):
+    ws = ws or Workspace(n, 1, cmp.device, stream)
+    out = out if out is not None else torch.empty(n, dtype=out_dtype, device=cmp.device)
+    _check(zc_decompress(cmp.data_ptr(), cmp_cap if cmp_cap is not None else cmp.numel(),
+                         out.data_ptr(), n, dtype_code(out), ws.ptr, ws.nbytes, _stream(stream)),
+           "zc_decompress")
+    return out
+
+
+def reduce_step(cmp_in, local: torch.Tensor, eb_abs: float, block: int = 32, want_stream=True,
+                want_sum=False, ws: Workspace | None = None, out=None, out_bytes=None,
+                sum_out=None, stream=None):
+    n = local.numel()
+    ws = ws or Workspace(n, 1, local.device, stream)
+    if want_stream:
+        out = out if out is not None else empty_stream_buffer(n, block, local.device)
+        out_bytes = out_bytes if out_bytes is not None else torch.zeros(1, dtype=torch.int64,
+                                                                        device=local.device)
+    if want_sum:
+        sum_out = sum_out if sum_out is not None else torch.empty(n, dtype=torch.float32,
+                                                                  device=local.device)
+    _check(zc_reduce_step(_ptr(cmp_in), cmp_in.numel() if cmp_in is not None else 0,
+                          local.data_ptr(), n, float(eb_abs), block,
+                          _ptr(out) if want_stream else None, out.numel() if want_stream else 0,
+                          _ptr(out_bytes) if want_stream else None,
+                          _ptr(sum_out) if want_sum else None, ws.ptr, ws.nbytes,
+                          _stream(stream)), "zc_reduce_step")
+    return (out if want_stream else None), (out_bytes if want_stream else None), \
+        (sum_out if want_sum else None)
+
+
+def scatter_pack(x: torch.Tensor, counts, displs, eb: float, block: int = 32, mode: int = EB_ABS,
+                 ws: Workspace | None = None, out=None, seg_off=None, stream=None):
+    x = x.contiguous()
+    P = len(counts)
+    ws = ws or Workspace(int(sum(counts)), P, x.device, stream)
+    cap = sum(zc_max_compressed_bytes(int(c), block) for c in counts)
+    out = out if out is not None else torch.empty(cap, dtype=torch.uint8, device=x.device)
+    seg_off = seg_off if seg_off is not None else torch.zeros(P + 1, dtype=torch.int64,
+                                                              device=x.device)
+    hc = (ctypes.c_uint64 * P)(*[int(c) for c in counts])
+    hd = (ctypes.c_uint64 * P)(*[int(d) for d in displs])
+    _check(zc_scatter_pack(x.data_ptr(), dtype_code(x), P, ctypes.addressof(hc),
+                           ctypes.addressof(hd), mode, float(eb), block, out.data_ptr(),
+                           out.numel(), seg_off.data_ptr(), ws.ptr, ws.nbytes, _stream(stream)),
+           "zc_scatter_pack")
+    return out, seg_off
+
+
+def stream_bytes(out: torch.Tensor, out_bytes: torch.Tensor) -> bytes:
+    """Copy a finished stream to the host (synchronises)."""
+    n = int(out_bytes.item())
+    return out[:n].cpu().numpy().tobytes()

@@ -1,0 +1,93 @@
+"""The C-ABI library on the CPU: it builds for sm_103a, loads, exports every
+function include/zc.h declares, and its host-side sizing rules agree with
+the stream format.  No compute call (there is no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+from paper_2308_05199_gb300 import build as zbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = zbuild.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "zc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(zc_[a-z0-9_]+)\s*\(",
+                       src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("zc_compress", "zc_decompress", "zc_reduce_step", "zc_scatter_pack",
+                 "zc_reduce_step_batch", "zc_minmax", "zc_workspace_bytes"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2308_05199_gb300 import zc
+    assert set(declared_functions()) <= set(zc.exported_names())
+
+
+def test_sizing_matches_format(lib):
+    lib.zc_max_compressed_bytes.restype = ctypes.c_size_t
+    lib.zc_max_compressed_bytes.argtypes = [ctypes.c_uint64, ctypes.c_int]
+    lib.zc_raw_stream_bytes.restype = ctypes.c_size_t
+    lib.zc_raw_stream_bytes.argtypes = [ctypes.c_uint64, ctypes.c_int]
+    lib.zc_workspace_bytes.restype = ctypes.c_size_t
+    lib.zc_workspace_bytes.argtypes = [ctypes.c_uint64, ctypes.c_int]
+    for n in (0, 1, 15, 16, 17, 1 << 20, (1 << 27) + 3):
+        for log2L in (4, 5, 6, 7):
+            assert lib.zc_max_compressed_bytes(n, 1 << log2L) == oracle.max_stream_bytes(n, log2L)
+        assert lib.zc_raw_stream_bytes(n, 0) == 32 + (4 * n + 15) // 16 * 16
+        assert lib.zc_raw_stream_bytes(n, 1) == 32 + (2 * n + 15) // 16 * 16
+    assert lib.zc_max_compressed_bytes(100, 48) == 0
+    a = lib.zc_workspace_bytes(1 << 20, 1)
+    b = lib.zc_workspace_bytes(1 << 27, 1)
+    c = lib.zc_workspace_bytes(1 << 27, 64)
+    assert 0 < a < b < c and a % 256 == 0
+    # one look-back record set per 1024-element tile, at most
+    assert b >= 7 * 8 * ((1 << 27) // 1024)
+
+
+def test_argument_errors_without_gpu(lib):
+    """Argument checks run before any CUDA call."""
+    lib.zc_compress.restype = ctypes.c_int
+    lib.zc_compress.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                ctypes.c_void_p]
+    fake = 1 << 20  # never dereferenced: every call below fails its argument check
+    # block size 48
+    assert lib.zc_compress(fake, 10, 0, 0, 1e-3, 48, fake, 4096, fake, fake, 1 << 20, None) == 1
+    # eb <= 0, NaN
+    assert lib.zc_compress(fake, 10, 0, 0, 0.0, 32, fake, 4096, fake, fake, 1 << 20, None) == 1
+    assert lib.zc_compress(fake, 10, 0, 0, float("nan"), 32, fake, 4096, fake, fake, 1 << 20,
+                           None) == 1
+    # misaligned output
+    assert lib.zc_compress(fake, 10, 0, 0, 1e-3, 32, fake + 4, 4096, fake, fake, 1 << 20,
+                           None) == 1
+    # output too small for header + widths
+    assert lib.zc_compress(fake, 1 << 20, 0, 0, 1e-3, 32, fake, 64, fake, fake, 1 << 24,
+                           None) == 4
+    # workspace too small
+    assert lib.zc_compress(fake, 1 << 20, 0, 0, 1e-3, 32, fake, 1 << 23, fake, fake, 4096,
+                           None) == 8
+    lib.zc_set_rows_per_warp.restype = ctypes.c_int
+    assert lib.zc_set_rows_per_warp(5) == 1
+    assert lib.zc_set_rows_per_warp(8) == 0
