@@ -248,7 +248,8 @@ def run_ours(args, rank, world):
     if args.rows:
         assert zc.zc_set_rows_per_warp(args.rows) == 0
     W = Workload(torch, zc, workloads, args.side, dev)
-    for _ in range(max(args.warmup, 3)):
+    args.warmup = max(args.warmup, 3)
+    for _ in range(args.warmup):
         W.step()
     torch.cuda.synchronize()
     st, det = W.ws.status()
