@@ -195,6 +195,31 @@ int zc_scatter_pack(const void* d_in, int dtype, int P, const uint64_t* h_counts
                     void* d_out, size_t out_cap, uint64_t* d_seg_off, void* d_ws,
                     size_t ws_bytes, zc_stream_t s);
 
+/* Compression for callers that may not allocate device memory (the paper has
+ * no counterpart to this entry point).  Code on a collective's progress path
+ * must not call cudaMalloc, which synchronises the whole device and would
+ * stall the communication it serves; a plugin inside a framework that owns
+ * all device memory through its own allocator has no way to obtain a
+ * workspace.  This variant of zc_compress takes no workspace: its scratch
+ * (look-back records, range partials, status word) is one fixed 1 MiB device
+ * array inside this library, present on every GPU that loads the library
+ * until the process exits.  It allocates nothing and calls no allocating
+ * routine.
+ *   - Arguments as zc_compress; n may not exceed ZC_NOALLOC_MAX_N (2^24
+ *     elements), larger n returns ZC_ERR_ARG at once.
+ *   - *d_status (device int, caller-owned) receives this call's device status
+ *     (a zc_status, 0 = success) when the call has run on s.
+ *   - The first call on a device sets the array up on that device (looks up
+ *     its address, zeroes it on s); make that first call before any stream
+ *     capture.
+ *   - All calls share the one array: calls that overlap on the GPU (on
+ *     different streams at the same time) race and corrupt each other's
+ *     output; order them on one stream or with events. */
+#define ZC_NOALLOC_MAX_N (1ull << 24)
+int zc_compress_noalloc(const void* d_in, uint64_t n, int dtype, int eb_mode, double eb_value,
+                        int block, void* d_out, size_t out_cap, uint64_t* d_out_bytes,
+                        int* d_status, zc_stream_t s);
+
 /* Block until s is idle, then read the workspace status word (a zc_status)
  * and the index (element or tile) where the first error was seen. */
 int zc_get_device_status(const void* d_ws, zc_stream_t s, int* status, uint64_t* detail);

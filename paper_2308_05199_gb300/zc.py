@@ -83,6 +83,7 @@ def _declare(L):
                                  sz]),
         "zc_reduce_step_batch": (i32, [c.POINTER(ZcPlan), vp, sz, vp]),
         "zc_scatter_pack": (i32, [vp, i32, i32, vp, vp, i32, dbl, i32, vp, sz, vp, vp, sz, vp]),
+        "zc_compress_noalloc": (i32, [vp, u64, i32, i32, dbl, i32, vp, sz, vp, vp, vp]),
         "zc_get_device_status": (i32, [vp, vp, c.POINTER(c.c_int), c.POINTER(u64)]),
         "zc_clear_device_status": (i32, [vp, vp]),
         "zc_set_wait_limit_ns": (None, [u64]),
@@ -100,6 +101,7 @@ def exported_names():
     return ["zc_max_compressed_bytes", "zc_raw_stream_bytes", "zc_workspace_bytes",
             "zc_workspace_init", "zc_minmax", "zc_compress", "zc_decompress", "zc_reduce_step",
             "zc_plan_table_bytes", "zc_plan_reduce", "zc_reduce_step_batch", "zc_scatter_pack",
+            "zc_compress_noalloc",
             "zc_get_device_status", "zc_clear_device_status", "zc_set_wait_limit_ns",
             "zc_debug_withhold_tile", "zc_set_rows_per_warp", "zc_version"]
 
@@ -181,6 +183,15 @@ def zc_scatter_pack(d_in, dtype, P, h_counts, h_displs, eb_mode, eb_value, block
                     out_cap, d_seg_off, d_ws, ws_bytes, stream) -> int:
     return lib().zc_scatter_pack(d_in, dtype, P, h_counts, h_displs, eb_mode, eb_value, block,
                                  d_out, out_cap, d_seg_off, d_ws, ws_bytes, stream)
+
+
+def zc_compress_noalloc(d_in, n, dtype, eb_mode, eb_value, block, d_out, out_cap, d_out_bytes,
+                        d_status, stream) -> int:
+    return lib().zc_compress_noalloc(d_in, n, dtype, eb_mode, eb_value, block, d_out, out_cap,
+                                     d_out_bytes, d_status, stream)
+
+
+NOALLOC_MAX_N = 1 << 24
 
 
 def zc_get_device_status(d_ws, stream):
