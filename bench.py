@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--side", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--rows", type=int, default=0, help="tile height (rows of 32 per warp)")
+    ap.add_argument("--chunks", type=int, default=0, help="2048-element chunks per CTA tile")
     return ap.parse_args()
 
 
@@ -199,7 +199,8 @@ class Workload:
         self.pcap = P_RING * self.ccap
         self.packed = t.empty(self.pcap, dtype=t.uint8, device=device)
         self.seg = t.zeros(P_RING + 1, dtype=t.int64, device=device)
-        self.launches_per_step = 5  # range, compress, decompress, ring step, scatter pack
+        # range, compress, width scan, decompress, width scan, ring step, scatter pack
+        self.launches_per_step = 7
 
     def step(self, ev=None):
         zc, s, ws = self.zc, self.s, self.ws
@@ -245,8 +246,8 @@ def run_ours(args, rank, world):
     build.build()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    if args.rows:
-        assert zc.zc_set_rows_per_warp(args.rows) == 0
+    if args.chunks:
+        assert zc.zc_set_tile_chunks(args.chunks) == 0
     W = Workload(torch, zc, workloads, args.side, dev)
     args.warmup = max(args.warmup, 3)
     for _ in range(args.warmup):

@@ -164,9 +164,11 @@ typedef struct {
  * times, also from a captured CUDA graph. */
 typedef struct {
     int n_items;             /* descriptors in the table                      */
-    int rows;                /* tile height the table was built for           */
+    int tile_chunks;         /* tile size the table was built for             */
     int block;               /* block size L                                  */
+    int has_input;           /* some item decodes a received stream           */
     uint64_t total_tiles;    /* tiles of all items together                   */
+    uint64_t total_chunks;   /* width-scan chunks of all items together       */
     const void* d_table;     /* the caller's device memory holding the table  */
 } zc_plan;
 
@@ -201,7 +203,7 @@ int zc_scatter_pack(const void* d_in, int dtype, int P, const uint64_t* h_counts
  * stall the communication it serves; a plugin inside a framework that owns
  * all device memory through its own allocator has no way to obtain a
  * workspace.  This variant of zc_compress takes no workspace: its scratch
- * (look-back records, range partials, status word) is one fixed 1 MiB device
+ * (look-back records, range partials, status word) is one fixed 2 MiB device
  * array inside this library, present on every GPU that loads the library
  * until the process exits.  It allocates nothing and calls no allocating
  * routine.
@@ -237,10 +239,11 @@ void zc_set_wait_limit_ns(uint64_t ns);
  * ZC_ERR_TIMEOUT.  -1 (default) disables it. */
 void zc_debug_withhold_tile(int64_t tile);
 
-/* Tile geometry of the next launches: rows of 32 elements per warp (4, 8 or
- * 16; a tile is 8 warps x rows x 32 elements).  Returns ZC_ERR_ARG for other
- * values.  Changes no stream byte. */
-int zc_set_rows_per_warp(int rows);
+/* Tile size of the next encoder launches and plans: chunks of 2048 elements
+ * per CTA tile (4, 8 or 16; default 8).  Larger tiles shorten the chain of
+ * offsets between tiles and use more shared memory per CTA (6.6 KB per
+ * chunk).  Returns ZC_ERR_ARG for other values.  Changes no stream byte. */
+int zc_set_tile_chunks(int chunks);
 
 /* Library version string. */
 const char* zc_version(void);

@@ -12,7 +12,7 @@ using namespace zc;
 
 namespace {
 
-int g_rows = 8;
+int g_chunks = 8;  // sub-tiles of 2048 elements per encoder tile
 unsigned long long g_wait_ns = 1000000000ull;
 long long g_withhold = -1;
 
@@ -31,11 +31,19 @@ int log2_block(int block)
 
 inline bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 inline bool dtype_ok(int t) { return t == ZC_F32 || t == ZC_BF16; }
-inline uint64_t tile_elems(int rows) { return (uint64_t)NTHREADS * rows; }
+// An encoder tile is NWARPS warp units of `rows` rows of 32 elements (tile
+// size knob: chunks of 2048 elements, rows = 8 chunks); the decompressor's
+// tile is NWARPS units of DEC_U rows.
 inline uint64_t tiles_for(uint64_t n, int rows)
 {
-    const uint64_t t = (n + tile_elems(rows) - 1) / tile_elems(rows);
+    const uint64_t te = (uint64_t)NWARPS * rows * 32;
+    const uint64_t t = (n + te - 1) / te;
     return t ? t : 1;
+}
+// Width-scan chunks for `ntiles` tiles (one thread per warp unit).
+inline uint64_t chunks_for(uint64_t ntiles)
+{
+    return (ntiles * NWARPS + WSCAN - 1) / WSCAN;
 }
 
 // Host copy of the FP32 bound: eb, 2 eb and the rounded reciprocal of 2 eb.
@@ -53,26 +61,33 @@ int qparams(double eb_abs, float* eb, float* two, float* inv)
     return ZC_OK;
 }
 
+// Workspace: control block, range partials, then 8 arrays of `cap` u64:
+// decode-tile offsets, encoder look-back (flag, wide aggregate, prefix),
+// width-scan look-back (same three), per-item stream-start flags.
+constexpr uint64_t WS_ARRAYS = 8;
+
 struct WsView {
     Ctl* ctl;
     float2* partial;
-    Chain chA, chB;
+    unsigned long long* offs;
+    Chain chB, chC;
     unsigned long long* seg_flag;
-    uint64_t cap;  // tiles (and items) the workspace can hold
+    uint64_t cap;  // decode tiles (and tiles, chunks, items) the workspace can hold
 };
 
 int ws_view(void* ws, size_t bytes, WsView& v)
 {
     if (ws == nullptr || !aligned(ws, 16)) return ZC_ERR_ARG;
     const uint64_t fixed = WS_CTL_BYTES + WS_RANGE_BYTES;
-    if (bytes < fixed + 7 * 8 * 4) return ZC_ERR_WORKSPACE;
-    const uint64_t cap = (bytes - fixed) / (7 * 8);
+    if (bytes < fixed + WS_ARRAYS * 8 * 4) return ZC_ERR_WORKSPACE;
+    const uint64_t cap = (bytes - fixed) / (WS_ARRAYS * 8);
     unsigned long long* base = (unsigned long long*)((char*)ws + fixed);
     v.ctl = (Ctl*)ws;
     v.partial = (float2*)((char*)ws + WS_CTL_BYTES);
-    v.chA = Chain{base, base + cap, base + 2 * cap};
-    v.chB = Chain{base + 3 * cap, base + 4 * cap, base + 5 * cap};
-    v.seg_flag = base + 6 * cap;
+    v.offs = base;
+    v.chB = Chain{base + cap, base + 2 * cap, base + 3 * cap};
+    v.chC = Chain{base + 4 * cap, base + 5 * cap, base + 6 * cap};
+    v.seg_flag = base + 7 * cap;
     v.cap = cap;
     return ZC_OK;
 }
@@ -82,10 +97,11 @@ Launch base_launch(const WsView& w)
     Launch P;
     std::memset(&P, 0, sizeof(P));
     P.ctl = w.ctl;
-    P.chA = w.chA;
     P.chB = w.chB;
+    P.chC = w.chC;
+    P.offs = w.offs;
     P.seg_flag = w.seg_flag;
-    P.expect_log2L = -1;
+    P.urows = DEC_U;
     P.wc.limit_ns = g_wait_ns;
     P.wc.withhold = g_withhold;
     return P;
@@ -101,35 +117,35 @@ unsigned range_grid(uint64_t n)
     return (unsigned)g;
 }
 
-cudaError_t launch_compress_any(int lg, int rows, int dt, const Launch& P, unsigned grid,
+cudaError_t launch_compress_any(int lg, int S, int dt, const Launch& P, unsigned grid,
                                 cudaStream_t s)
 {
     switch (lg) {
-    case 4: return launch_compress_l16(rows, dt, P, grid, s);
-    case 5: return launch_compress_l32(rows, dt, P, grid, s);
-    case 6: return launch_compress_l64(rows, dt, P, grid, s);
-    default: return launch_compress_l128(rows, dt, P, grid, s);
+    case 4: return launch_compress_l16(S, dt, P, grid, s);
+    case 5: return launch_compress_l32(S, dt, P, grid, s);
+    case 6: return launch_compress_l64(S, dt, P, grid, s);
+    default: return launch_compress_l128(S, dt, P, grid, s);
     }
 }
 
-cudaError_t launch_reduce_any(int lg, int rows, const Launch& P, unsigned grid, cudaStream_t s)
+cudaError_t launch_reduce_any(int lg, int S, const Launch& P, unsigned grid, cudaStream_t s)
 {
     switch (lg) {
-    case 4: return launch_reduce_l16(rows, P, grid, s);
-    case 5: return launch_reduce_l32(rows, P, grid, s);
-    case 6: return launch_reduce_l64(rows, P, grid, s);
-    default: return launch_reduce_l128(rows, P, grid, s);
+    case 4: return launch_reduce_l16(S, P, grid, s);
+    case 5: return launch_reduce_l32(S, P, grid, s);
+    case 6: return launch_reduce_l64(S, P, grid, s);
+    default: return launch_reduce_l128(S, P, grid, s);
     }
 }
 
-cudaError_t launch_scatter_any(int lg, int rows, int dt, const Launch& P, const ScatterParams& S,
+cudaError_t launch_scatter_any(int lg, int C, int dt, const Launch& P, const ScatterParams& S,
                                unsigned grid, cudaStream_t s)
 {
     switch (lg) {
-    case 4: return launch_scatter_l16(rows, dt, P, S, grid, s);
-    case 5: return launch_scatter_l32(rows, dt, P, S, grid, s);
-    case 6: return launch_scatter_l64(rows, dt, P, S, grid, s);
-    default: return launch_scatter_l128(rows, dt, P, S, grid, s);
+    case 4: return launch_scatter_l16(C, dt, P, S, grid, s);
+    case 5: return launch_scatter_l32(C, dt, P, S, grid, s);
+    case 6: return launch_scatter_l64(C, dt, P, S, grid, s);
+    default: return launch_scatter_l128(C, dt, P, S, grid, s);
     }
 }
 
@@ -157,8 +173,10 @@ size_t zc_raw_stream_bytes(uint64_t n, int dtype)
 size_t zc_workspace_bytes(uint64_t n_total, int n_items)
 {
     if (n_items < 1) n_items = 1;
-    const uint64_t tiles = n_total / (NTHREADS * MIN_ROWS) + 2ull * (uint64_t)n_items + 2;
-    const uint64_t b = WS_CTL_BYTES + WS_RANGE_BYTES + tiles * 7 * 8;
+    // decode slots: one per warp unit of at least 32 rows (1024 elements),
+    // plus the partial tiles of every item
+    const uint64_t cap = n_total / 1024 + 16ull * (uint64_t)n_items + 2;
+    const uint64_t b = WS_CTL_BYTES + WS_RANGE_BYTES + cap * WS_ARRAYS * 8;
     return (b + 255) & ~(uint64_t)255;
 }
 
@@ -206,8 +224,8 @@ int zc_compress(const void* d_in, uint64_t n, int dtype, int eb_mode, double eb_
     WsView w;
     int st = ws_view(d_ws, ws_bytes, w);
     if (st) return st;
-    const int rows = g_rows;
-    const uint64_t tiles = tiles_for(n, rows);
+    const int C = g_chunks;
+    const uint64_t tiles = tiles_for(n, unit_rows(C));
     if (tiles > w.cap || tiles > 0x7fffffffull) return ZC_ERR_WORKSPACE;
     Launch P = base_launch(w);
     Item& it = P.one;
@@ -216,7 +234,6 @@ int zc_compress(const void* d_in, uint64_t n, int dtype, int eb_mode, double eb_
     it.out_bytes = (unsigned long long*)d_out_bytes;
     it.n = n;
     it.out_cap = out_cap;
-    it.tile_begin = 0;
     it.ntiles = (unsigned)tiles;
     it.x_dtype = dtype;
     it.out_dtype = dtype;
@@ -237,7 +254,8 @@ int zc_compress(const void* d_in, uint64_t n, int dtype, int eb_mode, double eb_
     }
     P.n_items = 1;
     P.total_tiles = (unsigned)tiles;
-    return cuda_status(launch_compress_any(lg, rows, dtype, P, (unsigned)tiles, (cudaStream_t)s));
+    P.urows = unit_rows(C);
+    return cuda_status(launch_compress_any(lg, C, dtype, P, (unsigned)tiles, (cudaStream_t)s));
 }
 
 int zc_decompress(const void* d_cmp, size_t cmp_cap, void* d_out, uint64_t n, int out_dtype,
@@ -249,21 +267,24 @@ int zc_decompress(const void* d_cmp, size_t cmp_cap, void* d_out, uint64_t n, in
     WsView w;
     int st = ws_view(d_ws, ws_bytes, w);
     if (st) return st;
-    const int rows = g_rows;
-    const uint64_t tiles = tiles_for(n, rows);
-    if (tiles > w.cap || tiles > 0x7fffffffull) return ZC_ERR_WORKSPACE;
+    const uint64_t tiles = tiles_for(n, DEC_U);
+    const uint64_t chunks = chunks_for(tiles);
+    if (tiles * NWARPS > w.cap || tiles > 0x7fffffffull) return ZC_ERR_WORKSPACE;
     Launch P = base_launch(w);
     Item& it = P.one;
     it.cin = (const uint8_t*)d_cmp;
     it.cin_cap = cmp_cap;
     it.raw_out = d_out;
     it.n = n;
-    it.tile_begin = 0;
     it.ntiles = (unsigned)tiles;
+    it.nchunks = (unsigned)chunks;
     it.out_dtype = out_dtype;
     P.n_items = 1;
+    P.urows = DEC_U;
+    P.total_tiles = (unsigned)chunks;
+    if (launch_wscan(P, (unsigned)chunks, (cudaStream_t)s) != cudaSuccess) return ZC_ERR_CUDA;
     P.total_tiles = (unsigned)tiles;
-    return cuda_status(launch_decompress(rows, P, (unsigned)tiles, (cudaStream_t)s));
+    return cuda_status(launch_decompress(P, (unsigned)tiles, (cudaStream_t)s));
 }
 
 int zc_reduce_step(const void* d_cmp_in, size_t cmp_in_cap, const float* d_local, uint64_t n,
@@ -283,9 +304,10 @@ int zc_reduce_step(const void* d_cmp_in, size_t cmp_in_cap, const float* d_local
     WsView w;
     int st = ws_view(d_ws, ws_bytes, w);
     if (st) return st;
-    const int rows = g_rows;
-    const uint64_t tiles = tiles_for(n, rows);
-    if (tiles > w.cap || tiles > 0x7fffffffull) return ZC_ERR_WORKSPACE;
+    const int C = g_chunks;
+    const uint64_t tiles = tiles_for(n, unit_rows(C));
+    const uint64_t chunks = chunks_for(tiles);
+    if (tiles * NWARPS > w.cap || tiles > 0x7fffffffull) return ZC_ERR_WORKSPACE;
     Launch P = base_launch(w);
     Item& it = P.one;
     st = qparams(eb_abs, &it.eb, &it.two_eb, &it.inv);
@@ -298,13 +320,18 @@ int zc_reduce_step(const void* d_cmp_in, size_t cmp_in_cap, const float* d_local
     it.out_bytes = (unsigned long long*)d_out_bytes;
     it.raw_out = d_sum_out;
     it.n = n;
-    it.tile_begin = 0;
     it.ntiles = (unsigned)tiles;
+    it.nchunks = (unsigned)chunks;
     it.x_dtype = ZC_F32;
     it.out_dtype = ZC_F32;
     P.n_items = 1;
+    P.urows = unit_rows(C);
+    if (d_cmp_in != nullptr) {
+        P.total_tiles = (unsigned)chunks;
+        if (launch_wscan(P, (unsigned)chunks, (cudaStream_t)s) != cudaSuccess) return ZC_ERR_CUDA;
+    }
     P.total_tiles = (unsigned)tiles;
-    return cuda_status(launch_reduce_any(lg, rows, P, (unsigned)tiles, (cudaStream_t)s));
+    return cuda_status(launch_reduce_any(lg, C, P, (unsigned)tiles, (cudaStream_t)s));
 }
 
 size_t zc_plan_table_bytes(int n_items)
@@ -322,9 +349,10 @@ int zc_plan_reduce(zc_plan* plan, int P, const zc_reduce_item* h_items, double e
     float eb, two, inv;
     int st = qparams(eb_abs, &eb, &two, &inv);
     if (st) return st;
-    const int rows = g_rows;
+    const int C = g_chunks;
     std::vector<Item> items((size_t)P);
-    uint64_t tile = 0;
+    uint64_t tile = 0, chunk = 0;
+    int has_cin = 0;
     for (int r = 0; r < P; ++r) {
         const zc_reduce_item& h = h_items[r];
         const uint64_t nb = (h.n + (1ull << lg) - 1) >> lg;
@@ -334,6 +362,7 @@ int zc_plan_reduce(zc_plan* plan, int P, const zc_reduce_item* h_items, double e
         if (h.cmp_out != nullptr && (!aligned(h.cmp_out, 16) || h.out_bytes == nullptr))
             return ZC_ERR_ARG;
         if (h.cmp_out != nullptr && h.out_cap < 32 + pad16(nb)) return ZC_ERR_CAPACITY;
+        if (!aligned(h.local, 4) || !aligned(h.sum_out, 4)) return ZC_ERR_ARG;
         Item& it = items[r];
         std::memset(&it, 0, sizeof(it));
         it.x = h.local;
@@ -348,19 +377,25 @@ int zc_plan_reduce(zc_plan* plan, int P, const zc_reduce_item* h_items, double e
         it.two_eb = two;
         it.inv = inv;
         it.tile_begin = (unsigned)tile;
-        it.ntiles = (unsigned)tiles_for(h.n, rows);
+        it.ntiles = (unsigned)tiles_for(h.n, unit_rows(C));
+        it.chunk_begin = (unsigned)chunk;
+        it.nchunks = (unsigned)chunks_for(it.ntiles);
         it.x_dtype = ZC_F32;
         it.out_dtype = ZC_F32;
         tile += it.ntiles;
+        chunk += it.nchunks;
+        has_cin |= h.cmp_in != nullptr;
     }
     if (tile > 0x7fffffffull) return ZC_ERR_ARG;
     if (cudaMemcpy(d_table, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice) !=
         cudaSuccess)
         return ZC_ERR_CUDA;
     plan->n_items = P;
-    plan->rows = rows;
+    plan->tile_chunks = C;
     plan->block = block;
+    plan->has_input = has_cin;
     plan->total_tiles = tile;
+    plan->total_chunks = chunk;
     plan->d_table = d_table;
     return ZC_OK;
 }
@@ -373,12 +408,19 @@ int zc_reduce_step_batch(const zc_plan* plan, void* d_ws, size_t ws_bytes, zc_st
     WsView w;
     int st = ws_view(d_ws, ws_bytes, w);
     if (st) return st;
-    if (plan->total_tiles > w.cap) return ZC_ERR_WORKSPACE;
+    const int C = plan->tile_chunks;
+    if (plan->total_tiles * NWARPS > w.cap || plan->total_chunks > w.cap) return ZC_ERR_WORKSPACE;
     Launch P = base_launch(w);
     P.items = (const Item*)plan->d_table;
     P.n_items = (unsigned)plan->n_items;
+    P.urows = unit_rows(C);
+    if (plan->has_input) {
+        P.total_tiles = (unsigned)plan->total_chunks;
+        if (launch_wscan(P, (unsigned)plan->total_chunks, (cudaStream_t)s) != cudaSuccess)
+            return ZC_ERR_CUDA;
+    }
     P.total_tiles = (unsigned)plan->total_tiles;
-    return cuda_status(launch_reduce_any(lg, plan->rows, P, (unsigned)plan->total_tiles, (cudaStream_t)s));
+    return cuda_status(launch_reduce_any(lg, C, P, (unsigned)plan->total_tiles, (cudaStream_t)s));
 }
 
 int zc_scatter_pack(const void* d_in, int dtype, int P, const uint64_t* h_counts,
@@ -396,8 +438,8 @@ int zc_scatter_pack(const void* d_in, int dtype, int P, const uint64_t* h_counts
     WsView w;
     int st = ws_view(d_ws, ws_bytes, w);
     if (st) return st;
-    const int rows = g_rows;
-    static ScatterParams S;  // host staging of the by-value parameter block
+    const int C = g_chunks;
+    static ScatterParams SP;  // host staging of the by-value parameter block
     uint64_t tile = 0, total_n = 0, min_cap = 0;
     std::vector<const void*> ptrs((size_t)P);
     std::vector<unsigned long long> cnts((size_t)P);
@@ -406,16 +448,16 @@ int zc_scatter_pack(const void* d_in, int dtype, int P, const uint64_t* h_counts
         if (h_counts[p] > 0 && d_in == nullptr) return ZC_ERR_ARG;
         const uint64_t nb = (h_counts[p] + (1ull << lg) - 1) >> lg;
         if (nb > 0xffffffffull) return ZC_ERR_ARG;
-        S.tile_begin[p] = (unsigned)tile;
-        S.displ[p] = h_displs[p];
-        S.count[p] = h_counts[p];
-        tile += tiles_for(h_counts[p], rows);
+        SP.tile_begin[p] = (unsigned)tile;
+        SP.displ[p] = h_displs[p];
+        SP.count[p] = h_counts[p];
+        tile += tiles_for(h_counts[p], unit_rows(C));
         total_n += h_counts[p];
         min_cap += 32 + pad16(nb);
         ptrs[p] = (const uint8_t*)d_in + h_displs[p] * es;
         cnts[p] = h_counts[p];
     }
-    S.tile_begin[P] = (unsigned)tile;
+    SP.tile_begin[P] = (unsigned)tile;
     if (out_cap < min_cap) return ZC_ERR_CAPACITY;
     if (tile > w.cap || (uint64_t)P + 1 > w.cap || tile > 0x7fffffffull) return ZC_ERR_WORKSPACE;
     Launch L = base_launch(w);
@@ -445,7 +487,8 @@ int zc_scatter_pack(const void* d_in, int dtype, int P, const uint64_t* h_counts
     L.seg_off = (unsigned long long*)d_seg_off;
     L.n_items = (unsigned)P;
     L.total_tiles = (unsigned)tile;
-    return cuda_status(launch_scatter_any(lg, rows, dtype, L, S, (unsigned)tile, (cudaStream_t)s));
+    L.urows = unit_rows(C);
+    return cuda_status(launch_scatter_any(lg, C, dtype, L, SP, (unsigned)tile, (cudaStream_t)s));
 }
 
 int zc_get_device_status(const void* d_ws, zc_stream_t s, int* status, uint64_t* detail)
@@ -470,10 +513,10 @@ void zc_set_wait_limit_ns(uint64_t ns) { g_wait_ns = ns ? ns : 1; }
 
 void zc_debug_withhold_tile(int64_t tile) { g_withhold = tile; }
 
-int zc_set_rows_per_warp(int rows)
+int zc_set_tile_chunks(int chunks)
 {
-    if (rows != 4 && rows != 8 && rows != 16) return ZC_ERR_ARG;
-    g_rows = rows;
+    if (chunks != 4 && chunks != 8 && chunks != 16) return ZC_ERR_ARG;
+    g_chunks = chunks;
     return ZC_OK;
 }
 

@@ -1,30 +1,45 @@
-// zc_codec.cuh -- the tile kernels: compress, decompress and the fused ring
-// step (decompress -> add -> recompress) share one tile body.
+// zc_codec.cuh -- the tile kernels: compress, decompress, the fused ring step
+// (decompress -> add -> recompress) and the scatter pack.
 //
-// Geometry.  A CTA is 8 warps; a warp handles R rows of 32 consecutive
-// elements, lane i holding element i of the row, so a tile is 256 R elements.
-// A block of L elements is L/32 rows (L >= 32) or half a row (L = 16); blocks
-// never straddle warps.  Encoding a row: exact quantization, Lorenzo delta
-// against the previous element of the block (block head against 0), the
-// magnitude shifted left with the sign in bit 0, then one warp bit-transpose:
-// lane k then holds bit plane k-1 (lane 0: the sign plane) of the row, so a
-// block with w-bit deltas is exactly lanes 0 .. w of its rows, stored with one
-// 4/8/16-byte store per lane.  Decoding runs the same steps backwards with an
-// inclusive warp scan in place of the delta.
+// Geometry.  A CTA is 8 warps.  A sub-tile is 2048 consecutive elements: each
+// warp owns R = 8 rows of 32, lane i holding element i of a row.  A block of
+// L elements is L/32 rows (L >= 32) or half a row (L = 16); blocks never
+// straddle warps.
 //
-// Offsets.  Each tile's payload size is known after its own pass; the tile's
-// position in the stream comes from the bounded decoupled look-back of
-// zc_device.cuh (one pass, no second kernel, no host readback).  The first
-// tile of a stream also counts the 32-byte header and the padded width bytes,
-// the last one rounds the stream up to 16 bytes, so the scan value is the
-// absolute position within the output buffer.  In packed mode (the scatter
-// pack) one chain runs through all streams, so stream p starts where stream
-// p-1 ended.
+// Encoding a row: exact quantization, Lorenzo delta against the previous
+// element of the block (the block head against 0), the magnitude shifted left
+// with the sign in bit 0, then one warp bit-matrix transpose: lane k then
+// holds bit plane k-1 (lane 0: the sign plane) of the row, so a block with
+// w-bit deltas is exactly lanes 0 .. w of its rows.  Decoding runs the same
+// steps backwards with an inclusive warp scan in place of the delta.
+//
+// Encoder offsets.  An encoder tile is S sub-tiles.  Every warp appends its
+// blocks' planes to its own shared-memory segment of each sub-tile (the
+// running offset is warp-uniform: no scan), so nothing waits until the whole
+// tile is encoded.  Then one CTA scan over the 8 S segment sizes, one
+// CTA-wide decoupled look-back for the tile's position in the stream, and a
+// coalesced copy of every segment to its place.  The first tile of a stream
+// also counts the 32-byte header and the padded width bytes; the last one
+// rounds the stream up to 16 bytes; in packed mode (the scatter pack) one
+// chain runs through all streams.
+//
+// Decoder offsets.  k_wscan reads only the width bytes of a stream and
+// writes the payload offset of every 2048-element decode tile (a chain over
+// 256-tile chunks); decoding then needs no look-back and no barrier.
 #pragma once
 
 #include "zc_device.cuh"
 
 namespace zc {
+
+constexpr int GR = 8;                  // rows held in registers at a time
+constexpr int WSCAN = NTHREADS;        // warp units per width-scan chunk
+constexpr int DEC_U = 64;              // rows per warp unit of the decompressor
+
+// Rows per warp unit of an encoder tile of `chunks` 2048-element chunks.
+__host__ __device__ constexpr int unit_rows(int chunks) { return chunks * 8; }
+// Largest payload of one warp unit of U rows: 32 U elements x 25 planes / 8.
+__host__ __device__ constexpr int seg_bytes(int U) { return U * 100; }
 
 struct Item {
     const void* x;            // raw input (compress) or local chunk (ring step), or null
@@ -34,41 +49,51 @@ struct Item {
     unsigned long long* out_bytes;
     unsigned long long n, cin_cap, out_cap;
     float eb, two_eb, inv;    // encoding bound
-    unsigned tile_begin, ntiles;
+    unsigned tile_begin, ntiles;    // tiles of this launch's geometry
+    unsigned chunk_begin, nchunks;  // width-scan chunks
     int x_dtype, out_dtype;
 };
 
 struct Launch {
     Ctl* ctl;
-    Chain chA, chB;                   // chain A: input stream offsets, B: output
+    Chain chB;                        // encoder tiles
+    Chain chC;                        // width-scan chunks
+    unsigned long long* offs;         // payload offset of every decode tile (global slot)
     unsigned long long* seg_flag;     // packed mode: stream start published per item
     unsigned long long* seg_off;      // packed mode: P + 1 stream offsets (caller's)
     const Item* items;                // device items, or null for `one`
     Item one;
-    unsigned n_items, total_tiles;
+    unsigned n_items, total_tiles;    // total_tiles: tiles (or chunks for k_wscan)
+    int urows;                        // rows per warp unit (decode slot = tile * NWARPS + warp)
     int eb_from_ctl;                  // relative bound resolved into ctl
     int packed;
-    int expect_log2L;                 // decode: required block size of the input (-1: any)
     WaitCfg wc;
 };
 
 struct Smem {
-    unsigned long long warp_tot[NWARPS];
-    unsigned long long base_in, base_out, stream_start, end;
+    LbSmem lb;
+    unsigned long long base, start, end;
     unsigned ticket, item, E;
-    int abort_in, abort_out;
+    int abort, hdr_lg;
     float eb, two_eb, inv;
 };
 
-template <typename T>
-__device__ __forceinline__ float load_x(const void* p, unsigned long long i);
-template <>
-__device__ __forceinline__ float load_x<float>(const void* p, unsigned long long i)
+// Dynamic shared memory of an encoder CTA with U-row warp units: every warp's
+// payload segment and width bytes.
+__host__ __device__ constexpr int enc_smem_bytes(int U)
 {
-    return __ldg((const float*)p + i);
+    return NWARPS * (seg_bytes(U) + U * 2);
+}
+
+template <typename T>
+__device__ __forceinline__ float load_x(const T* p, int i);
+template <>
+__device__ __forceinline__ float load_x<float>(const float* p, int i)
+{
+    return __ldg(p + i);
 }
 template <>
-__device__ __forceinline__ float load_x<uint16_t>(const void* p, unsigned long long i)
+__device__ __forceinline__ float load_x<uint16_t>(const uint16_t* p, int i)
 {
     return bf16_to_f32(__ldg((const unsigned short*)p + i));
 }
@@ -91,8 +116,16 @@ __device__ __forceinline__ int warp_excl_scan(int v, int lane, int& total)
     return s - v;
 }
 
-// Reads and checks an input stream header for `it`; returns its log2 L, or -1
-// (format error, reported) , or -2 for a raw stream.
+__device__ __forceinline__ int warp_sum(int v)
+{
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    return v;
+}
+
+// Reads and checks an input stream header for `it`; returns its log2 L, -1
+// for a format error (reported when `report`), -2 / -3 for a raw FP32 / BF16
+// stream.
 __device__ __forceinline__ int check_header(const Item& it, Ctl* ctl, unsigned item_idx,
                                             int expect_log2L, float& eb_in, bool report)
 {
@@ -115,7 +148,7 @@ __device__ __forceinline__ int check_header(const Item& it, Ctl* ctl, unsigned i
         const unsigned long long es = dtype == 0 ? 4ull : 2ull;
         ok = nb == 0u && payload == n * es && 32ull + ceil16(payload) <= it.cin_cap &&
              expect_log2L < 0;
-        ret = -2 - dtype;  // -2: raw f32, -3: raw bf16
+        ret = -2 - dtype;
     } else if (ok) {
         ok = lg >= 4 && lg <= 7 && (expect_log2L < 0 || lg == expect_log2L) &&
              (unsigned long long)nb == ((n + (1ull << lg) - 1) >> lg) &&
@@ -129,339 +162,539 @@ __device__ __forceinline__ int check_header(const Item& it, Ctl* ctl, unsigned i
     return ret;
 }
 
-// One tile.  HAS_CIN: decode `it.cin` (block size LOG2L).  HAS_X: read `it.x`
-// (type TX) and add it.  ENCODE: encode the result into `it.out`.  The raw
-// result goes to `it.raw_out` when that is set.  Null pointers switch the
-// matching step off at run time.
-template <int LOG2L, int R, bool HAS_CIN, bool HAS_X, bool ENCODE, typename TX>
-__device__ __forceinline__ void tile_codec(const Launch& P, const Item& it, unsigned item_idx,
-                                           unsigned tile_in_item, unsigned g, Smem& sm)
+__device__ __forceinline__ int planes_of(int w) { return w ? w + 1 : 0; }
+
+
+__device__ __forceinline__ uint8_t width_byte(int np) { return (uint8_t)(np ? np - 1 : 0); }
+
+// Inclusive prefix sum of exact FP32 integers over 32 lanes (FMA pipe).
+__device__ __forceinline__ float scan_incl_f(float v)
+{
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        asm("{\n\t.reg .f32 t;\n\t.reg .pred p;\n\t"
+            "shfl.sync.up.b32 t|p, %0, %1, 0, -1;\n\t"
+            "@p add.rn.f32 %0, %0, t;\n\t}"
+            : "+f"(v)
+            : "r"(off));
+    }
+    return v;
+}
+// The same over segments of 16 lanes.
+__device__ __forceinline__ float scan_incl_f16(float v)
+{
+#pragma unroll
+    for (int off = 1; off < 16; off <<= 1) {
+        asm("{\n\t.reg .f32 t;\n\t.reg .pred p;\n\t"
+            "shfl.sync.up.b32 t|p, %0, %1, 4096, -1;\n\t"
+            "@p add.rn.f32 %0, %0, t;\n\t}"
+            : "+f"(v)
+            : "r"(off));
+    }
+    return v;
+}
+
+// ---- decoding ------------------------------------------------------------------
+// Block planes and payload offsets of one warp unit of an input stream:
+// meta[b] = (planes, byte offset from the unit's payload start) for the
+// unit's blocks.  Returns the unit's payload start in the stream; a unit whose
+// planes would lie beyond cin_cap is reported and gets zero planes.
+template <int LOG2L, int U>
+__device__ __forceinline__ unsigned long long unit_meta(const Launch& P, const Item& it,
+                                                        unsigned slot, unsigned long long ue0,
+                                                        int2* meta)
 {
     constexpr int L = 1 << LOG2L;
-    constexpr int BW = R * 32 / L;            // blocks per warp
-    constexpr int RPB = L >= 32 ? L / 32 : 1; // rows per block
-    constexpr int PB = L / 8;                 // bytes per bit plane
-    static_assert(BW >= 1 && BW <= 32, "blocks per warp");
+    constexpr int PB = L / 8;
+    constexpr int BU = U * 32 / L;                // blocks per unit
+    constexpr int BPL = BU >= 32 ? BU / 32 : 1;   // blocks per lane
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nb = (it.n + L - 1) >> LOG2L;
+    const unsigned long long b0 = (ue0 >> LOG2L) + (unsigned long long)lane * BPL;
+    static_assert(BPL == 1 || BPL == 2 || BPL == 4 || BPL == 8, "width bytes per lane");
+    const bool mine = BU >= 32 || lane < BU;
+    uint32_t wv[2] = {0u, 0u};  // this lane's BPL width bytes, little-endian
+    if (mine && b0 < ceil16(nb)) {
+        // b0 is a multiple of BPL and the width bytes are zero padded to 16:
+        // the BPL bytes from b0 are inside the stream and naturally aligned
+        const uint8_t* wp = it.cin + 32 + b0;
+        if (BPL == 8) {
+            const uint2 v = __ldg((const uint2*)wp);
+            wv[0] = v.x;
+            wv[1] = v.y;
+        } else if (BPL == 4) {
+            wv[0] = __ldg((const unsigned*)wp);
+        } else if (BPL == 2) {
+            wv[0] = __ldg((const unsigned short*)wp);
+        } else {
+            wv[0] = __ldg(wp);
+        }
+    }
+    int np[BPL];
+    int sum = 0;
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < BPL; ++i) {
+        int w = (wv[i >> 2] >> (8 * (i & 3))) & 0xff;
+        if (w > ZC_MAX_WIDTH) {
+            bad = true;
+            w = 0;
+        }
+        np[i] = planes_of(w);
+        sum += np[i] * PB;
+    }
+    if (bad) fail(P.ctl, ZC_ERR_FORMAT, b0);
+    int tot;
+    int off = warp_excl_scan(sum, lane, tot);
+    const unsigned long long base = 32ull + ceil16(nb) + P.offs[slot];
+    const bool ok = base + (unsigned long long)tot <= it.cin_cap;
+    if (!ok && lane == 0) fail(P.ctl, ZC_ERR_FORMAT, slot);
+    __syncwarp();  // earlier readers of meta are done
+    if (mine) {
+#pragma unroll
+        for (int i = 0; i < BPL; ++i) {
+            meta[lane * BPL + i] = make_int2(ok ? np[i] : 0, off);
+            off += np[i] * PB;
+        }
+    }
+    __syncwarp();
+    return ok ? base : 0ull;
+}
+
+// Sign-magnitude word of one element -> its delta as an exact FP32 value
+// (|d| < 2^23), the sign injected into the float's sign bit.
+__device__ __forceinline__ float delta_f(uint32_t u)
+{
+    const float mag = __fsub_rn(__int_as_float((u >> 1) | 0x4b000000u), 8388608.0f);
+    return __int_as_float(__float_as_int(mag) ^ (u << 31));
+}
+
+// Decodes rows [g GR, g GR + GR) of a warp unit into acc[] (x^ = q * 2eb).
+// `src` points at the stream, offsets in `meta` are from the unit's payload
+// start `base`.  A pair of rows whose blocks have at most 16 planes shares one
+// transpose and is scanned in FP32 (every partial sum is an integer below
+// 2^22: exact); wider rows are scanned in integers.
+template <int LOG2L>
+__device__ __forceinline__ void decode_group(const uint8_t* src, const int2* meta, int g,
+                                             float two_eb, float acc[GR], const TpC& tc)
+{
+    constexpr int L = 1 << LOG2L;
+    constexpr int RPB = L >= 32 ? L / 32 : 1;
+    const int lane = threadIdx.x & 31;
+    const int k = lane & 15;
+    const bool hi = lane >= 16;
+    const int fb = L >= 32 ? g * GR / RPB : g * GR * 2;  // first block of the group
+    const int2* mt = meta + fb;
+#pragma unroll
+    for (int r = 0; r < GR; r += (L == 128 ? 4 : 2)) {
+        uint32_t u[4];
+        bool paired;
+        if (L == 32) {
+            const int4 m = *(const int4*)&mt[r];
+            paired = m.x <= 16 && m.z <= 16;
+            if (paired) {
+                const int np = hi ? m.z : m.x, off = hi ? m.w : m.y;
+                const uint32_t w = k < np ? __ldg((const unsigned*)(src + off) + k) : 0u;
+                const uint32_t t = tpose(w, tc);
+                u[0] = t & 0xffffu;
+                u[1] = t >> 16;
+            } else {
+                const uint32_t wa = lane < m.x ? __ldg((const unsigned*)(src + m.y) + lane) : 0u;
+                const uint32_t wb = lane < m.z ? __ldg((const unsigned*)(src + m.w) + lane) : 0u;
+                u[0] = tpose(wa, tc);
+                u[1] = tpose(wb, tc);
+            }
+        } else if (L == 16) {
+            const int4 m0 = *(const int4*)&mt[2 * r];
+            const int4 m1 = *(const int4*)&mt[2 * r + 2];
+            paired = max(max(m0.x, m0.z), max(m1.x, m1.z)) <= 16;
+            if (paired) {
+                const int npL = hi ? m1.x : m0.x, offL = hi ? m1.y : m0.y;
+                const int npH = hi ? m1.z : m0.z, offH = hi ? m1.w : m0.w;
+                const uint32_t wl = k < npL ? __ldg((const unsigned short*)(src + offL) + k) : 0u;
+                const uint32_t wh = k < npH ? __ldg((const unsigned short*)(src + offH) + k) : 0u;
+                const uint32_t t = tpose(wl | (wh << 16), tc);
+                u[0] = t & 0xffffu;
+                u[1] = t >> 16;
+            } else {
+                uint32_t wl = lane < m0.x ? __ldg((const unsigned short*)(src + m0.y) + lane) : 0u;
+                uint32_t wh = lane < m0.z ? __ldg((const unsigned short*)(src + m0.w) + lane) : 0u;
+                u[0] = tpose(wl | (wh << 16), tc);
+                wl = lane < m1.x ? __ldg((const unsigned short*)(src + m1.y) + lane) : 0u;
+                wh = lane < m1.z ? __ldg((const unsigned short*)(src + m1.w) + lane) : 0u;
+                u[1] = tpose(wl | (wh << 16), tc);
+            }
+        } else if (L == 64) {
+            const int2 m = mt[r / 2];
+            paired = m.x <= 16;
+            if (paired) {
+                const uint32_t w =
+                    k < m.x ? __ldg((const unsigned*)(src + m.y + 8 * k + (hi ? 4 : 0))) : 0u;
+                const uint32_t t = tpose(w, tc);
+                u[0] = t & 0xffffu;
+                u[1] = t >> 16;
+            } else {
+                uint2 v = make_uint2(0u, 0u);
+                if (lane < m.x) v = __ldg((const uint2*)(src + m.y) + lane);
+                u[0] = tpose(v.x, tc);
+                u[1] = tpose(v.y, tc);
+            }
+        } else {
+            const int2 m = mt[r / 4];
+            paired = m.x <= 16;
+            if (paired) {
+                const uint8_t* pp = src + m.y + 16 * k + (hi ? 4 : 0);
+                const uint32_t w0 = k < m.x ? __ldg((const unsigned*)pp) : 0u;
+                const uint32_t w1 = k < m.x ? __ldg((const unsigned*)(pp + 8)) : 0u;
+                const uint32_t t0 = tpose(w0, tc), t1 = tpose(w1, tc);
+                u[0] = t0 & 0xffffu;
+                u[1] = t0 >> 16;
+                u[2] = t1 & 0xffffu;
+                u[3] = t1 >> 16;
+            } else {
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (lane < m.x) v = __ldg((const uint4*)(src + m.y) + lane);
+                u[0] = tpose(v.x, tc);
+                u[1] = tpose(v.y, tc);
+                u[2] = tpose(v.z, tc);
+                u[3] = tpose(v.w, tc);
+            }
+        }
+        constexpr int NR = L == 128 ? 4 : 2;
+        if (paired) {
+            float carry = 0.0f;
+#pragma unroll
+            for (int h = 0; h < NR; ++h) {
+                float v = L == 16 ? scan_incl_f16(delta_f(u[h])) : scan_incl_f(delta_f(u[h]));
+                if (L >= 64 && ((r + h) % RPB) != 0) v = __fadd_rn(v, carry);
+                if (L >= 64 && ((r + h) % RPB) != RPB - 1) carry = __shfl_sync(FULL, v, 31);
+                acc[r + h] = __fmul_rn(v, two_eb);
+            }
+        } else {
+            int carry = 0;
+#pragma unroll
+            for (int h = 0; h < NR; ++h) {
+                const int mag = (int)(u[h] >> 1);
+                int v = L == 16 ? scan_incl<16>((u[h] & 1u) ? -mag : mag)
+                                : scan_incl<32>((u[h] & 1u) ? -mag : mag);
+                if (L >= 64 && ((r + h) % RPB) != 0) v += carry;
+                if (L >= 64 && ((r + h) % RPB) != RPB - 1) carry = __shfl_sync(FULL, v, 31);
+                acc[r + h] = __fmul_rn(__int2float_rn(v), two_eb);
+            }
+        }
+    }
+}
+
+// ---- encoding ------------------------------------------------------------------
+// Quantizes, delta-codes and bit-plane packs GR rows (the first `nrem`
+// elements are valid; the rest are padding with zero deltas), appends the
+// planes of their blocks to `seg` at byte `lo` in stream order, writes their
+// width bytes to `wb`, ORs any quantizer error into `err`, and returns the new
+// `lo`.  Two rows whose values fit 16 bits share one transpose.
+template <int LOG2L>
+__device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float eb, float two_eb,
+                                            float inv, uint8_t* seg, int lo, uint8_t* wb, int& err,
+                                            const TpC& tc)
+{
+    constexpr int L = 1 << LOG2L;
+    constexpr int RPB = L >= 32 ? L / 32 : 1;
+    const int lane = threadIdx.x & 31;
+    const int k = lane & 15;
+    const bool hi = lane >= 16;
+    uint32_t u[GR];
+    int carry = 0;
+#pragma unroll
+    for (int r = 0; r < GR; ++r) {
+        const bool valid = r * 32 + lane < nrem;
+        int q = 0;
+        if (valid) err |= quantize(acc[r], eb, two_eb, inv, q);
+        int prev = __shfl_up_sync(FULL, q, 1);
+        if (L == 16) {
+            if (k == 0) prev = 0;
+        } else if (lane == 0) {
+            prev = (L >= 64 && (r % RPB) != 0) ? carry : 0;
+        }
+        if (L >= 64 && (r % RPB) != RPB - 1) carry = __shfl_sync(FULL, q, 31);
+        const int d = valid ? q - prev : 0;
+        const uint32_t ad = (uint32_t)(d < 0 ? -d : d);
+        u[r] = __funnelshift_l((uint32_t)d, ad, 1);  // |d| << 1 | sign
+    }
+#pragma unroll
+    for (int r = 0; r < GR; r += (L == 128 ? 4 : 2)) {
+        if (L == 32) {
+            int npA, npB;
+            if (!__any_sync(FULL, ((u[r] | u[r + 1]) >> 16) != 0u)) {
+                const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
+                const unsigned m = __ballot_sync(FULL, t != 0u);
+                npA = 32 - __clz(m & 0xffffu);
+                npB = 32 - __clz(m >> 16);
+                if (k < (hi ? npB : npA)) *(uint32_t*)(seg + lo + (hi ? 4 * npA : 0) + 4 * k) = t;
+            } else {
+                const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
+                npA = 32 - __clz(__ballot_sync(FULL, ta != 0u));
+                npB = 32 - __clz(__ballot_sync(FULL, tb != 0u));
+                if (lane < npA) ((uint32_t*)(seg + lo))[lane] = ta;
+                if (lane < npB) ((uint32_t*)(seg + lo + 4 * npA))[lane] = tb;
+            }
+            if (lane == 0) {
+                wb[r] = width_byte(npA);
+                wb[r + 1] = width_byte(npB);
+            }
+            lo += 4 * (npA + npB);
+        } else if (L == 16) {
+            int npA, npB, npC, npD;
+            if (!__any_sync(FULL, ((u[r] | u[r + 1]) >> 16) != 0u)) {
+                const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
+                const unsigned m0 = __ballot_sync(FULL, (t & 0xffffu) != 0u);
+                const unsigned m1 = __ballot_sync(FULL, (t >> 16) != 0u);
+                npA = 32 - __clz(m0 & 0xffffu);
+                npB = 32 - __clz(m1 & 0xffffu);
+                npC = 32 - __clz(m0 >> 16);
+                npD = 32 - __clz(m1 >> 16);
+                const int oA = lo, oB = oA + 2 * npA, oC = oB + 2 * npB, oD = oC + 2 * npC;
+                const int npL = hi ? npC : npA, npH = hi ? npD : npB;
+                const int offL = hi ? oC : oA, offH = hi ? oD : oB;
+                if (k < npL) *(uint16_t*)(seg + offL + 2 * k) = (uint16_t)(t & 0xffffu);
+                if (k < npH) *(uint16_t*)(seg + offH + 2 * k) = (uint16_t)(t >> 16);
+            } else {
+                const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
+                npA = 32 - __clz(__ballot_sync(FULL, (ta & 0xffffu) != 0u));
+                npB = 32 - __clz(__ballot_sync(FULL, (ta >> 16) != 0u));
+                npC = 32 - __clz(__ballot_sync(FULL, (tb & 0xffffu) != 0u));
+                npD = 32 - __clz(__ballot_sync(FULL, (tb >> 16) != 0u));
+                const int oA = lo, oB = oA + 2 * npA, oC = oB + 2 * npB, oD = oC + 2 * npC;
+                if (lane < npA) ((uint16_t*)(seg + oA))[lane] = (uint16_t)(ta & 0xffffu);
+                if (lane < npB) ((uint16_t*)(seg + oB))[lane] = (uint16_t)(ta >> 16);
+                if (lane < npC) ((uint16_t*)(seg + oC))[lane] = (uint16_t)(tb & 0xffffu);
+                if (lane < npD) ((uint16_t*)(seg + oD))[lane] = (uint16_t)(tb >> 16);
+            }
+            if (lane == 0) {
+                wb[2 * r] = width_byte(npA);
+                wb[2 * r + 1] = width_byte(npB);
+                wb[2 * r + 2] = width_byte(npC);
+                wb[2 * r + 3] = width_byte(npD);
+            }
+            lo += 2 * (npA + npB + npC + npD);
+        } else if (L == 64) {
+            int np;
+            if (!__any_sync(FULL, ((u[r] | u[r + 1]) >> 16) != 0u)) {
+                const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
+                const unsigned m = __ballot_sync(FULL, t != 0u);
+                np = 32 - __clz((m & 0xffffu) | (m >> 16));
+                if (k < np) *(uint32_t*)(seg + lo + 8 * k + (hi ? 4 : 0)) = t;
+            } else {
+                const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
+                np = 32 - __clz(__ballot_sync(FULL, (ta | tb) != 0u));
+                if (lane < np) ((uint2*)(seg + lo))[lane] = make_uint2(ta, tb);
+            }
+            if (lane == 0) wb[r / 2] = width_byte(np);
+            lo += 8 * np;
+        } else {
+            int np;
+            if (!__any_sync(FULL, ((u[r] | u[r + 1] | u[r + 2] | u[r + 3]) >> 16) != 0u)) {
+                const uint32_t t0 = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
+                const uint32_t t1 = tpose(__byte_perm(u[r + 2], u[r + 3], 0x5410), tc);
+                const unsigned m = __ballot_sync(FULL, (t0 | t1) != 0u);
+                np = 32 - __clz((m & 0xffffu) | (m >> 16));
+                if (k < np) {
+                    uint8_t* pp = seg + lo + 16 * k + (hi ? 4 : 0);
+                    *(uint32_t*)pp = t0;
+                    *(uint32_t*)(pp + 8) = t1;
+                }
+            } else {
+                const uint32_t t0 = tpose(u[r], tc), t1 = tpose(u[r + 1], tc);
+                const uint32_t t2 = tpose(u[r + 2], tc), t3 = tpose(u[r + 3], tc);
+                np = 32 - __clz(__ballot_sync(FULL, (t0 | t1 | t2 | t3) != 0u));
+                if (lane < np) ((uint4*)(seg + lo))[lane] = make_uint4(t0, t1, t2, t3);
+            }
+            if (lane == 0) wb[r / 4] = width_byte(np);
+            lo += 16 * np;
+        }
+    }
+    return lo;
+}
+
+// Copies `len` bytes (a multiple of UNIT, both ends UNIT-aligned) from shared
+// to global memory with one warp.
+template <int UNIT>
+__device__ __forceinline__ void warp_copy(uint8_t* dst, const uint8_t* src, int len)
+{
+    const int lane = threadIdx.x & 31;
+    if (UNIT == 16) {
+        for (int i = lane; i < len / 16; i += 32) ((uint4*)dst)[i] = ((const uint4*)src)[i];
+    } else if (UNIT == 8) {
+        for (int i = lane; i < len / 8; i += 32) ((uint2*)dst)[i] = ((const uint2*)src)[i];
+    } else if (UNIT == 4) {
+        for (int i = lane; i < len / 4; i += 32) ((uint32_t*)dst)[i] = ((const uint32_t*)src)[i];
+    } else {
+        for (int i = lane; i < len / 2; i += 32) ((uint16_t*)dst)[i] = ((const uint16_t*)src)[i];
+    }
+}
+
+// One encoder tile: NWARPS warp units of U rows, each warp encoding its unit
+// into its own shared-memory segment.  HAS_CIN: decode `it.cin` first (same
+// block size, unit offsets from k_wscan) and add the local chunk.  The FP32
+// sum goes to `it.raw_out` when that is set.  Null pointers switch a step off.
+template <int LOG2L, int U, bool HAS_CIN, typename TX>
+__device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, unsigned item_idx,
+                                            unsigned tile_in_item, unsigned g, Smem& sm,
+                                            uint8_t* dsm)
+{
+    constexpr int L = 1 << LOG2L;
+    constexpr int PB = L / 8;
+    constexpr int BU = U * 32 / L;  // blocks per warp unit
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     Ctl* ctl = P.ctl;
     const unsigned E = sm.E;
     const unsigned long long n = it.n;
-    const unsigned long long e0 = (unsigned long long)tile_in_item * (NTHREADS * R);
-    const unsigned long long row0 = e0 + (unsigned long long)warp * R * 32;
+    const unsigned long long te0 = (unsigned long long)tile_in_item * (NWARPS * U * 32);
+    const unsigned long long ue0 = te0 + (unsigned long long)warp * U * 32;
     const unsigned long long nb = (n + L - 1) >> LOG2L;
     const unsigned long long wbytes = ceil16(nb);
     const bool first = tile_in_item == 0;
     const bool last = tile_in_item + 1 == it.ntiles;
-    const unsigned long long wb0 = (row0 >> LOG2L);  // first block of this warp (L>=32)
-    const unsigned long long wblk0 = L >= 32 ? wb0 : (row0 >> 4);
     const bool do_cin = HAS_CIN && it.cin != nullptr;
-    const bool do_x = HAS_X && it.x != nullptr;
-    const bool do_enc = ENCODE && it.out != nullptr;
+    const bool do_enc = it.out != nullptr;
+    uint8_t* const seg = dsm + warp * seg_bytes(U);                   // this warp's payload
+    uint8_t* const wb = dsm + NWARPS * seg_bytes(U) + warp * (U * 2);  // its width bytes
+    __shared__ int segsz[NWARPS];
 
-    // ---- 1. raw loads issued first (they overlap the input look-back) -----
-    float xv[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const unsigned long long e = row0 + r * 32 + lane;
-        xv[r] = (do_x && e < n) ? load_x<TX>(it.x, e) : 0.0f;
-    }
-
-    // ---- 2. input stream: header, widths, look-back ------------------------
     float two_eb_in = 0.0f;
-    int np_in = 0, off_in = 0;   // lane i: planes and warp-local offset of block i
-    if (tid == 0) {
-        sm.abort_in = 0;
-        sm.abort_out = 0;
-    }
     if (do_cin) {
-        float eb_in = 0.0f;
-        const int lg = check_header(it, ctl, item_idx, LOG2L, eb_in, tid == 0 && tile_in_item == 0);
-        if (lg != LOG2L) {
-            if (tid == 0) sm.abort_in = 1;
-        } else {
-            two_eb_in = __fadd_rn(eb_in, eb_in);
-            int w = 0;
-            if (lane < BW) {
-                const unsigned long long gb = wblk0 + lane;
-                if (gb < nb) w = __ldg(it.cin + 32 + gb);
-                if (w > ZC_MAX_WIDTH) {
-                    fail(ctl, ZC_ERR_FORMAT, gb);
-                    w = 0;
-                }
-            }
-            np_in = w ? w + 1 : 0;
-            int tot;
-            off_in = warp_excl_scan(np_in * PB, lane, tot);
-            if (lane == 0) sm.warp_tot[warp] = (unsigned long long)tot;
-        }
-    }
-    __syncthreads();
-    if (do_cin && !sm.abort_in) {
-        if (warp == 0) {
-            unsigned long long agg = first ? 32ull + wbytes : 0ull;
-#pragma unroll
-            for (int w = 0; w < NWARPS; ++w) agg += sm.warp_tot[w];
-            bool to = false;
-            const unsigned long long ex =
-                lookback(P.chA, g, g - tile_in_item, agg, false, E, P.wc, ctl, &to);
-            if (lane == 0) {
-                sm.base_in = ex + (first ? 32ull + wbytes : 0ull);
-                if (to) sm.abort_in = 1;
-                if (last && !to && ex + agg != 32ull + wbytes + __ldg((const unsigned long long*)it.cin + 3))
-                    fail(ctl, ZC_ERR_FORMAT, item_idx);
-            }
+        if (tid == 0) {
+            float eb_in;
+            const int lg = check_header(it, ctl, item_idx, LOG2L, eb_in, tile_in_item == 0);
+            sm.abort = lg != LOG2L;
+            sm.eb = eb_in;
         }
         __syncthreads();
+        if (sm.abort) return;
+        two_eb_in = __fadd_rn(sm.eb, sm.eb);
     }
-    const bool dec_ok = do_cin && !sm.abort_in;
-    unsigned long long wbase_in = 0;
-    if (dec_ok) {
-        wbase_in = sm.base_in;
-        for (int w = 0; w < warp; ++w) wbase_in += sm.warp_tot[w];
-    }
-    __syncthreads();  // warp_tot is reused by the encoder
-
-    // ---- 3. decode words -> values, add, (raw store) ------------------------
-    float acc[R];
-    if (dec_ok) {
-        uint32_t wd[R];
-        // loads: lane k < planes reads plane k of the block
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (L == 16) {
-                const int bA = 2 * r, bB = 2 * r + 1;
-                const int npA = __shfl_sync(FULL, np_in, bA), npB = __shfl_sync(FULL, np_in, bB);
-                const unsigned long long pA = wbase_in + __shfl_sync(FULL, off_in, bA);
-                const unsigned long long pB = wbase_in + __shfl_sync(FULL, off_in, bB);
-                const bool okA = pA + npA * PB <= it.cin_cap, okB = pB + npB * PB <= it.cin_cap;
-                if ((!okA || !okB) && lane == 0) fail(ctl, ZC_ERR_FORMAT, g);
-                uint32_t lo = (okA && lane < npA) ? __ldg((const unsigned short*)(it.cin + pA) + lane) : 0u;
-                uint32_t hi = (okB && lane < npB) ? __ldg((const unsigned short*)(it.cin + pB) + lane) : 0u;
-                wd[r] = lo | (hi << 16);
-            } else if (L == 32) {
-                const int np = __shfl_sync(FULL, np_in, r);
-                const unsigned long long p = wbase_in + __shfl_sync(FULL, off_in, r);
-                const bool ok = p + np * PB <= it.cin_cap;
-                if (!ok && lane == 0) fail(ctl, ZC_ERR_FORMAT, g);
-                wd[r] = (ok && lane < np) ? __ldg((const unsigned*)(it.cin + p) + lane) : 0u;
-            } else if (L == 64) {
-                if ((r & 1) == 0) {
-                    const int b = r >> 1;
-                    const int np = __shfl_sync(FULL, np_in, b);
-                    const unsigned long long p = wbase_in + __shfl_sync(FULL, off_in, b);
-                    const bool ok = p + np * PB <= it.cin_cap;
-                    if (!ok && lane == 0) fail(ctl, ZC_ERR_FORMAT, g);
-                    uint2 v = make_uint2(0u, 0u);
-                    if (ok && lane < np) v = __ldg((const uint2*)(it.cin + p) + lane);
-                    wd[r] = v.x;
-                    if (r + 1 < R) wd[r + 1] = v.y;
-                }
-            } else {
-                if ((r & 3) == 0) {
-                    const int b = r >> 2;
-                    const int np = __shfl_sync(FULL, np_in, b);
-                    const unsigned long long p = wbase_in + __shfl_sync(FULL, off_in, b);
-                    const bool ok = p + np * PB <= it.cin_cap;
-                    if (!ok && lane == 0) fail(ctl, ZC_ERR_FORMAT, g);
-                    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                    if (ok && lane < np) v = __ldg((const uint4*)(it.cin + p) + lane);
-                    wd[r] = v.x;
-                    if (r + 1 < R) wd[r + 1] = v.y;
-                    if (r + 2 < R) wd[r + 2] = v.z;
-                    if (r + 3 < R) wd[r + 3] = v.w;
-                }
-            }
-        }
-        int carry = 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint32_t u = transpose32(wd[r], lane);
-            const int mag = (int)(u >> 1);
-            int v = (u & 1u) ? -mag : mag;
-            constexpr int W = L == 16 ? 16 : 32;
-#pragma unroll
-            for (int off = 1; off < W; off <<= 1) {
-                const int o = __shfl_up_sync(FULL, v, off, W);
-                if ((lane & (W - 1)) >= off) v += o;
-            }
-            if (L >= 64 && (r % RPB) != 0) v += carry;
-            if (L >= 64) carry = __shfl_sync(FULL, v, 31);
-            const float xh = __fmul_rn(__int2float_rn(v), two_eb_in);
-            acc[r] = do_x ? __fadd_rn(xh, xv[r]) : xh;
-        }
-    } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = xv[r];
-    }
-    if (it.raw_out != nullptr && !(do_cin && !dec_ok)) {
-        const bool check = do_cin && do_x && !do_enc;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const unsigned long long e = row0 + r * 32 + lane;
-            if (e < n) {
-                store_raw(it.raw_out, it.out_dtype, e, acc[r]);
-                if (check && !isfinite(acc[r])) fail(ctl, ZC_ERR_NONFINITE, e);
-            }
-        }
-    }
-    if (!do_enc) return;
-    if (do_cin && !dec_ok) return;
-
-    // ---- 4. encode: quantize, Lorenzo, transpose, sizes ----------------------
     float eb = it.eb, two_eb = it.two_eb, inv = it.inv;
     if (P.eb_from_ctl) {
-        eb = sm.eb;
-        two_eb = sm.two_eb;
-        inv = sm.inv;
+        eb = ctl->eb;
+        two_eb = ctl->two_eb;
+        inv = ctl->inv;
     }
-    uint32_t tw[R];
-    int np_out = 0;  // lane i: planes of warp block i
+
+    // ---- 1. this warp's unit: decode / add / raw store / encode ----------------
+    const TpC tc = tp_consts(lane);
+    int err = 0;
+    int lo = 0;
+    if (ue0 < n) {
+        const uint8_t* src = nullptr;
+        int2* meta = nullptr;
+        if constexpr (HAS_CIN) {
+            __shared__ __align__(16) int2 meta_all[NWARPS][BU];
+            meta = meta_all[warp];
+            if (do_cin) src = it.cin + unit_meta<LOG2L, U>(P, it, g * NWARPS + warp, ue0, meta);
+        }
+#pragma unroll 1
+        for (int gi = 0; gi < U / GR; ++gi) {
+            const unsigned long long e0 = ue0 + (unsigned long long)gi * GR * 32;
+            if (e0 >= n) break;
+            const int nrem = (int)min(n - e0, (unsigned long long)(GR * 32));
+            float acc[GR];
+            if (it.x != nullptr) {
+                const TX* xp = (const TX*)it.x + e0 + lane;
+#pragma unroll
+                for (int r = 0; r < GR; ++r)
+                    acc[r] = r * 32 + lane < nrem ? load_x<TX>(xp, r * 32) : 0.0f;
+            } else {
+#pragma unroll
+                for (int r = 0; r < GR; ++r) acc[r] = 0.0f;
+            }
+            if constexpr (HAS_CIN) {
+                if (do_cin) {
+                    float dv[GR];
+                    decode_group<LOG2L>(src, meta, gi, two_eb_in, dv, tc);
+#pragma unroll
+                    for (int r = 0; r < GR; ++r) acc[r] = __fadd_rn(dv[r], acc[r]);
+                }
+            }
+            if (it.raw_out != nullptr) {
+                float* op = (float*)it.raw_out + e0 + lane;
+                const bool check = do_cin && !do_enc;
+#pragma unroll
+                for (int r = 0; r < GR; ++r) {
+                    if (r * 32 + lane < nrem) {
+                        op[r * 32] = acc[r];
+                        if (check && !isfinite(acc[r])) err |= ZC_ERR_NONFINITE;
+                    }
+                }
+            }
+            if (do_enc) {
+                const int b0 = L >= 32 ? gi * GR / (L / 32) : gi * GR * 2;
+                lo = encode_group<LOG2L>(acc, nrem, eb, two_eb, inv, seg, lo, wb + b0, err, tc);
+            }
+        }
+    }
     {
-        int carry = 0;
-        uint32_t orw = 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const unsigned long long e = row0 + r * 32 + lane;
-            const bool valid = e < n;
-            int q = 0;
-            const int err = valid ? quantize(acc[r], eb, two_eb, inv, q) : 0;
-            const unsigned bad = __ballot_sync(FULL, err != 0);
-            if (bad && lane == __ffs(bad) - 1) fail(ctl, (unsigned)err, e);
-            int prev = __shfl_up_sync(FULL, q, 1);
-            if (L == 16) {
-                if ((lane & 15) == 0) prev = 0;
-            } else if (lane == 0) {
-                prev = (L >= 64 && (r % RPB) != 0) ? carry : 0;
-            }
-            if (L >= 64) carry = __shfl_sync(FULL, q, 31);
-            const int d = valid ? q - prev : 0;
-            const uint32_t ad = (uint32_t)(d < 0 ? -d : d);
-            const uint32_t u = __funnelshift_l((uint32_t)d, ad, 1);  // |d| << 1 | sign
-            const uint32_t t = transpose32(u, lane);
-            tw[r] = t;
-            if (L == 16) {
-                const unsigned mA = __ballot_sync(FULL, (t & 0xffffu) != 0u);
-                const unsigned mB = __ballot_sync(FULL, (t >> 16) != 0u);
-                if (lane == 2 * r) np_out = 32 - __clz(mA);
-                if (lane == 2 * r + 1) np_out = 32 - __clz(mB);
-            } else {
-                orw |= t;
-                if ((r % RPB) == RPB - 1) {
-                    const unsigned m = __ballot_sync(FULL, orw != 0u);
-                    if (lane == r / RPB) np_out = 32 - __clz(m);
-                    orw = 0;
-                }
-            }
-        }
+        const unsigned bad = __ballot_sync(FULL, err != 0);
+        if (bad && lane == __ffs(bad) - 1) fail(ctl, (unsigned)err, ue0);
     }
-    int tot_out;
-    const int off_out = warp_excl_scan(np_out * PB, lane, tot_out);
-    if (lane == 0) sm.warp_tot[warp] = (unsigned long long)tot_out;
+    if (!do_enc) return;
+    if (lane == 0) segsz[warp] = lo;
     __syncthreads();
 
-    // ---- 5. output position: look-back, stream start (packed mode) ----------
-    if (warp == 0) {
-        unsigned long long agg = first ? 32ull + wbytes : 0ull;
+    // ---- 2. segment offsets, tile position (look-back), stream start ---------
+    int segoff = 0, payload_i = 0;
 #pragma unroll
-        for (int w = 0; w < NWARPS; ++w) agg += sm.warp_tot[w];
-        const unsigned g0 = P.packed ? 0u : g - tile_in_item;
-        bool to = false;
-        const unsigned long long ex = lookback(P.chB, g, g0, agg, last, E, P.wc, ctl, &to);
-        unsigned long long start = 0ull;
-        if (P.packed && !to) {
-            if (first) {
-                start = ex;
-                if (lane == 0) {
-                    st_relaxed(P.seg_off + item_idx, ex);
-                    st_release(P.seg_flag + item_idx, ((unsigned long long)E << 32) | 1ull);
-                }
-            } else {
-                bool okw = true;
-                if (lane == 0) okw = wait_flag(P.seg_flag + item_idx, E, P.wc.limit_ns);
-                okw = __shfl_sync(FULL, (int)okw, 0) != 0;
-                if (!okw) {
-                    to = true;
-                    if (lane == 0) fail(ctl, ZC_ERR_TIMEOUT, g);
-                } else {
-                    start = ld_relaxed(P.seg_off + item_idx);
-                }
-            }
-        }
-        if (lane == 0) {
-            sm.base_out = ex + (first ? 32ull + wbytes : 0ull);
-            sm.stream_start = start;
-            sm.abort_out = to ? 1 : 0;
-            if (last && !to) {
-                const unsigned long long end = ex + agg;  // unpadded end of payload
-                const unsigned long long total = ceil16(end);
-                if (it.out_bytes) *it.out_bytes = total - start;
-                if (P.packed) {
-                    P.seg_off[item_idx + 1] = total;
-                }
-                sm.end = end;  // handed to the header writer below
-            }
-        }
+    for (int w = 0; w < NWARPS; ++w) {
+        if (w < warp) segoff += segsz[w];
+        payload_i += segsz[w];
     }
-    __syncthreads();
-    if (sm.abort_out) return;
-    const unsigned long long start = sm.stream_start;
-    unsigned long long wbase = sm.base_out;
-    for (int w = 0; w < warp; ++w) wbase += sm.warp_tot[w];
-    const unsigned long long cap = it.out_cap;
-    uint8_t* const out = it.out;
-
-    // ---- 6. stores: payload words, width bytes, header and padding ----------
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        if (L == 16) {
-            const int bA = 2 * r, bB = 2 * r + 1;
-            const int npA = __shfl_sync(FULL, np_out, bA), npB = __shfl_sync(FULL, np_out, bB);
-            const unsigned long long pA = wbase + __shfl_sync(FULL, off_out, bA);
-            const unsigned long long pB = wbase + __shfl_sync(FULL, off_out, bB);
-            const bool okA = pA + npA * PB <= cap, okB = pB + npB * PB <= cap;
-            if ((!okA || !okB) && lane == 0) fail(ctl, ZC_ERR_CAPACITY, g);
-            if (okA && lane < npA) ((uint16_t*)(out + pA))[lane] = (uint16_t)(tw[r] & 0xffffu);
-            if (okB && lane < npB) ((uint16_t*)(out + pB))[lane] = (uint16_t)(tw[r] >> 16);
-        } else if (L == 32) {
-            const int np = __shfl_sync(FULL, np_out, r);
-            const unsigned long long p = wbase + __shfl_sync(FULL, off_out, r);
-            const bool ok = p + np * PB <= cap;
-            if (!ok && lane == 0) fail(ctl, ZC_ERR_CAPACITY, g);
-            if (ok && lane < np) ((uint32_t*)(out + p))[lane] = tw[r];
-        } else if (L == 64) {
-            if ((r & 1) == 0) {
-                const int b = r >> 1;
-                const int np = __shfl_sync(FULL, np_out, b);
-                const unsigned long long p = wbase + __shfl_sync(FULL, off_out, b);
-                const bool ok = p + np * PB <= cap;
-                if (!ok && lane == 0) fail(ctl, ZC_ERR_CAPACITY, g);
-                if (ok && lane < np) ((uint2*)(out + p))[lane] = make_uint2(tw[r], tw[r + 1]);
+    const unsigned long long payload = (unsigned long long)payload_i;
+    const unsigned long long agg = payload + (first ? 32ull + wbytes : 0ull);
+    const unsigned g0 = P.packed ? 0u : g - tile_in_item;
+    bool to = false;
+    const unsigned long long ex = lookback_cta(P.chB, g, g0, agg, last, E, P.wc, ctl, to, sm.lb);
+    unsigned long long start = 0ull;
+    if (P.packed && !to) {
+        if (first) {
+            start = ex;
+            if (tid == 0) {
+                st_relaxed(P.seg_off + item_idx, ex);
+                st_release(P.seg_flag + item_idx, ((unsigned long long)E << 32) | 1ull);
             }
         } else {
-            if ((r & 3) == 0) {
-                const int b = r >> 2;
-                const int np = __shfl_sync(FULL, np_out, b);
-                const unsigned long long p = wbase + __shfl_sync(FULL, off_out, b);
-                const bool ok = p + np * PB <= cap;
-                if (!ok && lane == 0) fail(ctl, ZC_ERR_CAPACITY, g);
-                if (ok && lane < np)
-                    ((uint4*)(out + p))[lane] = make_uint4(tw[r], tw[r + 1], tw[r + 2], tw[r + 3]);
+            if (tid == 0) {
+                sm.abort = !wait_flag(P.seg_flag + item_idx, E, P.wc.limit_ns);
+                if (sm.abort) fail(ctl, ZC_ERR_TIMEOUT, g);
+                else sm.start = ld_relaxed(P.seg_off + item_idx);
             }
+            __syncthreads();
+            if (sm.abort) to = true;
+            else start = sm.start;
         }
     }
-    // width bytes of this warp's blocks
-    if (lane < BW) {
-        const unsigned long long gb = wblk0 + lane;
-        const unsigned long long pos = start + 32 + gb;
-        if (gb < nb && pos < cap) out[pos] = (uint8_t)(np_out ? np_out - 1 : 0);
+    if (to) return;
+    const unsigned long long base = ex + (first ? 32ull + wbytes : 0ull);
+    const unsigned long long cap = it.out_cap;
+    uint8_t* const out = it.out;
+    const unsigned long long end = ex + agg;  // unpadded end of this tile's payload
+
+    // ---- 3. stores: each warp copies its segment and its width bytes -------------
+    if (base + payload <= cap) {
+        warp_copy<PB>(out + base + segoff, seg, lo);
+    } else if (tid == 0) {
+        fail(ctl, ZC_ERR_CAPACITY, g);
+    }
+    {
+        const unsigned long long b0 = ue0 >> LOG2L;
+        for (int i = lane; i < BU; i += 32) {
+            const unsigned long long b = b0 + i;
+            const unsigned long long pos = start + 32 + b;
+            if (b < nb && pos < cap) out[pos] = wb[i];
+        }
     }
     if (last) {
-        const unsigned long long end = sm.end;
-        const unsigned long long payload = end - start - 32 - wbytes;
-        // zero padding after the width bytes and after the payload
+        const unsigned long long total = ceil16(end);
+        const unsigned long long pl = end - start - 32 - wbytes;
         for (unsigned long long p = start + 32 + nb + tid; p < start + 32 + wbytes; p += NTHREADS)
             if (p < cap) out[p] = 0;
-        for (unsigned long long p = end + tid; p < ceil16(end); p += NTHREADS)
+        for (unsigned long long p = end + tid; p < total; p += NTHREADS)
             if (p < cap) out[p] = 0;
         if (tid < 8 && start + 32 <= cap) {
             uint32_t v = 0;
@@ -473,16 +706,20 @@ __device__ __forceinline__ void tile_codec(const Launch& P, const Item& it, unsi
             case 3: v = (uint32_t)(n >> 32); break;
             case 4: v = __float_as_uint(eb); break;
             case 5: v = (uint32_t)nb; break;
-            case 6: v = (uint32_t)payload; break;
-            default: v = (uint32_t)(payload >> 32); break;
+            case 6: v = (uint32_t)pl; break;
+            default: v = (uint32_t)(pl >> 32); break;
             }
             ((uint32_t*)(out + start))[tid] = v;
+        }
+        if (tid == 0) {
+            if (it.out_bytes) *it.out_bytes = total - start;
+            if (P.packed) P.seg_off[item_idx + 1] = total;
         }
     }
 }
 
-// Where a launch's items come from: the single item in the parameters, or a
-// device array of items sorted by first tile.
+// ---- item sources ------------------------------------------------------------
+
 struct ItemsSrc {
     const Launch& P;
     __device__ unsigned find(unsigned g) const
@@ -533,32 +770,28 @@ struct ScatterSrc {
     }
 };
 
-// Persistent tile loop shared by every codec kernel: CTAs take tiles in ticket
-// order (so a tile only ever waits for tiles taken earlier, by CTAs that are
-// running or done), the last CTA to finish advances the launch generation.
+// Tile loop of the encoders: CTAs take tiles in ticket order, so a tile only
+// ever waits for tiles taken earlier by CTAs that are running or done; the
+// last CTA to finish advances the launch generation.
 template <typename Src, typename Body>
 __device__ __forceinline__ void tile_loop(const Launch& P, const Src& src, Smem& sm, Body body)
 {
     if (threadIdx.x == 0) {
         sm.E = ld_volatile_u32(&P.ctl->epoch) + 1u;
-        sm.abort_in = ld_volatile_u32(&P.ctl->magic) != WS_MAGIC;
-        if (sm.abort_in) fail(P.ctl, ZC_ERR_WORKSPACE, 0);
-        if (P.eb_from_ctl) {
-            sm.eb = P.ctl->eb;
-            sm.two_eb = P.ctl->two_eb;
-            sm.inv = P.ctl->inv;
-            if (ld_volatile_u32(&P.ctl->eb_ok) != 1u) sm.abort_in = 2;
-        }
+        sm.abort = ld_volatile_u32(&P.ctl->magic) != WS_MAGIC;
+        if (sm.abort) fail(P.ctl, ZC_ERR_WORKSPACE, 0);
+        else if (P.eb_from_ctl && ld_volatile_u32(&P.ctl->eb_ok) != 1u) sm.abort = 2;
     }
     __syncthreads();
-    if (sm.abort_in == 1) return;        // uninitialised workspace: touch nothing
-    const bool no_eb = sm.abort_in == 2;  // the range kernel reported an error
+    if (sm.abort == 1) return;  // uninitialised workspace: touch nothing
+    const bool no_eb = sm.abort == 2;
     const unsigned modulus = P.total_tiles + gridDim.x - 1u;
     while (true) {
         __syncthreads();
         if (threadIdx.x == 0) {
             sm.ticket = atomicInc(&P.ctl->ticket, modulus);
             sm.item = sm.ticket < P.total_tiles ? src.find(sm.ticket) : 0u;
+            sm.abort = 0;
         }
         __syncthreads();
         const unsigned g = sm.ticket;
@@ -577,44 +810,154 @@ __device__ __forceinline__ void tile_loop(const Launch& P, const Src& src, Smem&
     }
 }
 
-// Compress raw input of type TX (one or several items; packed or not).
-template <int LOG2L, int R, typename TX>
-__global__ void __launch_bounds__(NTHREADS) k_compress(const Launch P)
+template <int LOG2L, int U, typename TX>
+__global__ void __launch_bounds__(NTHREADS, 4) k_compress(const Launch P)
 {
     __shared__ Smem sm;
+    extern __shared__ __align__(16) uint8_t dsm[];
     tile_loop(P, ItemsSrc{P}, sm, [&](const Item& it, unsigned idx, unsigned t, unsigned g) {
-        tile_codec<LOG2L, R, false, true, true, TX>(P, it, idx, t, g, sm);
+        tile_encode<LOG2L, U, false, TX>(P, it, idx, t, g, sm, dsm);
     });
 }
 
-// Scatter pack: every segment a stream of its own, packed back to back.
-template <int LOG2L, int R, typename TX>
-__global__ void __launch_bounds__(NTHREADS) k_scatter(const Launch P, const ScatterParams S)
+template <int LOG2L, int U, typename TX>
+__global__ void __launch_bounds__(NTHREADS, 4) k_scatter(const Launch P, const ScatterParams SP)
 {
     __shared__ Smem sm;
-    tile_loop(P, ScatterSrc{P, S}, sm, [&](const Item& it, unsigned idx, unsigned t, unsigned g) {
-        tile_codec<LOG2L, R, false, true, true, TX>(P, it, idx, t, g, sm);
+    extern __shared__ __align__(16) uint8_t dsm[];
+    tile_loop(P, ScatterSrc{P, SP}, sm, [&](const Item& it, unsigned idx, unsigned t, unsigned g) {
+        tile_encode<LOG2L, U, false, TX>(P, it, idx, t, g, sm, dsm);
     });
 }
 
-// Ring step: decode the received stream, add the local FP32 chunk, re-encode.
-template <int LOG2L, int R>
-__global__ void __launch_bounds__(NTHREADS) k_reduce(const Launch P)
+template <int LOG2L, int U>
+__global__ void __launch_bounds__(NTHREADS, 4) k_reduce(const Launch P)
 {
     __shared__ Smem sm;
+    extern __shared__ __align__(16) uint8_t dsm[];
     tile_loop(P, ItemsSrc{P}, sm, [&](const Item& it, unsigned idx, unsigned t, unsigned g) {
-        tile_codec<LOG2L, R, true, true, true, float>(P, it, idx, t, g, sm);
+        tile_encode<LOG2L, U, true, float>(P, it, idx, t, g, sm, dsm);
     });
 }
 
-// Raw streams: copy (and convert) the elements of this tile.
-template <int R>
-__device__ __forceinline__ void tile_raw_copy(const Item& it, int src_dtype, unsigned tile_in_item)
+#ifdef ZC_DECODE_KERNELS  // defined by the one translation unit that launches them
+
+// ---- width scan: payload offset of every decode tile --------------------------
+// One CTA per chunk of WSCAN warp units of one item; thread i sums the plane
+// bytes of unit i from its width bytes; a CTA scan and a look-back over the
+// item's chunks give every unit's payload offset (global decode slot = item
+// tile slot * NWARPS + unit in tile).
+__global__ void __launch_bounds__(NTHREADS) k_wscan(const Launch P)
 {
-    const unsigned long long e0 = (unsigned long long)tile_in_item * (NTHREADS * R);
+    __shared__ Smem sm;
+    __shared__ int wsum[NWARPS];
+    if (threadIdx.x == 0) {
+        sm.E = ld_volatile_u32(&P.ctl->epoch) + 1u;
+        sm.abort = ld_volatile_u32(&P.ctl->magic) != WS_MAGIC;
+        if (sm.abort) fail(P.ctl, ZC_ERR_WORKSPACE, 0);
+    }
+    __syncthreads();
+    if (sm.abort) return;
+    const unsigned modulus = P.total_tiles + gridDim.x - 1u;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    while (true) {
+        __syncthreads();
+        if (tid == 0) {
+            sm.ticket = atomicInc(&P.ctl->ticket, modulus);
+            unsigned it = 0;
+            if (P.items != nullptr && sm.ticket < P.total_tiles) {
+                unsigned lo = 0, hi = P.n_items;
+                while (hi - lo > 1) {
+                    const unsigned mid = (lo + hi) >> 1;
+                    if (P.items[mid].chunk_begin <= sm.ticket) lo = mid;
+                    else hi = mid;
+                }
+                it = lo;
+            }
+            sm.item = it;
+        }
+        __syncthreads();
+        const unsigned c = sm.ticket;
+        if (c >= P.total_tiles) break;
+        const Item it = P.items != nullptr ? P.items[sm.item] : P.one;
+        if (it.cin == nullptr) continue;  // nothing received: no offsets needed
+        const unsigned chunk = c - it.chunk_begin;
+        float eb_in;
+        const int lg = check_header(it, P.ctl, sm.item, -1, eb_in, false);
+        if (lg < 4) continue;  // raw or malformed: the decoder reports it
+        const unsigned long long L = 1ull << lg;
+        const unsigned long long nb = (it.n + L - 1) >> lg;
+        const int PB = (int)(L / 8);
+        const unsigned long long ntile = (unsigned long long)it.ntiles * NWARPS;  // units
+        const unsigned long long k = (unsigned long long)chunk * WSCAN + tid;    // unit in item
+        const int bpt = (P.urows * 32) >> lg;                                    // blocks per unit
+        int sum = 0;
+        if (k < ntile) {
+            const unsigned long long b0 = k * bpt;
+            const uint8_t* w = it.cin + 32;
+            // bpt is 8 (32-row units at L = 128) or a multiple of 16
+            const int step = bpt < 16 ? 8 : 16;
+            for (int i = 0; i < bpt; i += step) {
+                if (b0 + i >= ceil16(nb)) break;
+                unsigned ws[4] = {0u, 0u, 0u, 0u};
+                if (step == 16) {
+                    const uint4 v = __ldg((const uint4*)(w + b0 + i));
+                    ws[0] = v.x;
+                    ws[1] = v.y;
+                    ws[2] = v.z;
+                    ws[3] = v.w;
+                } else {
+                    const uint2 v = __ldg((const uint2*)(w + b0 + i));
+                    ws[0] = v.x;
+                    ws[1] = v.y;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int wv = (ws[q] >> (8 * b)) & 0xff;
+                        if (wv > ZC_MAX_WIDTH) fail(P.ctl, ZC_ERR_FORMAT, b0 + i + 4 * q + b);
+                        else sum += planes_of(wv) * PB;
+                    }
+            }
+        }
+        int tot;
+        const int ex = warp_excl_scan(sum, lane, tot);
+        if (lane == 0) wsum[warp] = tot;
+        __syncthreads();
+        unsigned long long wbase = 0, cagg = 0;
+        for (int w = 0; w < NWARPS; ++w) {
+            if (w < warp) wbase += wsum[w];
+            cagg += wsum[w];
+        }
+        bool to = false;
+        const unsigned long long cex =
+            lookback_cta(P.chC, c, it.chunk_begin, cagg, false, sm.E, P.wc, P.ctl, to, sm.lb);
+        if (to) continue;
+        if (k < ntile) P.offs[(unsigned long long)it.tile_begin * NWARPS + k] = cex + wbase + ex;
+        if (chunk + 1 == it.nchunks && tid == 0) {
+            const unsigned long long payload = __ldg((const unsigned long long*)it.cin + 3);
+            if (cex + cagg != payload) fail(P.ctl, ZC_ERR_FORMAT, sm.item);
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicInc(&P.ctl->done, gridDim.x - 1u) == gridDim.x - 1u) {
+            P.ctl->epoch = sm.E;
+            __threadfence();
+        }
+    }
+}
+
+// ---- decompression -------------------------------------------------------------
+
+// Raw streams: copy (and convert) the elements of this warp unit.
+__device__ __forceinline__ void unit_raw_copy(const Item& it, int src_dtype, unsigned long long ue0)
+{
     const uint8_t* src = it.cin + 32;
-    for (int r = 0; r < R; ++r) {
-        const unsigned long long e = e0 + (unsigned long long)r * NTHREADS + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    for (int r = 0; r < DEC_U; ++r) {
+        const unsigned long long e = ue0 + (unsigned long long)r * 32 + lane;
         if (e < it.n) {
             const float v = src_dtype == ZC_F32 ? __ldg((const float*)src + e)
                                                 : bf16_to_f32(__ldg((const unsigned short*)src + e));
@@ -623,24 +966,85 @@ __device__ __forceinline__ void tile_raw_copy(const Item& it, int src_dtype, uns
     }
 }
 
-// Decompress: the block size comes from each stream's header.
-template <int R>
+template <int LOG2L, typename TO>
+__device__ __forceinline__ void unit_decode(const Launch& P, const Item& it, unsigned slot,
+                                            unsigned long long ue0, float two_eb, int2* meta)
+{
+    const int lane = threadIdx.x & 31;
+    const TpC tc = tp_consts(lane);
+    const uint8_t* src = it.cin + unit_meta<LOG2L, DEC_U>(P, it, slot, ue0, meta);
+#pragma unroll 1
+    for (int gi = 0; gi < DEC_U / GR; ++gi) {
+        const unsigned long long e0 = ue0 + (unsigned long long)gi * GR * 32;
+        if (e0 >= it.n) break;
+        const int nrem = (int)min(it.n - e0, (unsigned long long)(GR * 32));
+        float acc[GR];
+        decode_group<LOG2L>(src, meta, gi, two_eb, acc, tc);
+        TO* op = (TO*)it.raw_out + e0 + lane;
+        if (nrem == GR * 32) {
+#pragma unroll
+            for (int r = 0; r < GR; ++r) {
+                if (sizeof(TO) == 4) ((float*)op)[r * 32] = acc[r];
+                else ((uint16_t*)op)[r * 32] = f32_to_bf16(acc[r]);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < GR; ++r) {
+                if (r * 32 + lane < nrem) {
+                    if (sizeof(TO) == 4) ((float*)op)[r * 32] = acc[r];
+                    else ((uint16_t*)op)[r * 32] = f32_to_bf16(acc[r]);
+                }
+            }
+        }
+    }
+}
+
+// NWARPS warp units per CTA, one per warp, independent of each other; the
+// block size comes from the stream's header.
 __global__ void __launch_bounds__(NTHREADS) k_decompress(const Launch P)
 {
-    __shared__ Smem sm;
-    tile_loop(P, ItemsSrc{P}, sm, [&](const Item& it, unsigned idx, unsigned t, unsigned g) {
-        float eb_in;
-        const int lg = check_header(it, P.ctl, idx, -1, eb_in, threadIdx.x == 0 && t == 0);
+    __shared__ __align__(16) int2 meta[NWARPS][DEC_U * 2];
+    const unsigned tile = blockIdx.x;
+    unsigned idx = 0;
+    if (P.items != nullptr) {
+        unsigned lo = 0, hi = P.n_items;
+        while (hi - lo > 1) {
+            const unsigned mid = (lo + hi) >> 1;
+            if (P.items[mid].tile_begin <= tile) lo = mid;
+            else hi = mid;
+        }
+        idx = lo;
+    }
+    const Item it = P.items != nullptr ? P.items[idx] : P.one;
+    const unsigned t = tile - it.tile_begin;
+    const int warp = threadIdx.x >> 5;
+    const unsigned long long ue0 = ((unsigned long long)t * NWARPS + warp) * (DEC_U * 32);
+    const unsigned slot = tile * NWARPS + warp;
+    float eb_in;
+    const int lg = check_header(it, P.ctl, idx, -1, eb_in, threadIdx.x == 0 && t == 0);
+    if (ue0 >= it.n) return;
+    const float two = __fadd_rn(eb_in, eb_in);
+    if (it.out_dtype == ZC_F32) {
         switch (lg) {
-        case 4: tile_codec<4, R, true, false, false, float>(P, it, idx, t, g, sm); break;
-        case 5: tile_codec<5, R, true, false, false, float>(P, it, idx, t, g, sm); break;
-        case 6: tile_codec<6, R, true, false, false, float>(P, it, idx, t, g, sm); break;
-        case 7: tile_codec<7, R, true, false, false, float>(P, it, idx, t, g, sm); break;
-        case -2: tile_raw_copy<R>(it, ZC_F32, t); break;
-        case -3: tile_raw_copy<R>(it, ZC_BF16, t); break;
+        case 4: unit_decode<4, float>(P, it, slot, ue0, two, meta[warp]); return;
+        case 5: unit_decode<5, float>(P, it, slot, ue0, two, meta[warp]); return;
+        case 6: unit_decode<6, float>(P, it, slot, ue0, two, meta[warp]); return;
+        case 7: unit_decode<7, float>(P, it, slot, ue0, two, meta[warp]); return;
         default: break;
         }
-    });
+    } else {
+        switch (lg) {
+        case 4: unit_decode<4, uint16_t>(P, it, slot, ue0, two, meta[warp]); return;
+        case 5: unit_decode<5, uint16_t>(P, it, slot, ue0, two, meta[warp]); return;
+        case 6: unit_decode<6, uint16_t>(P, it, slot, ue0, two, meta[warp]); return;
+        case 7: unit_decode<7, uint16_t>(P, it, slot, ue0, two, meta[warp]); return;
+        default: break;
+        }
+    }
+    if (lg == -2) unit_raw_copy(it, ZC_F32, ue0);
+    else if (lg == -3) unit_raw_copy(it, ZC_BF16, ue0);
 }
+
+#endif  // ZC_DECODE_KERNELS
 
 }  // namespace zc

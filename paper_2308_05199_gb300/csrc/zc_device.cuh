@@ -22,7 +22,6 @@ constexpr unsigned WS_MAGIC = 0x5a435753u; // "ZCWS"
 constexpr int RANGE_SLOTS = 4096;          // partial min/max slots of the range kernel
 constexpr uint64_t WS_CTL_BYTES = 256;
 constexpr uint64_t WS_RANGE_BYTES = RANGE_SLOTS * 8;
-constexpr uint64_t WS_TILE_WORDS = 6;      // u64 words per tile: 2 look-back chains x 3
 constexpr int QMAX = 1 << 22;              // largest |q|
 
 // Workspace control block (first 256 bytes of the workspace).
@@ -93,26 +92,59 @@ __device__ __forceinline__ unsigned long long ceil16(unsigned long long v)
 
 // ---- warp bit-matrix transpose -----------------------------------------
 // Lane i holds word u_i; afterwards lane k holds the word whose bit i is bit k
-// of u_i.  Five butterfly stages; each exchanges the off-diagonal sub-blocks
-// of the current block size with one shuffle, one funnel rotate and one
-// bit-select.  The transpose is its own inverse.
-__device__ __forceinline__ uint32_t transpose32(uint32_t u, int lane)
+// of u_i.  Five butterfly stages exchange the off-diagonal sub-blocks of the
+// current block size through one shuffle each: the two byte-granular stages
+// (16- and 8-bit blocks) merge with one byte permute, the three sub-byte
+// stages with one funnel rotate and one bit-select.  The per-lane selectors,
+// rotate counts and masks are computed once per kernel (TpC).  The transpose
+// is its own inverse.  If every u_i < 2^16, packing two rows as
+// u_a | u_b << 16 transposes both at once: lanes 0..15 get the planes of a,
+// lanes 16..31 those of b.
+struct TpC {
+    uint32_t s16, s8, r4, r2, r1, k4, k2, k1;
+};
+__device__ __forceinline__ TpC tp_consts(int lane)
+{
+    TpC c;
+    c.s16 = (lane & 16) ? 0x3276u : 0x5410u;
+    c.s8 = (lane & 8) ? 0x3715u : 0x6240u;
+    c.r4 = (lane & 4) ? 28u : 4u;
+    c.k4 = (lane & 4) ? 0xf0f0f0f0u : 0x0f0f0f0fu;
+    c.r2 = (lane & 2) ? 30u : 2u;
+    c.k2 = (lane & 2) ? 0xccccccccu : 0x33333333u;
+    c.r1 = (lane & 1) ? 31u : 1u;
+    c.k1 = (lane & 1) ? 0xaaaaaaaau : 0x55555555u;
+    return c;
+}
+__device__ __forceinline__ uint32_t tpose(uint32_t u, const TpC& c)
+{
+    uint32_t p = __shfl_xor_sync(FULL, u, 16);
+    u = __byte_perm(u, p, c.s16);
+    p = __shfl_xor_sync(FULL, u, 8);
+    u = __byte_perm(u, p, c.s8);
+    p = __shfl_xor_sync(FULL, u, 4);
+    u = (u & c.k4) | (__funnelshift_l(p, p, c.r4) & ~c.k4);
+    p = __shfl_xor_sync(FULL, u, 2);
+    u = (u & c.k2) | (__funnelshift_l(p, p, c.r2) & ~c.k2);
+    p = __shfl_xor_sync(FULL, u, 1);
+    u = (u & c.k1) | (__funnelshift_l(p, p, c.r1) & ~c.k1);
+    return u;
+}
+
+// Inclusive prefix sum over segments of W lanes, using the in-range predicate
+// of shfl.up so each step is one shuffle and one predicated add.
+template <int W>
+__device__ __forceinline__ int scan_incl(int v)
 {
 #pragma unroll
-    for (int s = 0; s < 5; ++s) {
-        const int j = 16 >> s;
-        const uint32_t m = s == 0 ? 0x0000ffffu
-                         : s == 1 ? 0x00ff00ffu
-                         : s == 2 ? 0x0f0f0f0fu
-                         : s == 3 ? 0x33333333u
-                                  : 0x55555555u;
-        const bool lo = (lane & j) == 0;
-        const uint32_t p = __shfl_xor_sync(FULL, u, j);
-        const uint32_t sh = __funnelshift_l(p, p, lo ? j : 32 - j);
-        const uint32_t keep = lo ? m : ~m;
-        u = (u & keep) | (sh & ~keep);
+    for (int off = 1; off < W; off <<= 1) {
+        asm("{\n\t.reg .s32 t;\n\t.reg .pred p;\n\t"
+            "shfl.sync.up.b32 t|p, %0, %1, %2, -1;\n\t"
+            "@p add.s32 %0, %0, t;\n\t}"
+            : "+r"(v)
+            : "r"(off), "r"((32 - W) << 8));
     }
-    return u;
+    return v;
 }
 
 // ---- prequantization ------------------------------------------------------
@@ -226,35 +258,47 @@ struct WaitCfg {
     long long withhold;  // tile that never publishes (test hook), -1 = none
 };
 
-// Run by one full warp.  g: this tile's slot; g0: first slot of its chain
-// (whose exclusive value is 0).  Publishes g's aggregate, looks back, publishes
-// g's inclusive prefix, and returns g's exclusive value.  On a wait that runs
-// out, sets *timed_out and returns 0 (the tile then writes nothing).
-__device__ __forceinline__ unsigned long long lookback(const Chain& ch, unsigned g, unsigned g0,
-                                       unsigned long long agg, bool h, unsigned E,
-                                       const WaitCfg& wc, Ctl* ctl, bool* timed_out)
+// Scratch of the CTA-wide look-back.
+struct LbSmem {
+    Xf wx[NWARPS];
+    int wp[NWARPS];
+    unsigned long long pv;
+};
+
+// Run by the whole CTA.  g: this tile's slot; g0: first slot of its chain
+// (whose exclusive value is 0).  Publishes g's aggregate, then inspects the
+// NTHREADS preceding slots at once (one flag per thread), waits until all of
+// them have published, composes the aggregates after the nearest inclusive
+// prefix, and repeats further back if there is none.  Publishes g's inclusive
+// prefix and returns g's exclusive value (the same in every thread).  If the
+// wait runs out, records ZC_ERR_TIMEOUT, sets timed_out and returns 0.
+__device__ __forceinline__ unsigned long long lookback_cta(const Chain& ch, unsigned g,
+                                                           unsigned g0, unsigned long long agg,
+                                                           bool h, unsigned E, const WaitCfg& wc,
+                                                           Ctl* ctl, bool& timed_out, LbSmem& ls)
 {
-    const int lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool publish = (long long)g != wc.withhold;
     const Xf self{agg, 0ull, h};
-    *timed_out = false;
+    timed_out = false;
     if (g == g0) {
-        if (lane == 0 && publish) {
+        if (tid == 0 && publish) {
             st_relaxed(ch.pref + g, xf_apply(self, 0ull));
             if (agg > AGG_INLINE_MAX) st_relaxed(ch.aggw + g, agg);
             st_release(ch.flag + g, make_flag(E, ST_PREFIX, h, agg));
         }
         return 0ull;
     }
-    if (lane == 0 && publish) {
+    if (tid == 0 && publish) {
         if (agg > AGG_INLINE_MAX) st_relaxed(ch.aggw + g, agg);
         st_release(ch.flag + g, make_flag(E, ST_AGG, h, agg));
     }
     Xf acc = xf_id();
     long long hi = (long long)g - 1;
     unsigned long long excl = 0ull;
+    const unsigned long long t0 = globaltimer();
     while (true) {
-        const long long j = hi - 31 + lane;
+        const long long j = hi - (NTHREADS - 1) + tid;
         const bool virt = j < (long long)g0;
         unsigned long long f = 0ull;
         bool valid = virt;
@@ -262,53 +306,58 @@ __device__ __forceinline__ unsigned long long lookback(const Chain& ch, unsigned
             f = ld_acquire(ch.flag + j);
             valid = (unsigned)(f >> 32) == E && ((f >> 30) & 3u) != 0u;
         }
-        const unsigned long long t0 = globaltimer();
         unsigned ns = 32;
-        bool expired = false;
-        while (!__all_sync(FULL, valid)) {
-            // the decision to give up is taken by the whole warp at once
-            expired = __any_sync(FULL, globaltimer() - t0 > wc.limit_ns);
-            if (expired) break;
+        while (!__syncthreads_and(valid)) {
+            // the decision to give up is taken by the whole CTA at once
+            if (__syncthreads_or(tid == 0 && globaltimer() - t0 > wc.limit_ns)) {
+                timed_out = true;
+                break;
+            }
             __nanosleep(ns);
-            ns = ns < 2048 ? ns * 2 : ns;
+            ns = ns < 256 ? ns * 2 : ns;
             if (!valid) {
                 f = ld_acquire(ch.flag + j);
                 valid = (unsigned)(f >> 32) == E && ((f >> 30) & 3u) != 0u;
             }
         }
-        if (expired) {
-            *timed_out = true;
-            if (lane == 0) fail(ctl, ZC_ERR_TIMEOUT, g);
+        if (timed_out) {
+            if (tid == 0) fail(ctl, ZC_ERR_TIMEOUT, g);
             excl = 0ull;
             break;
         }
         const bool is_pref = virt || ((f >> 30) & 3u) == ST_PREFIX;
-        const unsigned pmask = __ballot_sync(FULL, is_pref);
+        const unsigned pm = __ballot_sync(FULL, is_pref);
+        if (lane == 0) ls.wp[warp] = pm ? warp * 32 + 31 - __clz(pm) : -1;
         Xf t = xf_id();
         if (!virt) {
             t.h = (f >> 29) & 1u;
             t.a = ((f >> 28) & 1u) ? ld_relaxed(ch.aggw + j) : (f & AGG_INLINE_MAX);
         }
-        const int p = pmask ? 31 - __clz(pmask) : -1;
-        if (lane <= p) t = xf_id();
-        // inclusive composition over lanes: lane 31 ends with T_{p+1} o ... o T_31
+        __syncthreads();
+        int p = -1;
+#pragma unroll
+        for (int w = 0; w < NWARPS; ++w) p = ls.wp[w] > p ? ls.wp[w] : p;
+        if (tid <= p) t = xf_id();
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const Xf o = xf_shfl_up(t, off);
             if (lane >= off) t = xf_compose(o, t);
         }
-        const Xf w = xf_shfl(t, 31);
+        if (lane == 31) ls.wx[warp] = t;
+        if (tid == p) ls.pv = virt ? 0ull : ld_relaxed(ch.pref + j);
+        __syncthreads();
+        Xf w = xf_id();
+#pragma unroll
+        for (int k = 0; k < NWARPS; ++k) w = xf_compose(w, ls.wx[k]);
         acc = xf_compose(w, acc);
         if (p >= 0) {
-            unsigned long long pv = 0ull;
-            if (lane == p && !virt) pv = ld_relaxed(ch.pref + j);
-            pv = __shfl_sync(FULL, pv, p);
-            excl = xf_apply(acc, pv);
+            excl = xf_apply(acc, ls.pv);
             break;
         }
-        hi -= 32;
+        hi -= NTHREADS;
+        __syncthreads();  // ls is rewritten by the next window
     }
-    if (lane == 0 && publish) {
+    if (tid == 0 && publish) {
         st_relaxed(ch.pref + g, xf_apply(self, excl));
         st_release(ch.flag + g, make_flag(E, ST_PREFIX, h, agg));
     }

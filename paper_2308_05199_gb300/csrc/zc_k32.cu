@@ -1,53 +1,74 @@
-// zc_k32.cu -- compress and ring-step kernels at block size L = 32.
+// zc_k32.cu -- encoder kernels (compress, scatter pack, ring step) at L = 32.
 #include "zc_launch.h"
 
 namespace zc {
 
-template <int R>
-static cudaError_t compress_rows(int x_dtype, const Launch& P, unsigned grid, cudaStream_t s)
+template <typename K>
+static cudaError_t prepare(K kernel, int U)
 {
-    if (x_dtype == ZC_F32) k_compress<5, R, float><<<grid, NTHREADS, 0, s>>>(P);
-    else k_compress<5, R, uint16_t><<<grid, NTHREADS, 0, s>>>(P);
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                enc_smem_bytes(U));
+}
+
+template <int U>
+static cudaError_t compress_u(int x_dtype, const Launch& P, unsigned grid, cudaStream_t s)
+{
+    static const cudaError_t e32 = prepare(k_compress<5, U, float>, U);
+    static const cudaError_t e16 = prepare(k_compress<5, U, uint16_t>, U);
+    if (e32 != cudaSuccess || e16 != cudaSuccess) return e32 != cudaSuccess ? e32 : e16;
+    if (x_dtype == ZC_F32) k_compress<5, U, float><<<grid, NTHREADS, enc_smem_bytes(U), s>>>(P);
+    else k_compress<5, U, uint16_t><<<grid, NTHREADS, enc_smem_bytes(U), s>>>(P);
     return cudaGetLastError();
 }
 
-cudaError_t launch_compress_l32(int rows, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s)
+cudaError_t launch_compress_l32(int chunks, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s)
 {
-    switch (rows) {
-    case 4: return compress_rows<4>(x_dtype, P, grid, s);
-    case 8: return compress_rows<8>(x_dtype, P, grid, s);
-    case 16: return compress_rows<16>(x_dtype, P, grid, s);
+    switch (chunks) {
+    case 4: return compress_u<32>(x_dtype, P, grid, s);
+    case 8: return compress_u<64>(x_dtype, P, grid, s);
+    case 16: return compress_u<128>(x_dtype, P, grid, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_reduce_l32(int rows, const Launch& P, unsigned grid, cudaStream_t s)
+template <int U>
+static cudaError_t scatter_u(int x_dtype, const Launch& P, const ScatterParams& SP, unsigned grid,
+                             cudaStream_t s)
 {
-    switch (rows) {
-    case 4: k_reduce<5, 4><<<grid, NTHREADS, 0, s>>>(P); break;
-    case 8: k_reduce<5, 8><<<grid, NTHREADS, 0, s>>>(P); break;
-    case 16: k_reduce<5, 16><<<grid, NTHREADS, 0, s>>>(P); break;
-    default: return cudaErrorInvalidValue;
-    }
+    static const cudaError_t e32 = prepare(k_scatter<5, U, float>, U);
+    static const cudaError_t e16 = prepare(k_scatter<5, U, uint16_t>, U);
+    if (e32 != cudaSuccess || e16 != cudaSuccess) return e32 != cudaSuccess ? e32 : e16;
+    if (x_dtype == ZC_F32) k_scatter<5, U, float><<<grid, NTHREADS, enc_smem_bytes(U), s>>>(P, SP);
+    else k_scatter<5, U, uint16_t><<<grid, NTHREADS, enc_smem_bytes(U), s>>>(P, SP);
     return cudaGetLastError();
 }
 
-template <int R>
-static cudaError_t scatter_rows(int x_dtype, const Launch& P, const ScatterParams& S, unsigned grid,
-                                cudaStream_t s)
-{
-    if (x_dtype == ZC_F32) k_scatter<5, R, float><<<grid, NTHREADS, 0, s>>>(P, S);
-    else k_scatter<5, R, uint16_t><<<grid, NTHREADS, 0, s>>>(P, S);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_scatter_l32(int rows, int x_dtype, const Launch& P, const ScatterParams& S,
+cudaError_t launch_scatter_l32(int chunks, int x_dtype, const Launch& P, const ScatterParams& SP,
                                unsigned grid, cudaStream_t s)
 {
-    switch (rows) {
-    case 4: return scatter_rows<4>(x_dtype, P, S, grid, s);
-    case 8: return scatter_rows<8>(x_dtype, P, S, grid, s);
-    case 16: return scatter_rows<16>(x_dtype, P, S, grid, s);
+    switch (chunks) {
+    case 4: return scatter_u<32>(x_dtype, P, SP, grid, s);
+    case 8: return scatter_u<64>(x_dtype, P, SP, grid, s);
+    case 16: return scatter_u<128>(x_dtype, P, SP, grid, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int U>
+static cudaError_t reduce_u(const Launch& P, unsigned grid, cudaStream_t s)
+{
+    static const cudaError_t e = prepare(k_reduce<5, U>, U);
+    if (e != cudaSuccess) return e;
+    k_reduce<5, U><<<grid, NTHREADS, enc_smem_bytes(U), s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_l32(int chunks, const Launch& P, unsigned grid, cudaStream_t s)
+{
+    switch (chunks) {
+    case 4: return reduce_u<32>(P, grid, s);
+    case 8: return reduce_u<64>(P, grid, s);
+    case 16: return reduce_u<128>(P, grid, s);
     default: return cudaErrorInvalidValue;
     }
 }

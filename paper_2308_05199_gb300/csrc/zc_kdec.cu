@@ -1,16 +1,18 @@
-// zc_kdec.cu -- decompression kernels (block size read from each stream).
+// zc_kdec.cu -- width scan (decode-tile offsets) and decompression kernels.
+#define ZC_DECODE_KERNELS
 #include "zc_launch.h"
 
 namespace zc {
 
-cudaError_t launch_decompress(int rows, const Launch& P, unsigned grid, cudaStream_t s)
+cudaError_t launch_wscan(const Launch& P, unsigned grid, cudaStream_t s)
 {
-    switch (rows) {
-    case 4: k_decompress<4><<<grid, NTHREADS, 0, s>>>(P); break;
-    case 8: k_decompress<8><<<grid, NTHREADS, 0, s>>>(P); break;
-    case 16: k_decompress<16><<<grid, NTHREADS, 0, s>>>(P); break;
-    default: return cudaErrorInvalidValue;
-    }
+    k_wscan<<<grid, NTHREADS, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decompress(const Launch& P, unsigned grid, cudaStream_t s)
+{
+    k_decompress<<<grid, NTHREADS, 0, s>>>(P);
     return cudaGetLastError();
 }
 

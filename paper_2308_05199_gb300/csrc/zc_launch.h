@@ -5,21 +5,23 @@
 
 namespace zc {
 
-// One translation unit per block size instantiates the compress and ring-step
-// kernels for every tile height; these pick the instantiation at run time.
-cudaError_t launch_compress_l16(int rows, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_compress_l32(int rows, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_compress_l64(int rows, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_compress_l128(int rows, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_reduce_l16(int rows, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_reduce_l32(int rows, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_reduce_l64(int rows, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_reduce_l128(int rows, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_decompress(int rows, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_scatter_l16(int rows, int x_dtype, const Launch& P, const ScatterParams& S, unsigned grid, cudaStream_t s);
-cudaError_t launch_scatter_l32(int rows, int x_dtype, const Launch& P, const ScatterParams& S, unsigned grid, cudaStream_t s);
-cudaError_t launch_scatter_l64(int rows, int x_dtype, const Launch& P, const ScatterParams& S, unsigned grid, cudaStream_t s);
-cudaError_t launch_scatter_l128(int rows, int x_dtype, const Launch& P, const ScatterParams& S, unsigned grid, cudaStream_t s);
+// One translation unit per block size instantiates the encoder kernels for
+// every tile size S (sub-tiles of 2048 elements per CTA tile); these pick the
+// instantiation at run time.
+cudaError_t launch_compress_l16(int S, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_compress_l32(int S, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_compress_l64(int S, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_compress_l128(int S, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_reduce_l16(int S, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_reduce_l32(int S, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_reduce_l64(int S, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_reduce_l128(int S, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_scatter_l16(int S, int x_dtype, const Launch& P, const ScatterParams& SP, unsigned grid, cudaStream_t s);
+cudaError_t launch_scatter_l32(int S, int x_dtype, const Launch& P, const ScatterParams& SP, unsigned grid, cudaStream_t s);
+cudaError_t launch_scatter_l64(int S, int x_dtype, const Launch& P, const ScatterParams& SP, unsigned grid, cudaStream_t s);
+cudaError_t launch_scatter_l128(int S, int x_dtype, const Launch& P, const ScatterParams& SP, unsigned grid, cudaStream_t s);
+cudaError_t launch_wscan(const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_decompress(const Launch& P, unsigned grid, cudaStream_t s);
 
 // Range: extremes of the listed segments, then (rel > 0) the bound they imply.
 struct RangeSeg {

@@ -15,7 +15,7 @@
 namespace {
 
 constexpr uint64_t NOALLOC_MAX_N = ZC_NOALLOC_MAX_N;
-constexpr size_t NOALLOC_BYTES = 1u << 20;  // 1 MiB on every GPU that loads the library
+constexpr size_t NOALLOC_BYTES = 2u << 20;  // 2 MiB on every GPU that loads the library
 constexpr int MAX_DEVICES = 64;
 
 std::mutex g_mutex;

@@ -43,8 +43,9 @@ class ZcReduceItem(ctypes.Structure):
 
 
 class ZcPlan(ctypes.Structure):
-    _fields_ = [("n_items", ctypes.c_int), ("rows", ctypes.c_int), ("block", ctypes.c_int),
-                ("total_tiles", ctypes.c_uint64), ("d_table", ctypes.c_void_p)]
+    _fields_ = [("n_items", ctypes.c_int), ("tile_chunks", ctypes.c_int), ("block", ctypes.c_int),
+                ("has_input", ctypes.c_int), ("total_tiles", ctypes.c_uint64),
+                ("total_chunks", ctypes.c_uint64), ("d_table", ctypes.c_void_p)]
 
 
 def lib_path() -> str:
@@ -88,7 +89,7 @@ def _declare(L):
         "zc_clear_device_status": (i32, [vp, vp]),
         "zc_set_wait_limit_ns": (None, [u64]),
         "zc_debug_withhold_tile": (None, [c.c_int64]),
-        "zc_set_rows_per_warp": (i32, [i32]),
+        "zc_set_tile_chunks": (i32, [i32]),
         "zc_version": (c.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -103,7 +104,7 @@ def exported_names():
             "zc_plan_table_bytes", "zc_plan_reduce", "zc_reduce_step_batch", "zc_scatter_pack",
             "zc_compress_noalloc",
             "zc_get_device_status", "zc_clear_device_status", "zc_set_wait_limit_ns",
-            "zc_debug_withhold_tile", "zc_set_rows_per_warp", "zc_version"]
+            "zc_debug_withhold_tile", "zc_set_tile_chunks", "zc_version"]
 
 
 def _check(st: int, where: str):
@@ -213,8 +214,8 @@ def zc_debug_withhold_tile(tile: int):
     lib().zc_debug_withhold_tile(int(tile))
 
 
-def zc_set_rows_per_warp(rows: int) -> int:
-    return lib().zc_set_rows_per_warp(rows)
+def zc_set_tile_chunks(chunks: int) -> int:
+    return lib().zc_set_tile_chunks(chunks)
 
 
 def zc_version() -> str:

@@ -28,7 +28,7 @@ def zc():
     from paper_2308_05199_gb300 import build
     build.build()
     from paper_2308_05199_gb300 import zc as z
-    z.zc_set_rows_per_warp(8)
+    z.zc_set_tile_chunks(8)
     return z
 
 
@@ -75,18 +75,52 @@ def test_compress_stream_bytes_match_oracle(zc, block, kind):
         assert s_gpu == s_ref, (n, block, kind)
 
 
-@pytest.mark.parametrize("rows", [4, 8, 16])
-def test_tile_height_does_not_change_the_stream(zc, rows):
-    x = signal("walk", 50000, 3)
+@pytest.mark.parametrize("chunks", [4, 8, 16])
+def test_tile_size_does_not_change_the_stream(zc, chunks):
+    x = signal("walk", 150000, 3)
     ref = oracle.compress(np_of(x), 1e-4, 5)
     try:
-        assert zc.zc_set_rows_per_warp(rows) == 0
+        assert zc.zc_set_tile_chunks(chunks) == 0
         for block in BLOCKS:
             s, st = gpu_compress(zc, x, 1e-4, block)
             assert st[0] == 0 and s == oracle.compress(np_of(x), 1e-4, int(math.log2(block)))
         assert gpu_compress(zc, x, 1e-4, 32)[0] == ref
+        # decode and the ring step at this tile size too, every block size
+        for block in BLOCKS:
+            lg = int(math.log2(block))
+            rb = oracle.compress(np_of(x), 1e-4, lg)
+            cmp = torch.frombuffer(bytearray(rb), dtype=torch.uint8).cuda()
+            np.testing.assert_array_equal(np_of(zc.decompress(cmp, x.numel())),
+                                          oracle.decompress(rb, x.numel()))
+            out, ob, sm = zc.reduce_step(cmp, x.cuda(), 1e-4, block, want_sum=True)
+            r_s, r_sum = oracle.reduce_step(rb, np_of(x), 1e-4, lg, want_sum=True)
+            assert zc.stream_bytes(out, ob) == r_s
+            np.testing.assert_array_equal(np_of(sm), r_sum)
     finally:
-        zc.zc_set_rows_per_warp(8)
+        zc.zc_set_tile_chunks(8)
+
+
+@pytest.mark.parametrize("block", BLOCKS)
+def test_wide_and_narrow_blocks_mixed(zc, block):
+    """Heavy-tailed data at a tight bound: blocks above 16 planes (one row per
+    transpose) next to narrow ones (two rows per transpose), through
+    compress, decompress and the ring step."""
+    lg = int(math.log2(block))
+    g = np.random.default_rng(17)
+    scale = np.where(np.arange(70000) < 35000, 0.002, 100.0)  # narrow half, wide half
+    x = np.clip(g.standard_t(2, 70000) * scale, -3000, 3000).astype(np.float32)
+    xt = torch.from_numpy(x)
+    s, st = gpu_compress(zc, xt, 1e-3, block)
+    ref = oracle.compress(x, 1e-3, lg)
+    assert st[0] == 0 and s == ref
+    widths = np.frombuffer(ref[32:32 + (70000 + block - 1) // block], np.uint8)
+    assert widths.max() > 16 and widths.min() < 15
+    cmp = torch.frombuffer(bytearray(ref), dtype=torch.uint8).cuda()
+    np.testing.assert_array_equal(np_of(zc.decompress(cmp, 70000)), oracle.decompress(ref, 70000))
+    out, ob, sm = zc.reduce_step(cmp, xt.cuda(), 1e-3, block, want_sum=True)
+    r_s, r_sum = oracle.reduce_step(ref, x, 1e-3, lg, want_sum=True)
+    assert zc.stream_bytes(out, ob) == r_s
+    np.testing.assert_array_equal(np_of(sm), r_sum)
 
 
 @pytest.mark.parametrize("block", BLOCKS)
@@ -364,7 +398,7 @@ def test_lookback_wait_times_out_and_recovers(zc):
     """A tile that never publishes its offset: its successors' bounded waits
     run out, ZC_ERR_TIMEOUT is recorded, the kernel returns, and the same
     workspace works normally afterwards."""
-    n = 2048 * 12
+    n = 16384 * 12  # 12 encoder tiles of 8 chunks
     x = signal("walk", n, 2)
     ws = zc.Workspace(n, 1)
     try:

@@ -61,8 +61,10 @@ def test_sizing_matches_format(lib):
     b = lib.zc_workspace_bytes(1 << 27, 1)
     c = lib.zc_workspace_bytes(1 << 27, 64)
     assert 0 < a < b < c and a % 256 == 0
-    # one look-back record set per 1024-element tile, at most
-    assert b >= 7 * 8 * ((1 << 27) // 1024)
+    # one record set (8 u64) per 2048-element decode tile
+    assert b >= 8 * 8 * ((1 << 27) // 2048)
+    # the no-allocation entry point's fixed 2 MiB scratch covers its 2^24 limit
+    assert lib.zc_workspace_bytes(1 << 24, 1) <= 2 << 20
 
 
 def test_argument_errors_without_gpu(lib):
@@ -88,6 +90,6 @@ def test_argument_errors_without_gpu(lib):
     # workspace too small
     assert lib.zc_compress(fake, 1 << 20, 0, 0, 1e-3, 32, fake, 1 << 23, fake, fake, 4096,
                            None) == 8
-    lib.zc_set_rows_per_warp.restype = ctypes.c_int
-    assert lib.zc_set_rows_per_warp(5) == 1
-    assert lib.zc_set_rows_per_warp(8) == 0
+    lib.zc_set_tile_chunks.restype = ctypes.c_int
+    assert lib.zc_set_tile_chunks(5) == 1
+    assert lib.zc_set_tile_chunks(8) == 0
