@@ -202,7 +202,7 @@ __device__ __forceinline__ float scan_incl_f16(float v)
 template <int LOG2L, int U>
 __device__ __forceinline__ unsigned long long unit_meta(const Launch& P, const Item& it,
                                                         unsigned slot, unsigned long long ue0,
-                                                        int2* meta)
+                                                        int2* meta, bool& narrow)
 {
     constexpr int L = 1 << LOG2L;
     constexpr int PB = L / 8;
@@ -244,6 +244,12 @@ __device__ __forceinline__ unsigned long long unit_meta(const Launch& P, const I
         sum += np[i] * PB;
     }
     if (bad) fail(P.ctl, ZC_ERR_FORMAT, b0);
+    {
+        int npmax = 0;
+#pragma unroll
+        for (int i = 0; i < BPL; ++i) npmax = max(npmax, np[i]);
+        narrow = __all_sync(FULL, npmax <= 16);
+    }
     int tot;
     int off = warp_excl_scan(sum, lane, tot);
     const unsigned long long base = 32ull + ceil16(nb) + P.offs[slot];
@@ -270,98 +276,107 @@ __device__ __forceinline__ float delta_f(uint32_t u)
 }
 
 // Decodes rows [g GR, g GR + GR) of a warp unit into acc[] (x^ = q * 2eb).
-// `src` points at the stream, offsets in `meta` are from the unit's payload
-// start `base`.  A pair of rows whose blocks have at most 16 planes shares one
-// transpose and is scanned in FP32 (every partial sum is an integer below
+// `src` points at the unit's payload, `meta` at its block metadata.  All of
+// the group's plane words are requested before the first transpose so their
+// loads overlap.  A pair of rows whose blocks have at most 16 planes shares
+// one transpose and is scanned in FP32 (every partial sum is an integer below
 // 2^22: exact); wider rows are scanned in integers.
-template <int LOG2L>
+template <int LOG2L, bool NARROW>
 __device__ __forceinline__ void decode_group(const uint8_t* src, const int2* meta, int g,
                                              float two_eb, float acc[GR], const TpC& tc)
 {
     constexpr int L = 1 << LOG2L;
     constexpr int RPB = L >= 32 ? L / 32 : 1;
+    constexpr int NR = L == 128 ? 4 : 2;  // rows per step (pair, or quad at L = 128)
+    constexpr int NS = GR / NR;           // steps per group
     const int lane = threadIdx.x & 31;
     const int k = lane & 15;
     const bool hi = lane >= 16;
     const int fb = L >= 32 ? g * GR / RPB : g * GR * 2;  // first block of the group
     const int2* mt = meta + fb;
+    // ---- phase 1: metadata and plane loads of every step ----
+    uint32_t wv[NS][NR];
+    unsigned paired = 0;  // bit s: step s has at most 16 planes per block
 #pragma unroll
-    for (int r = 0; r < GR; r += (L == 128 ? 4 : 2)) {
-        uint32_t u[4];
-        bool paired;
+    for (int st = 0; st < NS; ++st) {
+        const int r = st * NR;
         if (L == 32) {
             const int4 m = *(const int4*)&mt[r];
-            paired = m.x <= 16 && m.z <= 16;
-            if (paired) {
+            if (NARROW || (m.x <= 16 && m.z <= 16)) {
+                paired |= 1u << st;
                 const int np = hi ? m.z : m.x, off = hi ? m.w : m.y;
-                const uint32_t w = k < np ? __ldg((const unsigned*)(src + off) + k) : 0u;
-                const uint32_t t = tpose(w, tc);
-                u[0] = t & 0xffffu;
-                u[1] = t >> 16;
+                wv[st][0] = k < np ? __ldg((const unsigned*)src + (((unsigned)off >> 2) + k)) : 0u;
             } else {
-                const uint32_t wa = lane < m.x ? __ldg((const unsigned*)(src + m.y) + lane) : 0u;
-                const uint32_t wb = lane < m.z ? __ldg((const unsigned*)(src + m.w) + lane) : 0u;
-                u[0] = tpose(wa, tc);
-                u[1] = tpose(wb, tc);
+                wv[st][0] = lane < m.x ? __ldg((const unsigned*)(src + m.y) + lane) : 0u;
+                wv[st][1] = lane < m.z ? __ldg((const unsigned*)(src + m.w) + lane) : 0u;
             }
         } else if (L == 16) {
             const int4 m0 = *(const int4*)&mt[2 * r];
             const int4 m1 = *(const int4*)&mt[2 * r + 2];
-            paired = max(max(m0.x, m0.z), max(m1.x, m1.z)) <= 16;
-            if (paired) {
+            if (NARROW || max(max(m0.x, m0.z), max(m1.x, m1.z)) <= 16) {
+                paired |= 1u << st;
                 const int npL = hi ? m1.x : m0.x, offL = hi ? m1.y : m0.y;
                 const int npH = hi ? m1.z : m0.z, offH = hi ? m1.w : m0.w;
                 const uint32_t wl = k < npL ? __ldg((const unsigned short*)(src + offL) + k) : 0u;
                 const uint32_t wh = k < npH ? __ldg((const unsigned short*)(src + offH) + k) : 0u;
-                const uint32_t t = tpose(wl | (wh << 16), tc);
-                u[0] = t & 0xffffu;
-                u[1] = t >> 16;
+                wv[st][0] = wl | (wh << 16);
             } else {
                 uint32_t wl = lane < m0.x ? __ldg((const unsigned short*)(src + m0.y) + lane) : 0u;
                 uint32_t wh = lane < m0.z ? __ldg((const unsigned short*)(src + m0.w) + lane) : 0u;
-                u[0] = tpose(wl | (wh << 16), tc);
+                wv[st][0] = wl | (wh << 16);
                 wl = lane < m1.x ? __ldg((const unsigned short*)(src + m1.y) + lane) : 0u;
                 wh = lane < m1.z ? __ldg((const unsigned short*)(src + m1.w) + lane) : 0u;
-                u[1] = tpose(wl | (wh << 16), tc);
+                wv[st][1] = wl | (wh << 16);
             }
         } else if (L == 64) {
             const int2 m = mt[r / 2];
-            paired = m.x <= 16;
-            if (paired) {
-                const uint32_t w =
+            if (NARROW || m.x <= 16) {
+                paired |= 1u << st;
+                wv[st][0] =
                     k < m.x ? __ldg((const unsigned*)(src + m.y + 8 * k + (hi ? 4 : 0))) : 0u;
-                const uint32_t t = tpose(w, tc);
-                u[0] = t & 0xffffu;
-                u[1] = t >> 16;
             } else {
                 uint2 v = make_uint2(0u, 0u);
                 if (lane < m.x) v = __ldg((const uint2*)(src + m.y) + lane);
-                u[0] = tpose(v.x, tc);
-                u[1] = tpose(v.y, tc);
+                wv[st][0] = v.x;
+                wv[st][1] = v.y;
             }
         } else {
             const int2 m = mt[r / 4];
-            paired = m.x <= 16;
-            if (paired) {
+            if (NARROW || m.x <= 16) {
+                paired |= 1u << st;
                 const uint8_t* pp = src + m.y + 16 * k + (hi ? 4 : 0);
-                const uint32_t w0 = k < m.x ? __ldg((const unsigned*)pp) : 0u;
-                const uint32_t w1 = k < m.x ? __ldg((const unsigned*)(pp + 8)) : 0u;
-                const uint32_t t0 = tpose(w0, tc), t1 = tpose(w1, tc);
-                u[0] = t0 & 0xffffu;
-                u[1] = t0 >> 16;
-                u[2] = t1 & 0xffffu;
-                u[3] = t1 >> 16;
+                wv[st][0] = k < m.x ? __ldg((const unsigned*)pp) : 0u;
+                wv[st][1] = k < m.x ? __ldg((const unsigned*)(pp + 8)) : 0u;
             } else {
                 uint4 v = make_uint4(0u, 0u, 0u, 0u);
                 if (lane < m.x) v = __ldg((const uint4*)(src + m.y) + lane);
-                u[0] = tpose(v.x, tc);
-                u[1] = tpose(v.y, tc);
-                u[2] = tpose(v.z, tc);
-                u[3] = tpose(v.w, tc);
+                wv[st][0] = v.x;
+                wv[st][1] = v.y;
+                wv[st][2 % NR] = v.z;
+                wv[st][3 % NR] = v.w;
             }
         }
-        constexpr int NR = L == 128 ? 4 : 2;
-        if (paired) {
+    }
+    // ---- phase 2: transposes, prefix sums, reconstruction ----
+#pragma unroll
+    for (int st = 0; st < NS; ++st) {
+        const int r = st * NR;
+        uint32_t u[4];
+        const bool pr = NARROW || ((paired >> st) & 1u);
+        if (pr) {
+            const uint32_t t0 = tpose(wv[st][0], tc);
+            u[0] = t0 & 0xffffu;
+            u[1] = t0 >> 16;
+            if (NR == 4) {
+                const uint32_t t1 = tpose(wv[st][1 % NR], tc);
+                u[2] = t1 & 0xffffu;
+                u[3] = t1 >> 16;
+            }
+        } else {
+#pragma unroll
+            for (int h = 0; h < NR; ++h) u[h] = tpose(wv[st][h], tc);
+        }
+        if (pr) {
             float carry = 0.0f;
 #pragma unroll
             for (int h = 0; h < NR; ++h) {
@@ -387,11 +402,26 @@ __device__ __forceinline__ void decode_group(const uint8_t* src, const int2* met
 
 // ---- encoding ------------------------------------------------------------------
 // Quantizes, delta-codes and bit-plane packs GR rows (the first `nrem`
-// elements are valid; the rest are padding with zero deltas), appends the
+// elements are valid, all of them when ALL; the rest are padding with zero
+// deltas), appends the
 // planes of their blocks to `seg` at byte `lo` in stream order, writes their
 // width bytes to `wb`, ORs any quantizer error into `err`, and returns the new
 // `lo`.  Two rows whose values fit 16 bits share one transpose.
-template <int LOG2L>
+// The previous lane's q within segments of W lanes; the first lane of a
+// segment gets `fill` (uses the in-range predicate of shfl.up).
+template <int W>
+__device__ __forceinline__ int prev_lane(int q, int fill)
+{
+    int p;
+    asm("{\n\t.reg .pred ok;\n\t"
+        "shfl.sync.up.b32 %0|ok, %1, 1, %2, -1;\n\t"
+        "@!ok mov.b32 %0, %3;\n\t}"
+        : "=r"(p)
+        : "r"(q), "r"((32 - W) << 8), "r"(fill));
+    return p;
+}
+
+template <int LOG2L, bool ALL>
 __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float eb, float two_eb,
                                             float inv, uint8_t* seg, int lo, uint8_t* wb, int& err,
                                             const TpC& tc)
@@ -401,49 +431,60 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
     const int lane = threadIdx.x & 31;
     const int k = lane & 15;
     const bool hi = lane >= 16;
+    // quantize: the exactness of the fast rounding is voted once per group
+    int q[GR];
+    {
+        bool slow = false;
+#pragma unroll
+        for (int r = 0; r < GR; ++r) slow |= !quantize_fast(acc[r], inv, q[r]);
+        if (__any_sync(FULL, slow)) {
+#pragma unroll
+            for (int r = 0; r < GR; ++r) {
+                q[r] = 0;
+                if (ALL || r * 32 + lane < nrem) err |= quantize(acc[r], eb, two_eb, inv, q[r]);
+            }
+        }
+    }
     uint32_t u[GR];
+    uint32_t wide = 0;
     int carry = 0;
 #pragma unroll
     for (int r = 0; r < GR; ++r) {
-        const bool valid = r * 32 + lane < nrem;
-        int q = 0;
-        if (valid) err |= quantize(acc[r], eb, two_eb, inv, q);
-        int prev = __shfl_up_sync(FULL, q, 1);
-        if (L == 16) {
-            if (k == 0) prev = 0;
-        } else if (lane == 0) {
-            prev = (L >= 64 && (r % RPB) != 0) ? carry : 0;
-        }
-        if (L >= 64 && (r % RPB) != RPB - 1) carry = __shfl_sync(FULL, q, 31);
-        const int d = valid ? q - prev : 0;
+        const int fill = (L >= 64 && (r % RPB) != 0) ? carry : 0;
+        const int prev = prev_lane<L == 16 ? 16 : 32>(q[r], fill);
+        if (L >= 64 && (r % RPB) != RPB - 1) carry = __shfl_sync(FULL, q[r], 31);
+        int d = q[r] - prev;
+        if (!ALL && r * 32 + lane >= nrem) d = 0;
         const uint32_t ad = (uint32_t)(d < 0 ? -d : d);
         u[r] = __funnelshift_l((uint32_t)d, ad, 1);  // |d| << 1 | sign
+        wide |= u[r];
     }
+    // one vote: does any value of the group need more than 16 planes?
+    const bool any_wide = __any_sync(FULL, (wide >> 16) != 0u);
+    const uint32_t hmask = hi ? 0xffffffffu : 0u;
 #pragma unroll
     for (int r = 0; r < GR; r += (L == 128 ? 4 : 2)) {
         if (L == 32) {
-            int npA, npB;
-            if (!__any_sync(FULL, ((u[r] | u[r + 1]) >> 16) != 0u)) {
+            int fa, fb;  // highest nonzero plane of blocks r, r + 1 (-1: none)
+            if (!any_wide || !__any_sync(FULL, ((u[r] | u[r + 1]) >> 16) != 0u)) {
                 const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
                 const unsigned m = __ballot_sync(FULL, t != 0u);
-                npA = 32 - __clz(m & 0xffffu);
-                npB = 32 - __clz(m >> 16);
-                if (k < (hi ? npB : npA)) *(uint32_t*)(seg + lo + (hi ? 4 * npA : 0) + 4 * k) = t;
+                fa = 31 - __clz(m & 0xffffu);
+                fb = 31 - __clz(m >> 16);
+                const int npm = hi ? fb + 1 : fa + 1;
+                if (k < npm) *(uint32_t*)(seg + lo + (hmask & (4 * fa + 4)) + 4 * k) = t;
             } else {
                 const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
-                npA = 32 - __clz(__ballot_sync(FULL, ta != 0u));
-                npB = 32 - __clz(__ballot_sync(FULL, tb != 0u));
-                if (lane < npA) ((uint32_t*)(seg + lo))[lane] = ta;
-                if (lane < npB) ((uint32_t*)(seg + lo + 4 * npA))[lane] = tb;
+                fa = 31 - __clz(__ballot_sync(FULL, ta != 0u));
+                fb = 31 - __clz(__ballot_sync(FULL, tb != 0u));
+                if (lane <= fa) ((uint32_t*)(seg + lo))[lane] = ta;
+                if (lane <= fb) ((uint32_t*)(seg + lo + 4 * fa + 4))[lane] = tb;
             }
-            if (lane == 0) {
-                wb[r] = width_byte(npA);
-                wb[r + 1] = width_byte(npB);
-            }
-            lo += 4 * (npA + npB);
+            if (lane == 0) *(uint16_t*)(wb + r) = (uint16_t)(max(fa, 0) | (max(fb, 0) << 8));
+            lo += 4 * (fa + fb + 2);
         } else if (L == 16) {
             int npA, npB, npC, npD;
-            if (!__any_sync(FULL, ((u[r] | u[r + 1]) >> 16) != 0u)) {
+            if (!any_wide || !__any_sync(FULL, ((u[r] | u[r + 1]) >> 16) != 0u)) {
                 const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
                 const unsigned m0 = __ballot_sync(FULL, (t & 0xffffu) != 0u);
                 const unsigned m1 = __ballot_sync(FULL, (t >> 16) != 0u);
@@ -468,20 +509,18 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                 if (lane < npC) ((uint16_t*)(seg + oC))[lane] = (uint16_t)(tb & 0xffffu);
                 if (lane < npD) ((uint16_t*)(seg + oD))[lane] = (uint16_t)(tb >> 16);
             }
-            if (lane == 0) {
-                wb[2 * r] = width_byte(npA);
-                wb[2 * r + 1] = width_byte(npB);
-                wb[2 * r + 2] = width_byte(npC);
-                wb[2 * r + 3] = width_byte(npD);
-            }
+            if (lane == 0)
+                *(uint32_t*)(wb + 2 * r) = (uint32_t)width_byte(npA) | ((uint32_t)width_byte(npB) << 8) |
+                                           ((uint32_t)width_byte(npC) << 16) |
+                                           ((uint32_t)width_byte(npD) << 24);
             lo += 2 * (npA + npB + npC + npD);
         } else if (L == 64) {
             int np;
-            if (!__any_sync(FULL, ((u[r] | u[r + 1]) >> 16) != 0u)) {
+            if (!any_wide || !__any_sync(FULL, ((u[r] | u[r + 1]) >> 16) != 0u)) {
                 const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
                 const unsigned m = __ballot_sync(FULL, t != 0u);
                 np = 32 - __clz((m & 0xffffu) | (m >> 16));
-                if (k < np) *(uint32_t*)(seg + lo + 8 * k + (hi ? 4 : 0)) = t;
+                if (k < np) *(uint32_t*)(seg + lo + 8 * k + (hmask & 4)) = t;
             } else {
                 const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
                 np = 32 - __clz(__ballot_sync(FULL, (ta | tb) != 0u));
@@ -491,13 +530,14 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
             lo += 8 * np;
         } else {
             int np;
-            if (!__any_sync(FULL, ((u[r] | u[r + 1] | u[r + 2] | u[r + 3]) >> 16) != 0u)) {
+            if (!any_wide ||
+                !__any_sync(FULL, ((u[r] | u[r + 1] | u[r + 2] | u[r + 3]) >> 16) != 0u)) {
                 const uint32_t t0 = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
                 const uint32_t t1 = tpose(__byte_perm(u[r + 2], u[r + 3], 0x5410), tc);
                 const unsigned m = __ballot_sync(FULL, (t0 | t1) != 0u);
                 np = 32 - __clz((m & 0xffffu) | (m >> 16));
                 if (k < np) {
-                    uint8_t* pp = seg + lo + 16 * k + (hi ? 4 : 0);
+                    uint8_t* pp = seg + lo + 16 * k + (hmask & 4);
                     *(uint32_t*)pp = t0;
                     *(uint32_t*)(pp + 8) = t1;
                 }
@@ -585,10 +625,20 @@ __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, uns
     if (ue0 < n) {
         const uint8_t* src = nullptr;
         int2* meta = nullptr;
+        bool narrow = false;
         if constexpr (HAS_CIN) {
             __shared__ __align__(16) int2 meta_all[NWARPS][BU];
             meta = meta_all[warp];
-            if (do_cin) src = it.cin + unit_meta<LOG2L, U>(P, it, g * NWARPS + warp, ue0, meta);
+            if (do_cin) src = it.cin + unit_meta<LOG2L, U>(P, it, g * NWARPS + warp, ue0, meta, narrow);
+        }
+        // the next group's input is loaded while the current one is encoded
+        float xn[GR];
+        const TX* const xbase = it.x != nullptr ? (const TX*)it.x + ue0 + lane : nullptr;
+        {
+            const int nrem0 = (int)min(n - ue0, (unsigned long long)(GR * 32));
+#pragma unroll
+            for (int r = 0; r < GR; ++r)
+                xn[r] = (xbase != nullptr && r * 32 + lane < nrem0) ? load_x<TX>(xbase, r * 32) : 0.0f;
         }
 #pragma unroll 1
         for (int gi = 0; gi < U / GR; ++gi) {
@@ -596,19 +646,20 @@ __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, uns
             if (e0 >= n) break;
             const int nrem = (int)min(n - e0, (unsigned long long)(GR * 32));
             float acc[GR];
-            if (it.x != nullptr) {
-                const TX* xp = (const TX*)it.x + e0 + lane;
+#pragma unroll
+            for (int r = 0; r < GR; ++r) acc[r] = xn[r];
+            if (gi + 1 < U / GR && e0 + GR * 32 < n) {
+                const int nrem1 = (int)min(n - e0 - GR * 32, (unsigned long long)(GR * 32));
+                const TX* xp = xbase + (gi + 1) * GR * 32;
 #pragma unroll
                 for (int r = 0; r < GR; ++r)
-                    acc[r] = r * 32 + lane < nrem ? load_x<TX>(xp, r * 32) : 0.0f;
-            } else {
-#pragma unroll
-                for (int r = 0; r < GR; ++r) acc[r] = 0.0f;
+                    xn[r] = (xbase != nullptr && r * 32 + lane < nrem1) ? load_x<TX>(xp, r * 32) : 0.0f;
             }
             if constexpr (HAS_CIN) {
                 if (do_cin) {
                     float dv[GR];
-                    decode_group<LOG2L>(src, meta, gi, two_eb_in, dv, tc);
+                    if (narrow) decode_group<LOG2L, true>(src, meta, gi, two_eb_in, dv, tc);
+                    else decode_group<LOG2L, false>(src, meta, gi, two_eb_in, dv, tc);
 #pragma unroll
                     for (int r = 0; r < GR; ++r) acc[r] = __fadd_rn(dv[r], acc[r]);
                 }
@@ -626,7 +677,12 @@ __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, uns
             }
             if (do_enc) {
                 const int b0 = L >= 32 ? gi * GR / (L / 32) : gi * GR * 2;
-                lo = encode_group<LOG2L>(acc, nrem, eb, two_eb, inv, seg, lo, wb + b0, err, tc);
+                if (nrem == GR * 32)
+                    lo = encode_group<LOG2L, true>(acc, nrem, eb, two_eb, inv, seg, lo, wb + b0,
+                                                   err, tc);
+                else
+                    lo = encode_group<LOG2L, false>(acc, nrem, eb, two_eb, inv, seg, lo, wb + b0,
+                                                    err, tc);
             }
         }
     }
@@ -972,14 +1028,16 @@ __device__ __forceinline__ void unit_decode(const Launch& P, const Item& it, uns
 {
     const int lane = threadIdx.x & 31;
     const TpC tc = tp_consts(lane);
-    const uint8_t* src = it.cin + unit_meta<LOG2L, DEC_U>(P, it, slot, ue0, meta);
+    bool narrow;
+    const uint8_t* src = it.cin + unit_meta<LOG2L, DEC_U>(P, it, slot, ue0, meta, narrow);
 #pragma unroll 1
     for (int gi = 0; gi < DEC_U / GR; ++gi) {
         const unsigned long long e0 = ue0 + (unsigned long long)gi * GR * 32;
         if (e0 >= it.n) break;
         const int nrem = (int)min(it.n - e0, (unsigned long long)(GR * 32));
         float acc[GR];
-        decode_group<LOG2L>(src, meta, gi, two_eb, acc, tc);
+        if (narrow) decode_group<LOG2L, true>(src, meta, gi, two_eb, acc, tc);
+        else decode_group<LOG2L, false>(src, meta, gi, two_eb, acc, tc);
         TO* op = (TO*)it.raw_out + e0 + lane;
         if (nrem == GR * 32) {
 #pragma unroll

@@ -158,6 +158,18 @@ __device__ __forceinline__ int scan_incl(int v)
 // whether q0 or its neighbour is nearest (the residual is a multiple of
 // ulp(eb) near |r| = eb, so rounding cannot move it across eb).
 // Returns 0 or a zc_status code.
+// Branch-free fast path of quantize(): q = rint(x * inv); returns false when
+// that may differ from the exact rounding (near a tie, |v| >= 2^19, NaN/Inf).
+__device__ __forceinline__ bool quantize_fast(float x, float inv, int& q)
+{
+    const float v = __fmul_rn(x, inv);
+    const float t = __fadd_rn(v, 12582912.0f);
+    const float r = __fsub_rn(t, 12582912.0f);
+    const float f = fabsf(__fsub_rn(v, r));
+    q = __float_as_int(t) - 0x4b400000;
+    return __fmaf_rn(fabsf(v), 9.5367431640625e-07f, f) < 0.5f;  // |v| * 2^-20
+}
+
 __device__ __forceinline__ int quantize(float x, float eb, float two_eb, float inv, int& q)
 {
     const float v = __fmul_rn(x, inv);
