@@ -197,6 +197,123 @@ int zc_scatter_pack(const void* d_in, int dtype, int P, const uint64_t* h_counts
                     void* d_out, size_t out_cap, uint64_t* d_seg_off, void* d_ws,
                     size_t ws_bytes, zc_stream_t s);
 
+/* ---- Batched compression: many messages, one launch ----------------------
+ *
+ * Sec. 3.2.2 observes that one compression launch per small message leaves
+ * the GPU mostly idle, and Sec. 3.3.3 prices a collective's compression as
+ * the cost of one compression times the number of them; this interface
+ * compresses M messages of any sizes and either input
+ * type, each with its own block size and absolute bound or stored raw, in
+ * ONE persistent kernel launch.  Its CTAs take tiles of all messages from one
+ * atomic ticket counter; every message becomes a complete, independent zc
+ * stream (the format of zc_compress, raw streams with flag bit 0), and the
+ * streams are written back to back (each a multiple of 16 bytes) into one
+ * packed buffer.  d_msg_off (device, M + 1 u64) receives the start of every
+ * stream and, in d_msg_off[M], the packed length.  Nothing is read back to
+ * the host, so the launch can be captured in a CUDA graph (zc_graph_*). */
+#define ZC_RAW 0             /* zc_message.block: store the message verbatim */
+typedef struct {
+    const void* in;          /* compression: the message's values (device)    */
+    void* out;               /* decompression: where its values go (device)   */
+    uint64_t n;              /* elements                                      */
+    int dtype;               /* ZC_F32 or ZC_BF16: type of `in` (compression)
+                                or of `out` (decompression)                   */
+    int block;               /* 16, 32, 64 or 128, or ZC_RAW                  */
+    double eb_abs;           /* absolute error bound (unused for ZC_RAW)      */
+} zc_message;
+
+/* A batch plan: a descriptor table in the caller's device memory, built once
+ * at set-up time and launched any number of times. */
+typedef struct {
+    int n_msgs;
+    int tile_chunks;         /* compression tile: chunks of 2048 elements     */
+    int grid;                /* CTAs launched; 0 = one per tile               */
+    int decompress;          /* 0: compression plan, 1: decompression plan    */
+    uint64_t total_tiles;    /* tiles of all messages together                */
+    uint64_t total_chunks;   /* decompression: width-scan chunks              */
+    const void* d_table;     /* the descriptor table (device)                 */
+    void* d_packed;          /* the packed streams (device)                   */
+    size_t packed_cap;       /* bytes at d_packed                             */
+    uint64_t* d_msg_off;     /* M + 1 stream offsets (device)                 */
+} zc_batch;
+
+/* Device bytes of the descriptor table of a batch of n_msgs messages. */
+size_t zc_batch_table_bytes(int n_msgs);
+
+/* Largest packed length of the batch (every stream at its worst case);
+ * 0 for an invalid message. */
+size_t zc_batch_max_bytes(int n_msgs, const zc_message* h_msgs);
+
+/* Plan the compression of h_msgs[0 .. n_msgs) into d_packed (16-byte
+ * aligned).  tile_chunks: 4, 8, 16, or 0 for the current default
+ * (zc_set_tile_chunks); grid: CTAs to launch, 0 = one per tile.  Validates
+ * every message (ZC_ERR_ARG), checks that packed_cap holds at least every
+ * header and width array (ZC_ERR_CAPACITY; the payload is checked on the
+ * device), and copies the table to d_table with a synchronous cudaMemcpy. */
+int zc_plan_compress_batch(zc_batch* plan, int n_msgs, const zc_message* h_msgs, int tile_chunks,
+                           int grid, void* d_packed, size_t packed_cap, uint64_t* d_msg_off,
+                           void* d_table, size_t table_bytes);
+
+/* Launch a compression plan on s (one kernel).  Workspace: at least
+ * zc_workspace_bytes(sum of n, n_msgs). */
+int zc_compress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_stream_t s);
+
+/* Plan the decompression of a packed buffer: stream i starts at
+ * d_msg_off[i] (read on the device when the launch runs, so the offsets may
+ * come from a compression launch earlier on the same stream) and decodes into
+ * h_msgs[i].out as h_msgs[i].dtype; h_msgs[i].n must equal the stream's
+ * element count (ZC_ERR_FORMAT on the device otherwise).  Offsets that are
+ * not 16-byte aligned or lie outside packed_cap are format errors. */
+int zc_plan_decompress_batch(zc_batch* plan, int n_msgs, const zc_message* h_msgs,
+                             const void* d_packed, size_t packed_cap, const uint64_t* d_msg_off,
+                             void* d_table, size_t table_bytes);
+
+/* Launch a decompression plan on s (a width-scan and a decode kernel). */
+int zc_decompress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_stream_t s);
+
+/* Autotuner for batched compression.  Times zc_compress_batch on the given
+ * messages for every candidate tile size (4, 8, 16 chunks) and grid (1, 2 and
+ * 4 CTAs per SM, and one CTA per tile), and, with tune_block != 0, every
+ * block size (16 .. 128, applied to all non-raw messages).  Each candidate
+ * runs once untimed and `reps` times timed with CUDA events on s; its score
+ * is the median time plus, for link_gbs > 0, the time to send the packed
+ * bytes over a link of link_gbs GB/s (the end-to-end cost a compressed
+ * collective pays).  Synchronous (set-up time).  Writes up to max_points
+ * measured candidates to h_points (may be NULL), their number to *n_points
+ * (may be NULL) and the best one to *best; leaves d_table planned with the
+ * best candidate (call zc_plan_compress_batch again with best's settings to
+ * rebuild it elsewhere).  The buffers must fit every candidate:
+ * packed_cap >= zc_batch_max_bytes of the messages at the largest width. */
+typedef struct {
+    int block;               /* block size of the non-raw messages; 0 = as given */
+    int tile_chunks;
+    int grid;                /* 0 = one CTA per tile                           */
+    int status;              /* device status after the candidate's runs       */
+    float ms;                /* median compression time                        */
+    uint64_t packed_bytes;   /* packed length                                  */
+    double score_ms;         /* ms + packed_bytes / link                       */
+} zc_tune_point;
+
+int zc_autotune_batch(int n_msgs, const zc_message* h_msgs, int tune_block, double link_gbs,
+                      int reps, void* d_packed, size_t packed_cap, uint64_t* d_msg_off,
+                      void* d_table, size_t table_bytes, void* d_ws, size_t ws_bytes,
+                      zc_stream_t s, zc_tune_point* h_points, int max_points, int* n_points,
+                      zc_tune_point* best);
+
+/* ---- CUDA graphs of zc calls ----------------------------------------------
+ * Every zc launch function is asynchronous and reads nothing back, so a
+ * sequence of them can be recorded once and replayed with one launch.
+ * zc_graph_begin starts capturing s (a stream other than the legacy default
+ * stream); the zc calls that follow on s are recorded, not run; zc_graph_end
+ * stops the capture and instantiates the graph.  Make one ordinary call of
+ * each entry point before capturing it (first calls set kernel attributes),
+ * and build plans before the capture (planning copies synchronously). */
+typedef struct zc_graph_s* zc_graph;
+int zc_graph_begin(zc_stream_t s);
+int zc_graph_end(zc_stream_t s, zc_graph* g);
+int zc_graph_launch(zc_graph g, zc_stream_t s);
+void zc_graph_destroy(zc_graph g);
+
 /* Compression for callers that may not allocate device memory (the paper has
  * no counterpart to this entry point).  Code on a collective's progress path
  * must not call cudaMalloc, which synchronises the whole device and would

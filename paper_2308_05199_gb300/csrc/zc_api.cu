@@ -149,6 +149,17 @@ cudaError_t launch_scatter_any(int lg, int C, int dt, const Launch& P, const Sca
     }
 }
 
+cudaError_t launch_batch(int C, const Launch& P, unsigned grid, cudaStream_t s)
+{
+    switch (C) {
+    case 4: return launch_batch_c4(P, grid, s);
+    case 8: return launch_batch_c8(P, grid, s);
+    default: return launch_batch_c16(P, grid, s);
+    }
+}
+
+inline uint64_t elem_bytes(int dtype) { return dtype == ZC_F32 ? 4 : 2; }
+
 }  // namespace
 
 extern "C" {
@@ -489,6 +500,174 @@ int zc_scatter_pack(const void* d_in, int dtype, int P, const uint64_t* h_counts
     L.total_tiles = (unsigned)tile;
     L.urows = unit_rows(C);
     return cuda_status(launch_scatter_any(lg, C, dtype, L, SP, (unsigned)tile, (cudaStream_t)s));
+}
+
+size_t zc_batch_table_bytes(int n_msgs)
+{
+    return n_msgs > 0 ? sizeof(Item) * (size_t)n_msgs : 0;
+}
+
+size_t zc_batch_max_bytes(int n_msgs, const zc_message* h_msgs)
+{
+    if (n_msgs < 1 || h_msgs == nullptr) return 0;
+    size_t total = 0;
+    for (int i = 0; i < n_msgs; ++i) {
+        const zc_message& m = h_msgs[i];
+        const size_t b = m.block == ZC_RAW ? zc_raw_stream_bytes(m.n, m.dtype)
+                                           : zc_max_compressed_bytes(m.n, m.block);
+        if (b == 0) return 0;
+        total += b;
+    }
+    return total;
+}
+
+int zc_plan_compress_batch(zc_batch* plan, int n_msgs, const zc_message* h_msgs, int tile_chunks,
+                           int grid, void* d_packed, size_t packed_cap, uint64_t* d_msg_off,
+                           void* d_table, size_t table_bytes)
+{
+    if (plan == nullptr || n_msgs < 1 || h_msgs == nullptr || grid < 0 || d_packed == nullptr ||
+        !aligned(d_packed, 16) || d_msg_off == nullptr || !aligned(d_msg_off, 8) ||
+        d_table == nullptr || !aligned(d_table, 16) || table_bytes < zc_batch_table_bytes(n_msgs))
+        return ZC_ERR_ARG;
+    const int C = tile_chunks ? tile_chunks : g_chunks;
+    if (C != 4 && C != 8 && C != 16) return ZC_ERR_ARG;
+    std::vector<Item> items((size_t)n_msgs);
+    uint64_t tile = 0, min_cap = 0;
+    for (int i = 0; i < n_msgs; ++i) {
+        const zc_message& m = h_msgs[i];
+        if (!dtype_ok(m.dtype) || (m.n > 0 && m.in == nullptr) || !aligned(m.in, elem_bytes(m.dtype)))
+            return ZC_ERR_ARG;
+        Item& it = items[(size_t)i];
+        std::memset(&it, 0, sizeof(it));
+        if (m.block == ZC_RAW) {
+            it.log2L = -1;
+            min_cap += 32 + pad16(m.n * elem_bytes(m.dtype));
+        } else {
+            it.log2L = log2_block(m.block);
+            if (it.log2L < 0) return ZC_ERR_ARG;
+            const uint64_t nb = (m.n + (1ull << it.log2L) - 1) >> it.log2L;
+            if (nb > 0xffffffffull) return ZC_ERR_ARG;
+            const int st = qparams(m.eb_abs, &it.eb, &it.two_eb, &it.inv);
+            if (st) return st;
+            min_cap += 32 + pad16(nb);
+        }
+        it.x = m.in;
+        it.out = (uint8_t*)d_packed;
+        it.out_cap = packed_cap;
+        it.n = m.n;
+        it.tile_begin = (unsigned)tile;
+        it.ntiles = (unsigned)tiles_for(m.n, unit_rows(C));
+        it.x_dtype = m.dtype;
+        it.out_dtype = m.dtype;
+        tile += it.ntiles;
+        if (tile > 0x7fffffffull) return ZC_ERR_ARG;
+    }
+    if (packed_cap < min_cap) return ZC_ERR_CAPACITY;
+    if (cudaMemcpy(d_table, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return ZC_ERR_CUDA;
+    std::memset(plan, 0, sizeof(*plan));
+    plan->n_msgs = n_msgs;
+    plan->tile_chunks = C;
+    plan->grid = grid;
+    plan->decompress = 0;
+    plan->total_tiles = tile;
+    plan->d_table = d_table;
+    plan->d_packed = d_packed;
+    plan->packed_cap = packed_cap;
+    plan->d_msg_off = d_msg_off;
+    return ZC_OK;
+}
+
+int zc_compress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_stream_t s)
+{
+    if (plan == nullptr || plan->d_table == nullptr || plan->n_msgs < 1 || plan->decompress != 0)
+        return ZC_ERR_ARG;
+    const int C = plan->tile_chunks;
+    if (C != 4 && C != 8 && C != 16) return ZC_ERR_ARG;
+    WsView w;
+    const int st = ws_view(d_ws, ws_bytes, w);
+    if (st) return st;
+    if (plan->total_tiles > w.cap || (uint64_t)plan->n_msgs + 1 > w.cap) return ZC_ERR_WORKSPACE;
+    Launch P = base_launch(w);
+    P.items = (const Item*)plan->d_table;
+    P.n_items = (unsigned)plan->n_msgs;
+    P.packed = 1;
+    P.seg_off = (unsigned long long*)plan->d_msg_off;
+    P.urows = unit_rows(C);
+    P.total_tiles = (unsigned)plan->total_tiles;
+    uint64_t grid = plan->grid > 0 ? (uint64_t)plan->grid : plan->total_tiles;
+    if (grid > plan->total_tiles) grid = plan->total_tiles;
+    return cuda_status(launch_batch(C, P, (unsigned)grid, (cudaStream_t)s));
+}
+
+int zc_plan_decompress_batch(zc_batch* plan, int n_msgs, const zc_message* h_msgs,
+                             const void* d_packed, size_t packed_cap, const uint64_t* d_msg_off,
+                             void* d_table, size_t table_bytes)
+{
+    if (plan == nullptr || n_msgs < 1 || h_msgs == nullptr || d_packed == nullptr ||
+        !aligned(d_packed, 16) || d_msg_off == nullptr || !aligned(d_msg_off, 8) ||
+        d_table == nullptr || !aligned(d_table, 16) || table_bytes < zc_batch_table_bytes(n_msgs))
+        return ZC_ERR_ARG;
+    std::vector<Item> items((size_t)n_msgs);
+    uint64_t tile = 0, chunk = 0;
+    for (int i = 0; i < n_msgs; ++i) {
+        const zc_message& m = h_msgs[i];
+        if (!dtype_ok(m.dtype) || (m.n > 0 && m.out == nullptr) ||
+            !aligned(m.out, elem_bytes(m.dtype)))
+            return ZC_ERR_ARG;
+        Item& it = items[(size_t)i];
+        std::memset(&it, 0, sizeof(it));
+        it.cin = (const uint8_t*)d_packed;  // the kernels read the stream's start from d_msg_off
+        it.raw_out = m.out;
+        it.n = m.n;
+        it.tile_begin = (unsigned)tile;
+        it.ntiles = (unsigned)tiles_for(m.n, DEC_U);
+        it.chunk_begin = (unsigned)chunk;
+        it.nchunks = (unsigned)chunks_for(it.ntiles);
+        it.x_dtype = m.dtype;
+        it.out_dtype = m.dtype;
+        tile += it.ntiles;
+        chunk += it.nchunks;
+        if (tile > 0x7fffffffull) return ZC_ERR_ARG;
+    }
+    if (cudaMemcpy(d_table, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return ZC_ERR_CUDA;
+    std::memset(plan, 0, sizeof(*plan));
+    plan->n_msgs = n_msgs;
+    plan->tile_chunks = 0;
+    plan->grid = 0;
+    plan->decompress = 1;
+    plan->total_tiles = tile;
+    plan->total_chunks = chunk;
+    plan->d_table = d_table;
+    plan->d_packed = const_cast<void*>(d_packed);
+    plan->packed_cap = packed_cap;
+    plan->d_msg_off = const_cast<uint64_t*>(d_msg_off);
+    return ZC_OK;
+}
+
+int zc_decompress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_stream_t s)
+{
+    if (plan == nullptr || plan->d_table == nullptr || plan->n_msgs < 1 || plan->decompress != 1)
+        return ZC_ERR_ARG;
+    WsView w;
+    const int st = ws_view(d_ws, ws_bytes, w);
+    if (st) return st;
+    if (plan->total_tiles * NWARPS > w.cap || plan->total_chunks > w.cap) return ZC_ERR_WORKSPACE;
+    Launch P = base_launch(w);
+    P.items = (const Item*)plan->d_table;
+    P.n_items = (unsigned)plan->n_msgs;
+    P.urows = DEC_U;
+    P.in_base = (const uint8_t*)plan->d_packed;
+    P.in_off = (const unsigned long long*)plan->d_msg_off;
+    P.in_cap = plan->packed_cap;
+    P.total_tiles = (unsigned)plan->total_chunks;
+    if (launch_wscan(P, (unsigned)plan->total_chunks, (cudaStream_t)s) != cudaSuccess)
+        return ZC_ERR_CUDA;
+    P.total_tiles = (unsigned)plan->total_tiles;
+    return cuda_status(launch_decompress(P, (unsigned)plan->total_tiles, (cudaStream_t)s));
 }
 
 int zc_get_device_status(const void* d_ws, zc_stream_t s, int* status, uint64_t* detail)

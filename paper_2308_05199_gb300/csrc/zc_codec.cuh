@@ -52,6 +52,7 @@ struct Item {
     unsigned tile_begin, ntiles;    // tiles of this launch's geometry
     unsigned chunk_begin, nchunks;  // width-scan chunks
     int x_dtype, out_dtype;
+    int log2L;                // batched compression: block size, or -1 for a raw stream
 };
 
 struct Launch {
@@ -68,6 +69,11 @@ struct Launch {
     int eb_from_ctl;                  // relative bound resolved into ctl
     int packed;
     WaitCfg wc;
+    // batched decompression: item i's stream sits at in_base + in_off[i] (in_off
+    // written by an earlier launch; in_cap bytes at in_base)
+    const uint8_t* in_base;
+    const unsigned long long* in_off;
+    unsigned long long in_cap;
 };
 
 struct Smem {
@@ -571,6 +577,35 @@ __device__ __forceinline__ void warp_copy(uint8_t* dst, const uint8_t* src, int 
     }
 }
 
+// Packed mode (one chain through many streams): the first tile of a stream
+// publishes where the stream starts (its exclusive value ex), the stream's
+// other tiles wait for that.  Outside packed mode a stream starts at 0.
+// Returns false (status set) when the wait runs out.  Run by the whole CTA.
+__device__ __forceinline__ bool packed_start(const Launch& P, bool first, unsigned item_idx,
+                                             unsigned long long ex, unsigned g, Smem& sm,
+                                             unsigned long long& start)
+{
+    start = 0ull;
+    if (!P.packed) return true;
+    if (first) {
+        start = ex;
+        if (threadIdx.x == 0) {
+            st_relaxed(P.seg_off + item_idx, ex);
+            st_release(P.seg_flag + item_idx, ((unsigned long long)sm.E << 32) | 1ull);
+        }
+        return true;
+    }
+    if (threadIdx.x == 0) {
+        sm.abort = !wait_flag(P.seg_flag + item_idx, sm.E, P.wc.limit_ns);
+        if (sm.abort) fail(P.ctl, ZC_ERR_TIMEOUT, g);
+        else sm.start = ld_relaxed(P.seg_off + item_idx);
+    }
+    __syncthreads();
+    if (sm.abort) return false;
+    start = sm.start;
+    return true;
+}
+
 // One encoder tile: NWARPS warp units of U rows, each warp encoding its unit
 // into its own shared-memory segment.  HAS_CIN: decode `it.cin` first (same
 // block size, unit offsets from k_wscan) and add the local chunk.  The FP32
@@ -707,25 +742,7 @@ __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, uns
     bool to = false;
     const unsigned long long ex = lookback_cta(P.chB, g, g0, agg, last, E, P.wc, ctl, to, sm.lb);
     unsigned long long start = 0ull;
-    if (P.packed && !to) {
-        if (first) {
-            start = ex;
-            if (tid == 0) {
-                st_relaxed(P.seg_off + item_idx, ex);
-                st_release(P.seg_flag + item_idx, ((unsigned long long)E << 32) | 1ull);
-            }
-        } else {
-            if (tid == 0) {
-                sm.abort = !wait_flag(P.seg_flag + item_idx, E, P.wc.limit_ns);
-                if (sm.abort) fail(ctl, ZC_ERR_TIMEOUT, g);
-                else sm.start = ld_relaxed(P.seg_off + item_idx);
-            }
-            __syncthreads();
-            if (sm.abort) to = true;
-            else start = sm.start;
-        }
-    }
-    if (to) return;
+    if (to || !packed_start(P, first, item_idx, ex, g, sm, start)) return;
     const unsigned long long base = ex + (first ? 32ull + wbytes : 0ull);
     const unsigned long long cap = it.out_cap;
     uint8_t* const out = it.out;
@@ -896,6 +913,123 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_reduce(const Launch P)
     });
 }
 
+// ---- batched compression -----------------------------------------------------
+
+// One tile of a raw (verbatim) stream: the item's elements of this tile go
+// unchanged after the 32-byte header (flag bit 0 set, no width bytes).  Same
+// tile geometry, look-back and stream-start protocol as tile_encode, so raw
+// and encoded streams mix in one packed launch.
+template <int U>
+__device__ __forceinline__ void tile_raw(const Launch& P, const Item& it, unsigned item_idx,
+                                         unsigned tile_in_item, unsigned g, Smem& sm)
+{
+    constexpr unsigned long long TE = (unsigned long long)NWARPS * U * 32;
+    const int tid = threadIdx.x;
+    const unsigned long long n = it.n;
+    const unsigned long long es = it.x_dtype == ZC_F32 ? 4ull : 2ull;
+    const unsigned long long te0 = (unsigned long long)tile_in_item * TE;
+    const unsigned long long cnt = te0 < n ? min(n - te0, TE) : 0ull;
+    const unsigned long long bytes = cnt * es;
+    const bool first = tile_in_item == 0;
+    const bool last = tile_in_item + 1 == it.ntiles;
+    const unsigned long long agg = bytes + (first ? 32ull : 0ull);
+    const unsigned g0 = P.packed ? 0u : g - tile_in_item;
+    bool to = false;
+    const unsigned long long ex = lookback_cta(P.chB, g, g0, agg, last, sm.E, P.wc, P.ctl, to, sm.lb);
+    unsigned long long start = 0ull;
+    if (to || !packed_start(P, first, item_idx, ex, g, sm, start)) return;
+    const unsigned long long base = ex + (first ? 32ull : 0ull);  // 16-byte aligned
+    const unsigned long long cap = it.out_cap;
+    uint8_t* const out = it.out;
+    if (base + bytes <= cap) {
+        const uint8_t* src = (const uint8_t*)it.x + te0 * es;
+        if (((uintptr_t)src & 15u) == 0) {
+            const unsigned long long nv = bytes / 16;
+            for (unsigned long long i = tid; i < nv; i += NTHREADS)
+                ((uint4*)(out + base))[i] = __ldg((const uint4*)src + i);
+            for (unsigned long long i = nv * 16 + tid * 2; i < bytes; i += 2 * NTHREADS)
+                *(uint16_t*)(out + base + i) = __ldg((const unsigned short*)(src + i));
+        } else {
+            // the input is only element-aligned: 2-byte copies
+            for (unsigned long long i = (unsigned long long)tid * 2; i < bytes; i += 2 * NTHREADS)
+                *(uint16_t*)(out + base + i) = __ldg((const unsigned short*)(src + i));
+        }
+    } else if (tid == 0) {
+        fail(P.ctl, ZC_ERR_CAPACITY, g);
+    }
+    if (last) {
+        const unsigned long long end = ex + agg;
+        const unsigned long long total = ceil16(end);
+        const unsigned long long pl = n * es;
+        for (unsigned long long p = end + tid; p < total; p += NTHREADS)
+            if (p < cap) out[p] = 0;
+        if (tid < 8 && start + 32 <= cap) {
+            uint32_t v = 0;
+            switch (tid) {
+            case 0: v = 0x3176435au; break;  // "ZCv1"
+            case 1: v = (uint32_t)it.x_dtype | (5u << 8) | (1u << 16); break;  // raw flag
+            case 2: v = (uint32_t)n; break;
+            case 3: v = (uint32_t)(n >> 32); break;
+            case 4: v = 0u; break;  // eb: none
+            case 5: v = 0u; break;  // no blocks
+            case 6: v = (uint32_t)pl; break;
+            default: v = (uint32_t)(pl >> 32); break;
+            }
+            ((uint32_t*)(out + start))[tid] = v;
+        }
+        if (tid == 0) {
+            if (it.out_bytes) *it.out_bytes = total - start;
+            if (P.packed) P.seg_off[item_idx + 1] = total;
+        }
+    }
+}
+
+// Batched compression: every item is a stream of its own block size and
+// input type (or raw), all packed back to back by one chain; the CTAs take
+// tiles of all items from one ticket counter, so one launch of a few CTAs per
+// SM covers any mix of message sizes.
+template <int U>
+__global__ void __launch_bounds__(NTHREADS, 4) k_batch(const Launch P)
+{
+    __shared__ Smem sm;
+    extern __shared__ __align__(16) uint8_t dsm[];
+    tile_loop(P, ItemsSrc{P}, sm, [&](const Item& it, unsigned idx, unsigned t, unsigned g) {
+        const bool f32 = it.x_dtype == ZC_F32;
+        switch (it.log2L) {
+        case 4:
+            if (f32) tile_encode<4, U, false, float>(P, it, idx, t, g, sm, dsm);
+            else tile_encode<4, U, false, uint16_t>(P, it, idx, t, g, sm, dsm);
+            break;
+        case 5:
+            if (f32) tile_encode<5, U, false, float>(P, it, idx, t, g, sm, dsm);
+            else tile_encode<5, U, false, uint16_t>(P, it, idx, t, g, sm, dsm);
+            break;
+        case 6:
+            if (f32) tile_encode<6, U, false, float>(P, it, idx, t, g, sm, dsm);
+            else tile_encode<6, U, false, uint16_t>(P, it, idx, t, g, sm, dsm);
+            break;
+        case 7:
+            if (f32) tile_encode<7, U, false, float>(P, it, idx, t, g, sm, dsm);
+            else tile_encode<7, U, false, uint16_t>(P, it, idx, t, g, sm, dsm);
+            break;
+        default: tile_raw<U>(P, it, idx, t, g, sm); break;
+        }
+    });
+}
+
+// Batched decompression: item idx's stream, from a packed buffer written by an
+// earlier launch.  A start or an end outside the buffer, or a start that is
+// not 16-byte aligned, leaves a stream too short for its header (reported as
+// a format error by the decoder).
+__device__ __forceinline__ void resolve_packed(const Launch& P, Item& it, unsigned idx)
+{
+    if (P.in_off == nullptr) return;
+    const unsigned long long a = P.in_off[idx], b = P.in_off[idx + 1];
+    const bool ok = (a & 15ull) == 0 && a <= b && b <= P.in_cap;
+    it.cin = P.in_base + (ok ? a : 0ull);
+    it.cin_cap = ok ? b - a : 0ull;
+}
+
 #ifdef ZC_DECODE_KERNELS  // defined by the one translation unit that launches them
 
 // ---- width scan: payload offset of every decode tile --------------------------
@@ -935,7 +1069,8 @@ __global__ void __launch_bounds__(NTHREADS) k_wscan(const Launch P)
         __syncthreads();
         const unsigned c = sm.ticket;
         if (c >= P.total_tiles) break;
-        const Item it = P.items != nullptr ? P.items[sm.item] : P.one;
+        Item it = P.items != nullptr ? P.items[sm.item] : P.one;
+        resolve_packed(P, it, sm.item);
         if (it.cin == nullptr) continue;  // nothing received: no offsets needed
         const unsigned chunk = c - it.chunk_begin;
         float eb_in;
@@ -1073,7 +1208,8 @@ __global__ void __launch_bounds__(NTHREADS) k_decompress(const Launch P)
         }
         idx = lo;
     }
-    const Item it = P.items != nullptr ? P.items[idx] : P.one;
+    Item it = P.items != nullptr ? P.items[idx] : P.one;
+    resolve_packed(P, it, idx);
     const unsigned t = tile - it.tile_begin;
     const int warp = threadIdx.x >> 5;
     const unsigned long long ue0 = ((unsigned long long)t * NWARPS + warp) * (DEC_U * 32);

@@ -270,26 +270,35 @@ struct WaitCfg {
     long long withhold;  // tile that never publishes (test hook), -1 = none
 };
 
-// Scratch of the CTA-wide look-back.
+// Scratch of the look-back.
 struct LbSmem {
-    Xf wx[NWARPS];
-    int wp[NWARPS];
-    unsigned long long pv;
+    unsigned long long excl;
+    int timed_out;
 };
 
-// Run by the whole CTA.  g: this tile's slot; g0: first slot of its chain
-// (whose exclusive value is 0).  Publishes g's aggregate, then inspects the
-// NTHREADS preceding slots at once (one flag per thread), waits until all of
-// them have published, composes the aggregates after the nearest inclusive
-// prefix, and repeats further back if there is none.  Publishes g's inclusive
-// prefix and returns g's exclusive value (the same in every thread).  If the
-// wait runs out, records ZC_ERR_TIMEOUT, sets timed_out and returns 0.
+constexpr int LB_PER_LANE = 8;                 // predecessors inspected per lane
+constexpr int LB_WINDOW = 32 * LB_PER_LANE;    // predecessors per look-back round
+
+__device__ __forceinline__ bool flag_valid(unsigned long long f, unsigned E)
+{
+    return (unsigned)(f >> 32) == E && ((f >> 30) & 3u) != 0u;
+}
+
+// Run by the whole CTA; only warp 0 polls (the other warps wait at a
+// barrier and issue nothing).  g: this tile's slot; g0: first slot of its
+// chain (whose exclusive value is 0).  Publishes g's aggregate, then inspects
+// the LB_WINDOW preceding slots (LB_PER_LANE consecutive slots per lane),
+// waits until all of them have published, composes the aggregates after the
+// nearest inclusive prefix, and repeats further back if there is none.
+// Publishes g's inclusive prefix and returns g's exclusive value (the same in
+// every thread).  If the wait runs out, records ZC_ERR_TIMEOUT, sets
+// timed_out and returns 0.
 __device__ __forceinline__ unsigned long long lookback_cta(const Chain& ch, unsigned g,
                                                            unsigned g0, unsigned long long agg,
                                                            bool h, unsigned E, const WaitCfg& wc,
                                                            Ctl* ctl, bool& timed_out, LbSmem& ls)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const bool publish = (long long)g != wc.withhold;
     const Xf self{agg, 0ull, h};
     timed_out = false;
@@ -301,79 +310,109 @@ __device__ __forceinline__ unsigned long long lookback_cta(const Chain& ch, unsi
         }
         return 0ull;
     }
-    if (tid == 0 && publish) {
-        if (agg > AGG_INLINE_MAX) st_relaxed(ch.aggw + g, agg);
-        st_release(ch.flag + g, make_flag(E, ST_AGG, h, agg));
-    }
-    Xf acc = xf_id();
-    long long hi = (long long)g - 1;
-    unsigned long long excl = 0ull;
-    const unsigned long long t0 = globaltimer();
-    while (true) {
-        const long long j = hi - (NTHREADS - 1) + tid;
-        const bool virt = j < (long long)g0;
-        unsigned long long f = 0ull;
-        bool valid = virt;
-        if (!virt) {
-            f = ld_acquire(ch.flag + j);
-            valid = (unsigned)(f >> 32) == E && ((f >> 30) & 3u) != 0u;
+    if (tid < 32) {
+        if (tid == 0 && publish) {
+            if (agg > AGG_INLINE_MAX) st_relaxed(ch.aggw + g, agg);
+            st_release(ch.flag + g, make_flag(E, ST_AGG, h, agg));
         }
-        unsigned ns = 32;
-        while (!__syncthreads_and(valid)) {
-            // the decision to give up is taken by the whole CTA at once
-            if (__syncthreads_or(tid == 0 && globaltimer() - t0 > wc.limit_ns)) {
-                timed_out = true;
+        Xf acc = xf_id();
+        long long hi = (long long)g - 1;
+        unsigned long long excl = 0ull;
+        bool expired = false;
+        const unsigned long long t0 = globaltimer();
+        while (true) {
+            // slots j0 .. j0 + LB_PER_LANE - 1 of this lane, oldest first
+            const long long j0 = hi - (LB_WINDOW - 1) + (long long)lane * LB_PER_LANE;
+            unsigned long long f[LB_PER_LANE];
+            unsigned valid = 0;
+#pragma unroll
+            for (int i = 0; i < LB_PER_LANE; ++i) {
+                const long long j = j0 + i;
+                if (j < (long long)g0) {
+                    f[i] = 0ull;
+                    valid |= 1u << i;
+                } else {
+                    f[i] = ld_acquire(ch.flag + j);
+                    if (flag_valid(f[i], E)) valid |= 1u << i;
+                }
+            }
+            unsigned ns = 32;
+            while (!__all_sync(FULL, valid == (1u << LB_PER_LANE) - 1u)) {
+                expired = __any_sync(FULL, globaltimer() - t0 > wc.limit_ns);
+                if (expired) break;
+                __nanosleep(ns);
+                ns = ns < 256 ? ns * 2 : ns;
+#pragma unroll
+                for (int i = 0; i < LB_PER_LANE; ++i) {
+                    if (!((valid >> i) & 1u)) {
+                        f[i] = ld_acquire(ch.flag + (j0 + i));
+                        if (flag_valid(f[i], E)) valid |= 1u << i;
+                    }
+                }
+            }
+            if (expired) {
+                if (lane == 0) fail(ctl, ZC_ERR_TIMEOUT, g);
+                excl = 0ull;
                 break;
             }
-            __nanosleep(ns);
-            ns = ns < 256 ? ns * 2 : ns;
-            if (!valid) {
-                f = ld_acquire(ch.flag + j);
-                valid = (unsigned)(f >> 32) == E && ((f >> 30) & 3u) != 0u;
+            // this lane's newest prefix slot (virtual slots before g0 count as prefix 0)
+            int pi = -1;
+#pragma unroll
+            for (int i = 0; i < LB_PER_LANE; ++i) {
+                const bool is_pref = (j0 + i < (long long)g0) || ((f[i] >> 30) & 3u) == ST_PREFIX;
+                if (is_pref) pi = i;
             }
-        }
-        if (timed_out) {
-            if (tid == 0) fail(ctl, ZC_ERR_TIMEOUT, g);
-            excl = 0ull;
-            break;
-        }
-        const bool is_pref = virt || ((f >> 30) & 3u) == ST_PREFIX;
-        const unsigned pm = __ballot_sync(FULL, is_pref);
-        if (lane == 0) ls.wp[warp] = pm ? warp * 32 + 31 - __clz(pm) : -1;
-        Xf t = xf_id();
-        if (!virt) {
-            t.h = (f >> 29) & 1u;
-            t.a = ((f >> 28) & 1u) ? ld_relaxed(ch.aggw + j) : (f & AGG_INLINE_MAX);
-        }
-        __syncthreads();
-        int p = -1;
+            const unsigned pm = __ballot_sync(FULL, pi >= 0);
+            const int pl = pm ? 31 - __clz(pm) : -1;  // lane holding the newest prefix
+            // this lane's composed transform of its slots after the newest prefix
+            Xf t = xf_id();
+            if (lane >= pl) {
 #pragma unroll
-        for (int w = 0; w < NWARPS; ++w) p = ls.wp[w] > p ? ls.wp[w] : p;
-        if (tid <= p) t = xf_id();
+                for (int i = 0; i < LB_PER_LANE; ++i) {
+                    const long long j = j0 + i;
+                    if (j >= (long long)g0 && (lane > pl || i > pi)) {
+                        Xf x;
+                        x.h = (f[i] >> 29) & 1u;
+                        x.a = ((f[i] >> 28) & 1u) ? ld_relaxed(ch.aggw + j) : (f[i] & AGG_INLINE_MAX);
+                        x.b = 0ull;
+                        t = xf_compose(t, x);
+                    }
+                }
+            }
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const Xf o = xf_shfl_up(t, off);
-            if (lane >= off) t = xf_compose(o, t);
+            for (int off = 1; off < 32; off <<= 1) {
+                const Xf o = xf_shfl_up(t, off);
+                if (lane >= off) t = xf_compose(o, t);
+            }
+            acc = xf_compose(xf_shfl(t, 31), acc);
+            if (pl >= 0) {
+                unsigned long long pv = 0ull;
+                if (lane == pl && j0 + pi >= (long long)g0) pv = ld_relaxed(ch.pref + (j0 + pi));
+                pv = __shfl_sync(FULL, pv, pl);
+                excl = xf_apply(acc, pv);
+                break;
+            }
+            hi -= LB_WINDOW;
         }
-        if (lane == 31) ls.wx[warp] = t;
-        if (tid == p) ls.pv = virt ? 0ull : ld_relaxed(ch.pref + j);
-        __syncthreads();
-        Xf w = xf_id();
-#pragma unroll
-        for (int k = 0; k < NWARPS; ++k) w = xf_compose(w, ls.wx[k]);
-        acc = xf_compose(w, acc);
-        if (p >= 0) {
-            excl = xf_apply(acc, ls.pv);
-            break;
+        if (lane == 0) {
+            if (publish && !expired) {
+                st_relaxed(ch.pref + g, xf_apply(self, excl));
+                st_release(ch.flag + g, make_flag(E, ST_PREFIX, h, agg));
+            } else if (publish) {
+                // keep the chain moving: successors read a (wrong) prefix, the
+                // status word already says the result is unusable
+                st_relaxed(ch.pref + g, xf_apply(self, 0ull));
+                st_release(ch.flag + g, make_flag(E, ST_PREFIX, h, agg));
+            }
+            ls.excl = excl;
+            ls.timed_out = expired;
         }
-        hi -= NTHREADS;
-        __syncthreads();  // ls is rewritten by the next window
     }
-    if (tid == 0 && publish) {
-        st_relaxed(ch.pref + g, xf_apply(self, excl));
-        st_release(ch.flag + g, make_flag(E, ST_PREFIX, h, agg));
-    }
-    return excl;
+    __syncthreads();
+    timed_out = ls.timed_out != 0;
+    const unsigned long long ex = ls.excl;
+    __syncthreads();  // ls may be reused right after
+    return ex;
 }
 
 // Bounded wait for a value published with st_release on `flag` (epoch E in

@@ -20,6 +20,21 @@ cudaError_t launch_scatter_l16(int S, int x_dtype, const Launch& P, const Scatte
 cudaError_t launch_scatter_l32(int S, int x_dtype, const Launch& P, const ScatterParams& SP, unsigned grid, cudaStream_t s);
 cudaError_t launch_scatter_l64(int S, int x_dtype, const Launch& P, const ScatterParams& SP, unsigned grid, cudaStream_t s);
 cudaError_t launch_scatter_l128(int S, int x_dtype, const Launch& P, const ScatterParams& SP, unsigned grid, cudaStream_t s);
+// Batched compression (one translation unit per tile size).
+cudaError_t launch_batch_c4(const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_batch_c8(const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_batch_c16(const Launch& P, unsigned grid, cudaStream_t s);
+
+template <int U>
+cudaError_t launch_batch_u(const Launch& P, unsigned grid, cudaStream_t s)
+{
+    static const cudaError_t e = cudaFuncSetAttribute(
+        k_batch<U>, cudaFuncAttributeMaxDynamicSharedMemorySize, enc_smem_bytes(U));
+    if (e != cudaSuccess) return e;
+    k_batch<U><<<grid, NTHREADS, enc_smem_bytes(U), s>>>(P);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wscan(const Launch& P, unsigned grid, cudaStream_t s);
 cudaError_t launch_decompress(const Launch& P, unsigned grid, cudaStream_t s);
 

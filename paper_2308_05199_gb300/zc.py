@@ -48,6 +48,31 @@ class ZcPlan(ctypes.Structure):
                 ("total_chunks", ctypes.c_uint64), ("d_table", ctypes.c_void_p)]
 
 
+RAW = 0  # zc_message.block: store the message verbatim
+
+
+class ZcMessage(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("dtype", ctypes.c_int), ("block", ctypes.c_int), ("eb_abs", ctypes.c_double)]
+
+
+class ZcBatch(ctypes.Structure):
+    _fields_ = [("n_msgs", ctypes.c_int), ("tile_chunks", ctypes.c_int), ("grid", ctypes.c_int),
+                ("decompress", ctypes.c_int), ("total_tiles", ctypes.c_uint64),
+                ("total_chunks", ctypes.c_uint64), ("d_table", ctypes.c_void_p),
+                ("d_packed", ctypes.c_void_p), ("packed_cap", ctypes.c_size_t),
+                ("d_msg_off", ctypes.c_void_p)]
+
+
+class ZcTunePoint(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int), ("tile_chunks", ctypes.c_int), ("grid", ctypes.c_int),
+                ("status", ctypes.c_int), ("ms", ctypes.c_float),
+                ("packed_bytes", ctypes.c_uint64), ("score_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -85,6 +110,21 @@ def _declare(L):
         "zc_reduce_step_batch": (i32, [c.POINTER(ZcPlan), vp, sz, vp]),
         "zc_scatter_pack": (i32, [vp, i32, i32, vp, vp, i32, dbl, i32, vp, sz, vp, vp, sz, vp]),
         "zc_compress_noalloc": (i32, [vp, u64, i32, i32, dbl, i32, vp, sz, vp, vp, vp]),
+        "zc_batch_table_bytes": (sz, [i32]),
+        "zc_batch_max_bytes": (sz, [i32, c.POINTER(ZcMessage)]),
+        "zc_plan_compress_batch": (i32, [c.POINTER(ZcBatch), i32, c.POINTER(ZcMessage), i32, i32,
+                                         vp, sz, vp, vp, sz]),
+        "zc_compress_batch": (i32, [c.POINTER(ZcBatch), vp, sz, vp]),
+        "zc_plan_decompress_batch": (i32, [c.POINTER(ZcBatch), i32, c.POINTER(ZcMessage), vp, sz,
+                                           vp, vp, sz]),
+        "zc_decompress_batch": (i32, [c.POINTER(ZcBatch), vp, sz, vp]),
+        "zc_autotune_batch": (i32, [i32, c.POINTER(ZcMessage), i32, dbl, i32, vp, sz, vp, vp, sz,
+                                    vp, sz, vp, c.POINTER(ZcTunePoint), i32, c.POINTER(i32),
+                                    c.POINTER(ZcTunePoint)]),
+        "zc_graph_begin": (i32, [vp]),
+        "zc_graph_end": (i32, [vp, c.POINTER(vp)]),
+        "zc_graph_launch": (i32, [vp, vp]),
+        "zc_graph_destroy": (None, [vp]),
         "zc_get_device_status": (i32, [vp, vp, c.POINTER(c.c_int), c.POINTER(u64)]),
         "zc_clear_device_status": (i32, [vp, vp]),
         "zc_set_wait_limit_ns": (None, [u64]),
@@ -102,7 +142,10 @@ def exported_names():
     return ["zc_max_compressed_bytes", "zc_raw_stream_bytes", "zc_workspace_bytes",
             "zc_workspace_init", "zc_minmax", "zc_compress", "zc_decompress", "zc_reduce_step",
             "zc_plan_table_bytes", "zc_plan_reduce", "zc_reduce_step_batch", "zc_scatter_pack",
-            "zc_compress_noalloc",
+            "zc_compress_noalloc", "zc_batch_table_bytes", "zc_batch_max_bytes",
+            "zc_plan_compress_batch", "zc_compress_batch", "zc_plan_decompress_batch",
+            "zc_decompress_batch", "zc_autotune_batch", "zc_graph_begin", "zc_graph_end",
+            "zc_graph_launch", "zc_graph_destroy",
             "zc_get_device_status", "zc_clear_device_status", "zc_set_wait_limit_ns",
             "zc_debug_withhold_tile", "zc_set_tile_chunks", "zc_version"]
 
@@ -193,6 +236,58 @@ def zc_compress_noalloc(d_in, n, dtype, eb_mode, eb_value, block, d_out, out_cap
 
 
 NOALLOC_MAX_N = 1 << 24
+
+
+def zc_batch_table_bytes(n_msgs: int) -> int:
+    return lib().zc_batch_table_bytes(n_msgs)
+
+
+def zc_batch_max_bytes(n_msgs: int, h_msgs) -> int:
+    return lib().zc_batch_max_bytes(n_msgs, h_msgs)
+
+
+def zc_plan_compress_batch(plan, n_msgs, h_msgs, tile_chunks, grid, d_packed, packed_cap,
+                           d_msg_off, d_table, table_bytes) -> int:
+    return lib().zc_plan_compress_batch(ctypes.byref(plan), n_msgs, h_msgs, tile_chunks, grid,
+                                        d_packed, packed_cap, d_msg_off, d_table, table_bytes)
+
+
+def zc_compress_batch(plan, d_ws, ws_bytes, stream) -> int:
+    return lib().zc_compress_batch(ctypes.byref(plan), d_ws, ws_bytes, stream)
+
+
+def zc_plan_decompress_batch(plan, n_msgs, h_msgs, d_packed, packed_cap, d_msg_off, d_table,
+                             table_bytes) -> int:
+    return lib().zc_plan_decompress_batch(ctypes.byref(plan), n_msgs, h_msgs, d_packed,
+                                          packed_cap, d_msg_off, d_table, table_bytes)
+
+
+def zc_decompress_batch(plan, d_ws, ws_bytes, stream) -> int:
+    return lib().zc_decompress_batch(ctypes.byref(plan), d_ws, ws_bytes, stream)
+
+
+def zc_autotune_batch(n_msgs, h_msgs, tune_block, link_gbs, reps, d_packed, packed_cap,
+                      d_msg_off, d_table, table_bytes, d_ws, ws_bytes, stream, h_points,
+                      max_points, n_points, best) -> int:
+    return lib().zc_autotune_batch(n_msgs, h_msgs, tune_block, link_gbs, reps, d_packed,
+                                   packed_cap, d_msg_off, d_table, table_bytes, d_ws, ws_bytes,
+                                   stream, h_points, max_points, n_points, best)
+
+
+def zc_graph_begin(stream) -> int:
+    return lib().zc_graph_begin(stream)
+
+
+def zc_graph_end(stream, graph_out) -> int:
+    return lib().zc_graph_end(stream, graph_out)
+
+
+def zc_graph_launch(graph, stream) -> int:
+    return lib().zc_graph_launch(graph, stream)
+
+
+def zc_graph_destroy(graph):
+    lib().zc_graph_destroy(graph)
 
 
 def zc_get_device_status(d_ws, stream):
@@ -318,3 +413,165 @@ def stream_bytes(out: torch.Tensor, out_bytes: torch.Tensor) -> bytes:
     """Copy a finished stream to the host (synchronises)."""
     n = int(out_bytes.item())
     return out[:n].cpu().numpy().tobytes()
+
+
+# ---- batched compression -------------------------------------------------------
+
+def _messages(n_msgs):
+    return (ZcMessage * n_msgs)()
+
+
+class BatchCompress:
+    """Plan for compressing a list of FP32/BF16 tensors in one launch.
+
+    ``blocks`` and ``ebs`` give each message's block size (RAW = verbatim) and
+    absolute bound.  ``run()`` launches the plan; the streams are packed in
+    ``self.packed`` at offsets ``self.msg_off`` (device, M + 1 entries)."""
+
+    def __init__(self, xs, blocks, ebs, tile_chunks: int = 0, grid: int = 0,
+                 ws: Workspace | None = None, cap: int | None = None, packed=None,
+                 stream=None):
+        self.xs = [x.contiguous() for x in xs]
+        M = len(self.xs)
+        dev = self.xs[0].device
+        self.msgs = _messages(M)
+        for i, x in enumerate(self.xs):
+            m = self.msgs[i]
+            m.in_ = x.data_ptr() if x.numel() else None
+            m.out = None
+            m.n = x.numel()
+            m.dtype = dtype_code(x)
+            m.block = int(blocks[i])
+            m.eb_abs = float(ebs[i])
+        self.n_total = sum(x.numel() for x in self.xs)
+        self.ws = ws or Workspace(self.n_total, M, dev, stream)
+        self.cap = cap if cap is not None else self.max_bytes(max_width=True)
+        self.packed = packed if packed is not None else \
+            torch.empty(max(self.cap, 16), dtype=torch.uint8, device=dev)
+        self.msg_off = torch.zeros(M + 1, dtype=torch.int64, device=dev)
+        self.table = torch.empty(zc_batch_table_bytes(M), dtype=torch.uint8, device=dev)
+        self.plan = ZcBatch()
+        self.replan(tile_chunks, grid)
+
+    def max_bytes(self, max_width: bool = False) -> int:
+        """Worst-case packed length; with max_width, at the block size whose
+        worst case is largest (what an autotuner over block sizes needs)."""
+        M = len(self.xs)
+        if not max_width:
+            return zc_batch_max_bytes(M, self.msgs)
+        tmp = _messages(M)
+        ctypes.memmove(tmp, self.msgs, ctypes.sizeof(tmp))
+        best = 0
+        for b in (16, 32, 64, 128):
+            for i in range(M):
+                tmp[i].block = self.msgs[i].block if self.msgs[i].block == RAW else b
+            best = max(best, zc_batch_max_bytes(M, tmp))
+        return best
+
+    def replan(self, tile_chunks: int = 0, grid: int = 0, block: int = 0):
+        if block:
+            for i in range(len(self.xs)):
+                if self.msgs[i].block != RAW:
+                    self.msgs[i].block = block
+        _check(zc_plan_compress_batch(self.plan, len(self.xs), self.msgs, tile_chunks, grid,
+                                      self.packed.data_ptr(), self.cap, self.msg_off.data_ptr(),
+                                      self.table.data_ptr(), self.table.numel()),
+               "zc_plan_compress_batch")
+
+    def run(self, stream=None):
+        _check(zc_compress_batch(self.plan, self.ws.ptr, self.ws.nbytes, _stream(stream)),
+               "zc_compress_batch")
+        return self.packed, self.msg_off
+
+    def autotune(self, tune_block: bool = False, link_gbs: float = 0.0, reps: int = 3,
+                 stream=None):
+        """Run the library's autotuner; the plan is left at the best candidate.
+        Returns (best, [all measured candidates]) as dicts."""
+        pts = (ZcTunePoint * 64)()
+        npts = ctypes.c_int(0)
+        best = ZcTunePoint()
+        _check(zc_autotune_batch(len(self.xs), self.msgs, int(tune_block), float(link_gbs), reps,
+                                 self.packed.data_ptr(), self.cap, self.msg_off.data_ptr(),
+                                 self.table.data_ptr(), self.table.numel(), self.ws.ptr,
+                                 self.ws.nbytes, _stream(stream), pts, 64, ctypes.byref(npts),
+                                 ctypes.byref(best)), "zc_autotune_batch")
+        self.replan(best.tile_chunks, best.grid, best.block)
+        return best.as_dict(), [pts[i].as_dict() for i in range(min(npts.value, 64))]
+
+    def streams(self):
+        """Host copies of every message's stream (synchronises)."""
+        off = self.msg_off.cpu().tolist()
+        buf = self.packed[:off[-1]].cpu().numpy().tobytes()
+        return [buf[off[i]:off[i + 1]] for i in range(len(self.xs))]
+
+
+class BatchDecompress:
+    """Plan for decoding a packed buffer of M streams into ``outs``."""
+
+    def __init__(self, packed: torch.Tensor, msg_off: torch.Tensor, outs,
+                 ws: Workspace | None = None, stream=None):
+        self.outs = outs
+        M = len(outs)
+        self.msgs = _messages(M)
+        for i, o in enumerate(outs):
+            m = self.msgs[i]
+            m.in_ = None
+            m.out = o.data_ptr() if o.numel() else None
+            m.n = o.numel()
+            m.dtype = dtype_code(o)
+            m.block = 0
+            m.eb_abs = 0.0
+        dev = packed.device
+        self.packed, self.msg_off = packed, msg_off
+        self.ws = ws or Workspace(sum(o.numel() for o in outs), M, dev, stream)
+        self.table = torch.empty(zc_batch_table_bytes(M), dtype=torch.uint8, device=dev)
+        self.plan = ZcBatch()
+        _check(zc_plan_decompress_batch(self.plan, M, self.msgs, packed.data_ptr(), packed.numel(),
+                                        msg_off.data_ptr(), self.table.data_ptr(),
+                                        self.table.numel()), "zc_plan_decompress_batch")
+
+    def run(self, stream=None):
+        _check(zc_decompress_batch(self.plan, self.ws.ptr, self.ws.nbytes, _stream(stream)),
+               "zc_decompress_batch")
+        return self.outs
+
+
+class Graph:
+    """A CUDA graph of zc calls recorded on a (non-default) torch stream:
+
+        g = Graph(stream)
+        with g.capture():
+            batch.run(stream)
+        g.launch()
+    """
+
+    def __init__(self, stream: torch.cuda.Stream):
+        self.stream = stream
+        self.handle = ctypes.c_void_p(None)
+
+    def capture(self):
+        g = self
+
+        class _Ctx:
+            def __enter__(self_inner):
+                _check(zc_graph_begin(g.stream.cuda_stream), "zc_graph_begin")
+                return g
+
+            def __exit__(self_inner, et, ev, tb):
+                st = zc_graph_end(g.stream.cuda_stream, ctypes.byref(g.handle))
+                if et is None:
+                    _check(st, "zc_graph_end")
+                return False
+
+        return _Ctx()
+
+    def launch(self):
+        _check(zc_graph_launch(self.handle, self.stream.cuda_stream), "zc_graph_launch")
+
+    def __del__(self):
+        try:
+            if self.handle.value:
+                zc_graph_destroy(self.handle)
+                self.handle = ctypes.c_void_p(None)
+        except Exception:
+            pass

@@ -1,0 +1,192 @@
+"""Batched compression and decompression (many messages, one launch each)
+against the CPU oracle, through the C ABI (needs a GB300).
+
+Every message's stream inside the packed buffer must be byte-identical to the
+oracle's stream of that message alone; decoded values must be bit-identical
+to the oracle's decoding.  Messages mix FP32 and BF16, all block sizes and raw
+storage, sizes from empty to several tiles with ragged tails."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2308_05199_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SIZES_MIX = [0, 1, 17, 1000, 2048, 16383, 16384, 16385, 70001, 300001, 5, 65536,
+             131072 + 3, 40000]
+
+
+@pytest.fixture(scope="session")
+def zc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2308_05199_gb300 import build
+    build.build()
+    from paper_2308_05199_gb300 import zc as z
+    z.zc_set_tile_chunks(8)
+    return z
+
+
+def np_of(t: torch.Tensor) -> np.ndarray:
+    t = t.detach().cpu().contiguous()
+    if t.dtype == torch.bfloat16:
+        return t.view(torch.int16).numpy().view(np.uint16)
+    return t.numpy()
+
+
+def mixed_messages(seed, sizes, blocks_from=(16, 32, 64, 128, 0)):
+    """Student-t(3) messages with sigma log-uniform in [1e-4, 1e-1], eb = 1e-3 sigma,
+    alternating FP32 / BF16, block sizes drawn from blocks_from (0 = raw)."""
+    rng = np.random.default_rng(seed)
+    xs, blocks, ebs = [], [], []
+    for i, n in enumerate(sizes):
+        sigma = float(10 ** rng.uniform(-4, -1))
+        dt = torch.float32 if i % 2 == 0 else torch.bfloat16
+        xs.append(W.student_t3(n, sigma, seed * 1000 + i, dtype=dt))
+        blocks.append(int(blocks_from[rng.integers(len(blocks_from))]))
+        ebs.append(1e-3 * sigma)
+    return xs, blocks, ebs
+
+
+def oracle_stream(x, blk, eb):
+    a = np_of(x)
+    return oracle.compress_raw(a) if blk == 0 else oracle.compress(a, eb, int(math.log2(blk)))
+
+
+def check_against_oracle(b, xs, blocks, ebs):
+    assert b.ws.status()[0] == 0, b.ws.status()
+    streams = b.streams()
+    off = b.msg_off.cpu().tolist()
+    assert off[0] == 0
+    for i, (x, blk, eb) in enumerate(zip(xs, blocks, ebs)):
+        ref = oracle_stream(x, blk, eb)
+        assert off[i + 1] - off[i] == len(ref), (i, x.numel(), blk)
+        assert streams[i] == ref, (i, x.numel(), blk)
+
+
+@pytest.mark.parametrize("chunks", [4, 8, 16])
+@pytest.mark.parametrize("grid", [0, 152, 304])
+def test_batch_streams_match_oracle(zc, chunks, grid):
+    xs, blocks, ebs = mixed_messages(chunks * 7 + grid, SIZES_MIX)
+    b = zc.BatchCompress([x.cuda() for x in xs], blocks, ebs, tile_chunks=chunks, grid=grid)
+    b.run()
+    check_against_oracle(b, xs, blocks, ebs)
+
+
+def test_batch_single_message_equals_plain_compress(zc):
+    x = W.student_t3(250001, 0.01, 7).cuda()
+    b = zc.BatchCompress([x], [32], [1e-5])
+    b.run()
+    out, ob = zc.compress(x, 1e-5, 32)
+    assert b.streams()[0] == zc.stream_bytes(out, ob)
+
+
+def test_many_small_messages(zc):
+    rng = np.random.default_rng(11)
+    sizes = [int(v) for v in rng.integers(0, 5000, 1000)]
+    xs, blocks, ebs = mixed_messages(12, sizes)
+    b = zc.BatchCompress([x.cuda() for x in xs], blocks, ebs, grid=152)
+    b.run()
+    check_against_oracle(b, xs, blocks, ebs)
+
+
+def test_raw_messages_from_unaligned_inputs(zc):
+    big32 = W.student_t3(100003, 1.0, 3).cuda()
+    big16 = W.student_t3(100003, 1.0, 4, dtype=torch.bfloat16).cuda()
+    xs = [big32[1:], big16[1:], big16[3:50000], big32[2:7]]
+    b = zc.BatchCompress(xs, [0, 0, 0, 0], [0.0] * 4)
+    b.run()
+    check_against_oracle(b, [x.cpu() for x in xs], [0] * 4, [0.0] * 4)
+
+
+def test_batch_decompress_matches_oracle(zc):
+    xs, blocks, ebs = mixed_messages(5, SIZES_MIX)
+    b = zc.BatchCompress([x.cuda() for x in xs], blocks, ebs)
+    b.run()
+    outs = [torch.empty(x.numel(), dtype=(torch.float32, torch.bfloat16)[(i // 2) % 2],
+                        device="cuda") for i, x in enumerate(xs)]
+    d = zc.BatchDecompress(b.packed, b.msg_off, outs)
+    d.run()
+    assert d.ws.status()[0] == 0, d.ws.status()
+    for i, (x, blk, eb) in enumerate(zip(xs, blocks, ebs)):
+        s = oracle_stream(x, blk, eb)
+        code = 0 if outs[i].dtype == torch.float32 else 1
+        np.testing.assert_array_equal(np_of(outs[i]), oracle.decompress(s, x.numel(), code))
+
+
+def test_batch_decompress_wrong_count_is_a_format_error(zc):
+    xs, blocks, ebs = mixed_messages(6, [1000, 5000])
+    b = zc.BatchCompress([x.cuda() for x in xs], blocks, ebs)
+    b.run()
+    outs = [torch.empty(1000, device="cuda"), torch.empty(4999, device="cuda")]
+    d = zc.BatchDecompress(b.packed, b.msg_off, outs)
+    d.run()
+    assert d.ws.status()[0] == zc.ERR_FORMAT
+
+
+def test_batch_capacity_error_never_writes_past_capacity(zc):
+    xs = [W.student_t3(50000, 0.01, 20 + i) for i in range(3)]
+    blocks, ebs = [32] * 3, [1e-6] * 3
+    need = sum(len(oracle_stream(x, 32, 1e-6)) for x in xs)
+    cap = need - 8192
+    buf = torch.full((need,), 0xA5, dtype=torch.uint8, device="cuda")
+    b = zc.BatchCompress([x.cuda() for x in xs], blocks, ebs, cap=cap, packed=buf)
+    b.run()
+    assert b.ws.status()[0] == zc.ERR_CAPACITY
+    assert bool((buf[cap:] == 0xA5).all())
+
+
+def test_batch_and_decompress_in_a_cuda_graph(zc):
+    xs, blocks, ebs = mixed_messages(9, SIZES_MIX)
+    gx = [x.cuda() for x in xs]
+    s = torch.cuda.Stream()
+    b = zc.BatchCompress(gx, blocks, ebs, grid=304)
+    outs = [torch.empty(x.numel(), dtype=x.dtype, device="cuda") for x in xs]
+    d = zc.BatchDecompress(b.packed, b.msg_off, outs)
+    torch.cuda.synchronize()
+    b.run(s)  # ordinary calls first: they set the kernels' attributes
+    d.run(s)
+    s.synchronize()
+    b.packed.zero_()
+    b.msg_off.zero_()
+    for o in outs:
+        o.zero_()
+    torch.cuda.synchronize()
+    g = zc.Graph(s)
+    with g.capture():
+        b.run(s)
+        d.run(s)
+    for rep in range(3):
+        if rep == 2:  # new values in the same buffers: the graph compresses them
+            gx[9].mul_(-1.5)
+            xs[9] = gx[9].cpu()
+            torch.cuda.synchronize()
+        g.launch()
+        s.synchronize()
+        check_against_oracle(b, xs, blocks, ebs)
+        for i, (x, blk, eb) in enumerate(zip(xs, blocks, ebs)):
+            code = 0 if x.dtype == torch.float32 else 1
+            np.testing.assert_array_equal(
+                np_of(outs[i]), oracle.decompress(oracle_stream(x, blk, eb), x.numel(), code))
+
+
+def test_autotuner_picks_the_best_valid_candidate(zc):
+    xs, blocks, ebs = mixed_messages(13, [300000, 120000, 5000, 70000, 1 << 18, 33333],
+                                     blocks_from=(32, 32, 0))
+    b = zc.BatchCompress([x.cuda() for x in xs], blocks, ebs)
+    best, pts = b.autotune(tune_block=True, link_gbs=12.5, reps=2)
+    assert best["status"] == 0 and best["block"] in (16, 32, 64, 128)
+    ok = [p for p in pts if p["status"] == 0]
+    assert len(ok) >= 12
+    assert best["score_ms"] == min(p["score_ms"] for p in ok)
+    for p in ok:
+        assert p["score_ms"] == pytest.approx(p["ms"] + p["packed_bytes"] / 12.5e6, rel=1e-6)
+    # the plan is left at the winner; its streams are the oracle's at the chosen block size
+    b.run()
+    tuned = [best["block"] if blk else 0 for blk in blocks]
+    check_against_oracle(b, xs, tuned, ebs)

@@ -93,3 +93,39 @@ def test_argument_errors_without_gpu(lib):
     lib.zc_set_tile_chunks.restype = ctypes.c_int
     assert lib.zc_set_tile_chunks(5) == 1
     assert lib.zc_set_tile_chunks(8) == 0
+
+
+def test_batch_plan_argument_errors_without_gpu():
+    """Batch planning validates every message before touching the GPU."""
+    from paper_2308_05199_gb300 import zc as z
+    fake = 1 << 20  # never dereferenced
+    msgs = (z.ZcMessage * 2)()
+    for m in msgs:
+        m.in_, m.n, m.dtype, m.block, m.eb_abs = fake, 1000, 0, 32, 1e-3
+    msgs[1].block = z.RAW
+    plan = z.ZcBatch()
+    tb = z.zc_batch_table_bytes(2)
+    assert tb >= 2 * 64
+    assert z.zc_batch_max_bytes(2, msgs) == (z.zc_max_compressed_bytes(1000, 32) +
+                                             z.zc_raw_stream_bytes(1000, 0))
+
+    def plan_rc(chunks=8, grid=0, cap=1 << 20, table=tb):
+        return z.zc_plan_compress_batch(plan, 2, msgs, chunks, grid, fake, cap, fake, fake, table)
+
+    assert plan_rc(chunks=5) == z.ERR_ARG
+    assert plan_rc(grid=-1) == z.ERR_ARG
+    assert plan_rc(table=tb - 1) == z.ERR_ARG
+    assert plan_rc(cap=64) == z.ERR_CAPACITY  # below the headers, widths and raw payload
+    msgs[0].block = 48
+    assert plan_rc() == z.ERR_ARG
+    msgs[0].block = 32
+    msgs[0].eb_abs = 0.0
+    assert plan_rc() == z.ERR_ARG
+    msgs[0].eb_abs = 1e-3
+    msgs[0].dtype = 7
+    assert plan_rc() == z.ERR_ARG
+    msgs[0].dtype = 1
+    msgs[0].in_ = fake + 1  # BF16 input must be 2-byte aligned
+    assert plan_rc() == z.ERR_ARG
+    assert z.zc_plan_decompress_batch(plan, 2, msgs, fake + 8, 4096, fake, fake, tb) == z.ERR_ARG
+    assert z.zc_graph_begin(None) == z.ERR_ARG
