@@ -1,0 +1,216 @@
+"""Pins of the selector oracle (oracle/selector.py) against hand-derived
+values, the codec oracle's own encoder and finite differences -- nothing here
+re-types the oracle's formulas."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import selector as S
+
+EB = 2.0 ** -10  # 2 eb = 2^-9: multiples of it are exact in FP32
+
+
+def test_sample_positions_by_hand():
+    # n_c = 16384 FP32 elements (64 KiB): 128 spans, 16 sampled at 128 * floor(j * 127 / 15)
+    hand = [0, 8, 16, 25, 33, 42, 50, 59, 67, 76, 84, 93, 101, 110, 118, 127]
+    assert S.span_starts(16384) == [(128 * k, 128) for k in hand]
+    assert S.span_starts(128 * 3) == [(0, 128), (128, 128), (256, 128)]
+    assert S.span_starts(129) == [(0, 128)]
+    assert S.span_starts(100) == [(0, 100)]
+    assert S.span_starts(0) == []
+
+
+def test_zero_chunk():
+    f = S.chunk_stats(np.zeros(16384, np.float32), 1e-3)
+    for k, L in enumerate((16, 32, 64, 128)):
+        assert f[k] == 8.0 / L + 256.0 / 16384
+    assert list(f[4:14]) == [0, 0, 0, 1, 1, 0, 0, 0, 0, 0]
+    assert f[14] == 1.0 and f[15] == 14.0 / 16
+
+
+def test_constant_chunk():
+    # 0.3 / (2 * fl32(1e-3)) = 149.99999.. -> q = 150, bit length 8: every block
+    # holds its head (w = 8, 9 planes) and zero deltas
+    f = S.chunk_stats(np.full(16384, 0.3, np.float32), 1e-3)
+    for k, L in enumerate((16, 32, 64, 128)):
+        assert f[k] == 9 + 8.0 / L + 256.0 / 16384
+    assert f[4] == 0 and f[7] == 1 and f[8] == 0
+    assert f[9] == pytest.approx(math.log2(151), abs=1e-12)
+    assert f[12] == pytest.approx(8 / 24)
+
+
+def test_short_chunk_by_hand():
+    q = np.array([0, 2, 2, -1, 5])
+    x = (q * 2 * EB).astype(np.float32)
+    f = S.chunk_stats(x, EB)
+    # one partial span; deltas with the head from 0: [0, 2, 0, -3, 6] -> w = 3 at every L
+    for k, L in enumerate((16, 32, 64, 128)):
+        assert f[k] == pytest.approx(4 * L / 5 + 8.0 / L + 256.0 / 5)
+    assert f[4] == pytest.approx(math.log2(7))            # max q - min q = 6
+    assert f[5] == pytest.approx(math.log2(1 + 11 / 4))   # |d| = 2, 0, 3, 6
+    assert f[6] == pytest.approx(math.log2(7))
+    assert f[7] == pytest.approx(1 / 4)
+    assert f[8] == pytest.approx(1 / 5)
+    assert f[9] == pytest.approx(math.log2(3))            # mean |q| = 10 / 5
+    assert f[10] == pytest.approx(math.log2(1 + 14 / 3))  # second differences -2, -3, 9
+    assert f[11] == pytest.approx(1 / 3)                  # one sign change in 3 pairs
+    assert f[12] == 0 and f[13] == 0
+    assert f[15] == pytest.approx(math.log2(5) / 16)
+
+
+def test_ramp_widths_by_hand():
+    # q_i = i: a block starting at element a has deltas [a, 1, 1, ...], width bitlen(max(a, 1))
+    n = 16384
+    x = (np.arange(n) * 2 * EB).astype(np.float32)
+    f = S.chunk_stats(x, EB)
+    hand = [0, 8, 16, 25, 33, 42, 50, 59, 67, 76, 84, 93, 101, 110, 118, 127]
+    for k, L in enumerate((16, 32, 64, 128)):
+        bits = 0
+        for s in hand:
+            for a in range(128 * s, 128 * s + 128, L):
+                bits += (max(a, 1).bit_length() + 1) * L
+        assert f[k] == pytest.approx(bits / 2048 + 8.0 / L + 256.0 / n, rel=1e-15)
+    assert f[7] == 0 and f[11] == 0 and f[10] == 0  # constant unit steps
+    assert f[5] == pytest.approx(1.0)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_sampled_bits_equal_the_codec_oracle_on_the_spans(dtype):
+    """f0..f3 against the codec oracle's encoder run on each sampled span."""
+    r = np.random.default_rng(5)
+    x = (r.standard_t(3, 32768) * 0.05).astype(np.float32)
+    if dtype == "bf16":
+        x = (x.view(np.uint32) >> 16).astype(np.uint16)  # truncated to BF16 bits
+    eb = 1e-4
+    f = S.chunk_stats(x, eb)
+    spans = S.span_starts(x.size)
+    for k, lg in enumerate((4, 5, 6, 7)):
+        payload = sum(oracle.header(oracle.compress(x[a:a + c], eb, lg))["payload"]
+                      for a, c in spans)
+        L = 1 << lg
+        assert f[k] == pytest.approx(8 * payload / (128 * len(spans)) + 8.0 / L + 256.0 / x.size,
+                                     rel=1e-14)
+    assert f[14] == (1.0 if dtype == "f32" else 0.5)
+
+
+def test_unquantizable_and_empty_chunks_are_nan():
+    x = np.zeros(16384, np.float32)
+    x[0] = np.nan
+    assert np.isnan(S.chunk_stats(x, 1e-3)).all()
+    x[0] = 1e6  # |q| = 5e8 > 2^22
+    assert np.isnan(S.chunk_stats(x, 1e-3)).all()
+    x[0] = 0
+    x[200] = np.inf  # not sampled (span 1 starts at 1024): the sample is fine
+    assert np.isfinite(S.chunk_stats(x, 1e-3)).all()
+    assert np.isnan(S.chunk_stats(np.zeros(0, np.float32), 1e-3)).all()
+
+
+# ---- MLP ---------------------------------------------------------------------------
+
+def _rand_problem(B, seed):
+    r = np.random.default_rng(seed)
+    p = S.init_params(seed).astype(np.float64)
+    p += r.normal(0, 0.05, p.size)  # non-zero biases too
+    norm = np.concatenate([r.normal(0, 1, 16), r.uniform(0.5, 2, 16)])
+    X = r.normal(0, 1, (B, 16))
+    T = r.normal(0, 1, (B, 4))
+    return p, norm, X, T
+
+
+def test_gradient_matches_finite_differences():
+    p, norm, X, T = _rand_problem(7, 1)
+    loss, g = S.loss_grad(p, norm, X, T)
+    r = np.random.default_rng(2)
+    idx = np.concatenate([r.choice(S.N_PARAMS, 400, replace=False),
+                          np.arange(S.N_PARAMS - 4, S.N_PARAMS)])
+    h = 1e-6
+    for i in idx:
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (S.loss_grad(pp, norm, X, T)[0] - S.loss_grad(pm, norm, X, T)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g).max()), (i, fd, g[i])
+
+
+def test_linear_regime_closed_form():
+    """Positive inputs and weights keep every ReLU open: the network is the
+    product of its three affine maps."""
+    r = np.random.default_rng(3)
+    P = {"W1": r.uniform(0, 1, (64, 16)), "b1": r.uniform(0, 1, 64),
+         "W2": r.uniform(0, 1, (64, 64)), "b2": r.uniform(0, 1, 64),
+         "W3": r.normal(0, 1, (4, 64)), "b3": r.normal(0, 1, 4)}
+    p = S.pack(P)
+    norm = np.concatenate([np.zeros(16), np.ones(16)])
+    X = r.uniform(0, 1, (5, 16))
+    M = P["W3"] @ P["W2"] @ P["W1"]
+    c = P["W3"] @ (P["W2"] @ P["b1"] + P["b2"]) + P["b3"]
+    np.testing.assert_allclose(S.forward(p, norm, X), X @ M.T + c, rtol=1e-12)
+    T = r.normal(0, 1, (5, 4))
+    _, g = S.loss_grad(p, norm, X, T)
+    Y = X @ M.T + c
+    np.testing.assert_allclose(g[-4:], 2 * (Y - T).sum(0) / 20, rtol=1e-12)
+    # and the first layer's weights: dL/dW1 = sum_b (M' dY_b) x_b^T with M' = (W3 W2)^T
+    dY = 2 * (Y - T) / 20
+    np.testing.assert_allclose(g[:1024].reshape(64, 16),
+                               ((dY @ P["W3"] @ P["W2"]).T @ X), rtol=1e-10)
+
+
+def test_zero_network():
+    p = np.zeros(S.N_PARAMS)
+    norm = np.concatenate([np.zeros(16), np.ones(16)])
+    X = np.ones((3, 16))
+    T = np.arange(12.0).reshape(3, 4)
+    loss, g = S.loss_grad(p, norm, X, T)
+    assert loss == pytest.approx((T ** 2).sum() / 12)
+    assert np.all(g[:-4] == 0)
+    np.testing.assert_allclose(g[-4:], -2 * T.sum(0) / 12)
+
+
+def test_sgd_momentum_two_steps():
+    p, v = np.array([1.0, -2.0]), np.zeros(2)
+    g = np.array([0.5, 0.25])
+    p, v = S.sgd_step(p, v, g, 0.1, 0.9)
+    p, v = S.sgd_step(p, v, g, 0.1, 0.9)
+    # v1 = g, v2 = 1.9 g; p2 = p0 - 0.1 * 2.9 g
+    np.testing.assert_allclose(p, [1.0 - 0.29 * 0.5, -2.0 - 0.29 * 0.25])
+
+
+# ---- selection ---------------------------------------------------------------------
+
+CFG = {"link_gbs": 12.5, "ns_per_byte": [0.02, 0.015, 0.014, 0.013], "raw_ns_per_byte": 0.002,
+       "judge_log2": 1.0}
+
+
+def test_heuristic_choice():
+    f = np.zeros(16)
+    f[1] = 8.0
+    assert S.heuristic_choice(16384, 4, f, CFG) == 32
+    f[1] = 33.0  # more bits than raw FP32
+    assert S.heuristic_choice(16384, 4, f, CFG) == 0
+    f[1] = 15.0  # BF16: raw is 16 bits, but coding also costs codec time
+    # coded: 65536 * 0.015 + 32768 * 15 / 8 / 12.5 = 983.04 + 4915.2
+    # raw:   65536 * 0.002 + (32 + 65536) / 12.5   = 131.072 + 5245.44
+    assert S.heuristic_choice(32768, 2, f, CFG) == 0
+    f[1] = np.nan
+    assert S.heuristic_choice(16384, 4, f, CFG) == 0
+
+
+def test_mlp_choice_and_the_judge():
+    f = np.array([6.0, 5.5, 5.0, 6.0] + [0.0] * 12)
+    y = np.log2([6.2, 5.4, 4.1, 6.5])
+    # coded costs (ns): 65536 * c_k + 16384 * bits_k / 8 / 12.5 -> L = 64 is cheapest
+    assert S.mlp_choice(16384, 4, f, y, CFG) == (64, False)
+    y[2] = math.log2(1.5)  # 1.74 below log2(f[2]): the judge rejects it
+    assert S.mlp_choice(16384, 4, f, y, CFG) == (32, True)
+    y[2] = np.nan
+    assert S.mlp_choice(16384, 4, f, y, CFG) == (32, True)
+
+
+def test_best_choice():
+    c, coded, raw = S.best_choice(16384, 4, [9.0, 8.0, 8.5, 12.0], CFG)
+    assert c == 32
+    assert coded[1] == pytest.approx(65536 * 0.015 + 16384 * 8 / 8 / 12.5)
+    assert raw == pytest.approx(65536 * 0.002 + 65568 / 12.5)
+    assert S.best_choice(16384, 4, [40.0] * 4, CFG)[0] == 0
