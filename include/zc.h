@@ -300,6 +300,91 @@ int zc_autotune_batch(int n_msgs, const zc_message* h_msgs, int tune_block, doub
                       zc_stream_t s, zc_tune_point* h_points, int max_points, int* n_points,
                       zc_tune_point* best);
 
+/* ---- Per-chunk codec selection (statistics, MLP, choice) ------------------
+ *
+ * The paper runs one codec configuration per collective.  Sec. 3.2.2 shows
+ * that a compression step's cost depends on the message, and Sec. 3.3.3
+ * weighs compression cost against the bytes it saves on the link; the
+ * selector below (an addition to the paper's method: it has no learned part)
+ * makes that trade per chunk.  Every message of a compression plan is one
+ * chunk (the selector's unit is 64 KiB; split longer buffers into messages of
+ * that size).  The codec's arithmetic is unchanged: the selector only picks,
+ * per message, the block size L in {16, 32, 64, 128} or raw storage. */
+#define ZC_STATS 16
+#define ZC_MLP_IN 16
+#define ZC_MLP_HIDDEN 64
+#define ZC_MLP_OUT 4
+/* Parameters, FP32, in this order: W1[64][16], b1[64], W2[64][64], b2[64],
+ * W3[4][64], b3[4] (row-major, W[out][in]). */
+#define ZC_MLP_PARAMS 5508
+
+/* Statistics of every message of a compression plan, 16 FP32 per message
+ * into d_feat[n_msgs][16].  Sample: S = min(16, m) spans of 128 elements
+ * (m = n / 128 full spans), span j at 128 * floor(j (m - 1) / (S - 1)); one
+ * partial span when n < 128.  The sampled values are quantized exactly as the
+ * codec does, with the message's bound.  Features:
+ *   0..3  sampled bits per element at L = 16, 32, 64, 128 (the codec's
+ *         (w + 1) L bits per block of width w > 0) + 8 / L + 256 / n;
+ *   4     log2(1 + max q - min q);      5  log2(1 + mean |d|);
+ *   6     log2(1 + max |d|);            7  fraction of d == 0;
+ *   8     fraction of q == 0;           9  log2(1 + mean |q|);
+ *   10    log2(1 + mean |d_i - d_{i-1}|);
+ *   11    fraction of sign changes between consecutive d;
+ *   12    mean bit length of |q| at L = 32 block heads / 24;
+ *   13    standard deviation over spans of the span's L = 32 bits/element;
+ *   14    raw bits per element / 32;    15 log2(n) / 16;
+ * d = q_i - q_{i-1} within a span.  A message with no elements, no bound, or
+ * a sampled value the codec cannot quantize gets a row of NaN.  One kernel,
+ * one warp per message. */
+int zc_batch_chunk_stats(const zc_batch* plan, float* d_feat, zc_stream_t s);
+
+/* MLP forward: y[b] = W3 relu(W2 relu(W1 x'[b] + b1) + b2) + b3 with
+ * x' = (x - mu) * inv_sd, d_norm = {mu[16], inv_sd[16]}; d_x[B][16] ->
+ * d_y[B][4] (predicted log2 bits per element at L = 16 .. 128). */
+int zc_mlp_forward(const float* d_params, const float* d_norm, const float* d_x, int B,
+                   float* d_y, zc_stream_t s);
+
+/* Scratch bytes of zc_mlp_grad for a minibatch of B rows. */
+size_t zc_mlp_scratch_bytes(int B);
+
+/* Gradient of the mean squared error sum((y - t)^2) / (4 B) over the
+ * minibatch rows d_idx[0 .. B) of d_x / d_t (rows 0 .. B when d_idx is NULL)
+ * into d_grad[ZC_MLP_PARAMS] (layout of the parameters); the loss into
+ * *d_loss when d_loss is not NULL.  The ReLU derivative at 0 is 0.  Summation
+ * order is fixed, so results are reproducible. */
+int zc_mlp_grad(const float* d_params, const float* d_norm, const float* d_x, const float* d_t,
+                const int* d_idx, int B, float* d_grad, float* d_loss, void* d_scratch,
+                size_t scratch_bytes, zc_stream_t s);
+
+/* Momentum SGD: v <- momentum v + g; p <- p - lr v (all ZC_MLP_PARAMS). */
+int zc_mlp_sgd(float* d_params, float* d_vel, const float* d_grad, float lr, float momentum,
+               zc_stream_t s);
+
+/* Cost model of the selection: a message of n elements of s bytes costs,
+ * coded at L_k with b bits per element, n s ns_per_byte[k] + (n b / 8) /
+ * link_gbs ns, and raw, n s raw_ns_per_byte + (32 + n s) / link_gbs ns
+ * (ns_per_byte: measured codec time, compression plus decompression, per
+ * input byte; link_gbs in GB/s = bytes per ns). */
+typedef struct {
+    float link_gbs;
+    float ns_per_byte[4];
+    float raw_ns_per_byte;
+    float judge_log2;        /* largest accepted |prediction - log2 estimate| */
+} zc_select_cfg;
+
+/* Choose every message's storage and write it into the plan's table (the
+ * next zc_compress_batch of the plan uses it).  The heuristic: L = 32, or
+ * raw when the cost with the sampled estimate (feature 1) is not below raw's.
+ * With d_pred (zc_mlp_forward's output) the choice is the L of least cost
+ * with bits 2^pred[k], or raw when that is cheaper -- unless a prediction is
+ * not finite or the chosen L's prediction is more than judge_log2 from log2
+ * of its sampled estimate (features 0..3): then the heuristic decides (a
+ * fallback).  Messages planned raw stay raw.  d_choice[n_msgs] (nullable):
+ * the block size, 0 for raw; d_counts[2] (nullable): fallbacks, raw
+ * messages. */
+int zc_batch_select(const zc_batch* plan, const float* d_feat, const float* d_pred,
+                    const zc_select_cfg* cfg, int* d_choice, unsigned* d_counts, zc_stream_t s);
+
 /* ---- CUDA graphs of zc calls ----------------------------------------------
  * Every zc launch function is asynchronous and reads nothing back, so a
  * sequence of them can be recorded once and replayed with one launch.

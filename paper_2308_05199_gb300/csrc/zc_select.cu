@@ -1,0 +1,569 @@
+// zc_select.cu -- the per-chunk codec selector: chunk statistics, the
+// 16-64-64-4 MLP (forward, loss gradient, momentum SGD) and the selection of
+// block size or raw storage, written into a batched-compression plan.
+//
+// The statistics, the network and the cost model are defined in the header
+// comment of zc.h (zc_batch_chunk_stats .. zc_batch_select).  Everything runs
+// on the device; nothing is read back, so a whole select-then-compress
+// sequence can be captured in one CUDA graph.
+#include <cstring>
+
+#include "zc_launch.h"
+
+namespace zc {
+
+constexpr int N_STATS = ZC_STATS;
+constexpr int ST_SPANS = 16;
+constexpr int ST_SPAN = 128;
+
+constexpr int NI = ZC_MLP_IN, NH = ZC_MLP_HIDDEN, NO = ZC_MLP_OUT;
+constexpr int NPARAM = ZC_MLP_PARAMS;
+constexpr int OFF_B1 = NH * NI, OFF_W2 = OFF_B1 + NH, OFF_B2 = OFF_W2 + NH * NH;
+constexpr int OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NO * NH;
+static_assert(OFF_B3 + NO == NPARAM, "parameter layout");
+constexpr int NPAD = 5512;  // per-CTA partial gradient stride (NPARAM + loss, rounded)
+constexpr int TB = 64;      // samples per CTA
+constexpr int MT = 256;     // threads per MLP CTA
+
+__device__ __forceinline__ int bitlen_u(unsigned v) { return 32 - __clz(v); }
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    return v;
+}
+
+__device__ __forceinline__ float load_elem(const Item& it, unsigned long long i)
+{
+    return it.x_dtype == ZC_F32 ? __ldg((const float*)it.x + i)
+                                : bf16_to_f32(__ldg((const unsigned short*)it.x + i));
+}
+
+// ---- chunk statistics: one warp per item ------------------------------------------
+__global__ void __launch_bounds__(256) k_chunk_stats(const Item* items, unsigned n_items,
+                                                     float* feat)
+{
+    __shared__ double span_v[8][ST_SPANS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned idx = blockIdx.x * 8 + warp;
+    if (idx >= n_items) return;  // warp-uniform; only warp-level sync below
+    const Item it = items[idx];
+    float* out = feat + (size_t)idx * N_STATS;
+    const unsigned long long n = it.n;
+    if (n == 0 || it.x == nullptr || !(it.two_eb > 0.0f)) {
+        if (lane < N_STATS) out[lane] = __int_as_float(0x7fc00000);  // NaN row
+        return;
+    }
+    const unsigned long long m = n / ST_SPAN;
+    const int S = m == 0 ? 1 : (int)(m < ST_SPANS ? m : ST_SPANS);
+    unsigned b16 = 0, b32 = 0, b64 = 0, b128 = 0;  // lane-partial block bits
+    unsigned long long sum_ad = 0, sum_aq = 0, sum_ad2 = 0;
+    unsigned max_ad = 0, nz_d = 0, nz_q = 0, n_sc = 0, head_bits = 0;
+    int qmin = 0x7fffffff, qmax = -0x7fffffff - 1;
+    int bad = 0;
+    unsigned long long tot = 0, nd = 0, nd2 = 0, nheads = 0;
+    for (int j = 0; j < S; ++j) {
+        const unsigned long long s0 =
+            (m == 0 || S == 1) ? 0ull : (unsigned long long)ST_SPAN * (((unsigned long long)j * (m - 1)) / (S - 1));
+        const int cnt = m == 0 ? (int)n : ST_SPAN;
+        int q[4], d[4], pd[4];
+        bool v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = 32 * r + lane;
+            v[r] = i < cnt;
+            int qq = 0;
+            if (v[r]) {
+                const float x = load_elem(it, s0 + i);
+                if (quantize(x, it.eb, it.two_eb, it.inv, qq) != 0) {
+                    bad = 1;
+                    qq = 0;
+                }
+            }
+            q[r] = qq;
+        }
+        // d_i = q_i - q_{i-1}, and d_{i-1} (for the second differences)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int up = __shfl_up_sync(FULL, q[r], 1);
+            const int prev_row = __shfl_sync(FULL, q[r > 0 ? r - 1 : 0], 31);
+            d[r] = q[r] - (lane ? up : (r ? prev_row : 0));
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int up = __shfl_up_sync(FULL, d[r], 1);
+            const int prev_row = __shfl_sync(FULL, d[r > 0 ? r - 1 : 0], 31);
+            pd[r] = lane ? up : (r ? prev_row : 0);
+        }
+        unsigned aq[4], ad[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = 32 * r + lane;
+            aq[r] = v[r] ? (unsigned)abs(q[r]) : 0u;
+            ad[r] = (v[r] && i >= 1) ? (unsigned)abs(d[r]) : 0u;
+            if (v[r]) {
+                nz_q += q[r] == 0;
+                sum_aq += aq[r];
+                qmin = min(qmin, q[r]);
+                qmax = max(qmax, q[r]);
+                if (i >= 1) {
+                    sum_ad += ad[r];
+                    max_ad = max(max_ad, ad[r]);
+                    nz_d += d[r] == 0;
+                }
+                if (i >= 2) {
+                    sum_ad2 += (unsigned)abs(d[r] - pd[r]);
+                    n_sc += (d[r] > 0 && pd[r] < 0) || (d[r] < 0 && pd[r] > 0);
+                }
+            }
+        }
+        // the codec's block bits at every L: the block head's delta is |q|
+        unsigned span_b32 = 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            unsigned a = (lane & 15) == 0 ? aq[r] : ad[r];
+#pragma unroll
+            for (int off = 8; off; off >>= 1) a = max(a, __shfl_xor_sync(FULL, a, off));
+            if ((lane & 15) == 0 && a) b16 += (bitlen_u(a) + 1) * 16;
+            const unsigned m32 = __reduce_max_sync(FULL, lane == 0 ? aq[r] : ad[r]);
+            if (m32) span_b32 += (bitlen_u(m32) + 1) * 32;
+            if (lane == 0 && v[r]) head_bits += bitlen_u(aq[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r += 2) {
+            const unsigned m64 = __reduce_max_sync(FULL, max(lane == 0 ? aq[r] : ad[r], ad[r + 1]));
+            if (lane == 0 && m64) b64 += (bitlen_u(m64) + 1) * 64;
+        }
+        {
+            const unsigned a = max(max(lane == 0 ? aq[0] : ad[0], ad[1]), max(ad[2], ad[3]));
+            const unsigned m128 = __reduce_max_sync(FULL, a);
+            if (lane == 0 && m128) b128 += (bitlen_u(m128) + 1) * 128;
+        }
+        if (lane == 0) {
+            b32 += span_b32;
+            span_v[warp][j] = (double)span_b32 / (double)cnt;
+        }
+        tot += cnt;
+        nd += cnt - 1;
+        nd2 += cnt >= 2 ? cnt - 2 : 0;
+        nheads += (cnt + 31) / 32;
+    }
+    if (__any_sync(FULL, bad)) {
+        if (lane < N_STATS) out[lane] = __int_as_float(0x7fc00000);
+        return;
+    }
+    const unsigned long long B16 = warp_sum_u64(b16), B32 = warp_sum_u64(b32);
+    const unsigned long long B64 = warp_sum_u64(b64), B128 = warp_sum_u64(b128);
+    const unsigned long long SAD = warp_sum_u64(sum_ad), SAQ = warp_sum_u64(sum_aq);
+    const unsigned long long SAD2 = warp_sum_u64(sum_ad2);
+    const unsigned long long NZD = warp_sum_u64(nz_d), NZQ = warp_sum_u64(nz_q);
+    const unsigned long long NSC = warp_sum_u64(n_sc), HB = warp_sum_u64(head_bits);
+    const unsigned MAD = __reduce_max_sync(FULL, max_ad);
+    const int QMN = __reduce_min_sync(FULL, qmin), QMX = __reduce_max_sync(FULL, qmax);
+    __syncwarp();
+    if (lane != 0) return;
+    const double dt = (double)tot, dn = (double)n;
+    double f[N_STATS];
+    f[0] = (double)B16 / dt + 8.0 / 16 + 256.0 / dn;
+    f[1] = (double)B32 / dt + 8.0 / 32 + 256.0 / dn;
+    f[2] = (double)B64 / dt + 8.0 / 64 + 256.0 / dn;
+    f[3] = (double)B128 / dt + 8.0 / 128 + 256.0 / dn;
+    f[4] = log2(1.0 + (double)((long long)QMX - (long long)QMN));
+    f[5] = nd ? log2(1.0 + (double)SAD / (double)nd) : 0.0;
+    f[6] = nd ? log2(1.0 + (double)MAD) : 0.0;
+    f[7] = nd ? (double)NZD / (double)nd : 0.0;
+    f[8] = (double)NZQ / dt;
+    f[9] = log2(1.0 + (double)SAQ / dt);
+    f[10] = nd2 ? log2(1.0 + (double)SAD2 / (double)nd2) : 0.0;
+    f[11] = nd2 ? (double)NSC / (double)nd2 : 0.0;
+    f[12] = (double)HB / (double)nheads / 24.0;
+    double mean = 0.0;
+    for (int j = 0; j < S; ++j) mean += span_v[warp][j];
+    mean /= S;
+    double var = 0.0;
+    for (int j = 0; j < S; ++j) {
+        const double e = span_v[warp][j] - mean;
+        var += e * e;
+    }
+    f[13] = sqrt(var / S);
+    f[14] = it.x_dtype == ZC_F32 ? 1.0 : 0.5;
+    f[15] = log2(dn) / 16.0;
+#pragma unroll
+    for (int k = 0; k < N_STATS; ++k) out[k] = (float)f[k];
+}
+
+// ---- MLP ------------------------------------------------------------------------------
+// Shared memory of an MLP CTA (floats): the parameters with padded row
+// strides (no bank conflicts), the normalised inputs, both layers'
+// pre-activations, one 64 x 64 gradient buffer and the outputs.
+struct MlpSmem {
+    float W1[NH][NI + 1], b1[NH];
+    float W2[NH][NH + 1], b2[NH];
+    float W3[NO][NH + 1], b3[NO];
+    float X[TB][NI + 1];
+    float A1[TB][NH + 1];
+    float A2[TB][NH + 1];  // later: dA1
+    float D[TB][NH + 1];   // dA2
+    float Y[TB][NO];       // outputs, later dY
+    float red[MT / 32];
+};
+
+__device__ __forceinline__ float relu(float v) { return v > 0.0f ? v : 0.0f; }
+
+// Loads the parameters and the tile's rows (normalised); rows past B are zero.
+__device__ __forceinline__ void mlp_load(MlpSmem& sm, const float* P, const float* norm,
+                                         const float* X, const int* idx, int B, int row0)
+{
+    const int t = threadIdx.x;
+    for (int p = t; p < NH * NI; p += MT) sm.W1[p / NI][p % NI] = P[p];
+    for (int p = t; p < NH * NH; p += MT) sm.W2[p / NH][p % NH] = P[OFF_W2 + p];
+    for (int p = t; p < NO * NH; p += MT) sm.W3[p / NH][p % NH] = P[OFF_W3 + p];
+    if (t < NH) {
+        sm.b1[t] = P[OFF_B1 + t];
+        sm.b2[t] = P[OFF_B2 + t];
+    }
+    if (t < NO) sm.b3[t] = P[OFF_B3 + t];
+    for (int p = t; p < TB * NI; p += MT) {
+        const int s = p / NI, k = p % NI, r = row0 + s;
+        float v = 0.0f;
+        if (r < B) {
+            const long long row = idx != nullptr ? (long long)idx[r] : (long long)r;
+            v = __fmul_rn(__fsub_rn(X[row * NI + k], norm[k]), norm[NI + k]);
+        }
+        sm.X[s][k] = v;
+    }
+    __syncthreads();
+}
+
+// A1 = X W1^T + b1, A2 = relu(A1) W2^T + b2, Y = relu(A2) W3^T + b3.
+__device__ __forceinline__ void mlp_forward_tile(MlpSmem& sm)
+{
+    const int t = threadIdx.x, j = t & (NH - 1), g = t >> 6;
+    {
+        float w[NI];
+#pragma unroll
+        for (int k = 0; k < NI; ++k) w[k] = sm.W1[j][k];
+        for (int i = 0; i < TB / 4; ++i) {
+            const int s = g * (TB / 4) + i;
+            float a = sm.b1[j];
+#pragma unroll
+            for (int k = 0; k < NI; ++k) a = __fadd_rn(a, __fmul_rn(w[k], sm.X[s][k]));
+            sm.A1[s][j] = a;
+        }
+    }
+    __syncthreads();
+    {
+        float acc[TB / 4];
+#pragma unroll
+        for (int i = 0; i < TB / 4; ++i) acc[i] = sm.b2[j];
+        for (int k = 0; k < NH; ++k) {
+            const float w = sm.W2[j][k];
+#pragma unroll
+            for (int i = 0; i < TB / 4; ++i)
+                acc[i] = __fadd_rn(acc[i], __fmul_rn(w, relu(sm.A1[g * (TB / 4) + i][k])));
+        }
+#pragma unroll
+        for (int i = 0; i < TB / 4; ++i) sm.A2[g * (TB / 4) + i][j] = acc[i];
+    }
+    __syncthreads();
+    {
+        const int s = t >> 2, o = t & 3;
+        float y = sm.b3[o];
+        for (int k = 0; k < NH; ++k) y = __fadd_rn(y, __fmul_rn(sm.W3[o][k], relu(sm.A2[s][k])));
+        sm.Y[s][o] = y;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(MT) k_mlp_forward(const float* P, const float* norm,
+                                                    const float* X, int B, float* Yout)
+{
+    extern __shared__ __align__(16) uint8_t raw[];
+    MlpSmem& sm = *reinterpret_cast<MlpSmem*>(raw);
+    const int row0 = blockIdx.x * TB;
+    mlp_load(sm, P, norm, X, nullptr, B, row0);
+    mlp_forward_tile(sm);
+    const int t = threadIdx.x, s = t >> 2, o = t & 3;
+    if (row0 + s < B) Yout[(long long)(row0 + s) * NO + o] = sm.Y[s][o];
+}
+
+// Per-CTA partial gradient of sum((Y - T)^2) / (B * NO) over its rows, and
+// the partial sum of squared residuals, at partial + blockIdx.x * NPAD.
+__global__ void __launch_bounds__(MT) k_mlp_grad(const float* P, const float* norm,
+                                                 const float* X, const float* T, const int* idx,
+                                                 int B, float* partial)
+{
+    extern __shared__ __align__(16) uint8_t raw[];
+    MlpSmem& sm = *reinterpret_cast<MlpSmem*>(raw);
+    const int row0 = blockIdx.x * TB;
+    mlp_load(sm, P, norm, X, idx, B, row0);
+    mlp_forward_tile(sm);
+    const int t = threadIdx.x, j = t & (NH - 1), g = t >> 6;
+    float* G = partial + (size_t)blockIdx.x * NPAD;
+    const float scale = 2.0f / (float)(B * NO);
+    // dY and the squared residuals
+    {
+        const int s = t >> 2, o = t & 3, r = row0 + s;
+        float sq = 0.0f, dy = 0.0f;
+        if (r < B) {
+            const long long row = idx != nullptr ? (long long)idx[r] : (long long)r;
+            const float res = __fsub_rn(sm.Y[s][o], T[row * NO + o]);
+            sq = __fmul_rn(res, res);
+            dy = __fmul_rn(scale, res);
+        }
+        __syncthreads();  // every Y read before it becomes dY
+        sm.Y[s][o] = dy;
+#pragma unroll
+        for (int off = 16; off; off >>= 1) sq = __fadd_rn(sq, __shfl_xor_sync(FULL, sq, off));
+        if ((t & 31) == 0) sm.red[t >> 5] = sq;
+    }
+    __syncthreads();
+    if (t == 0) {
+        float l = 0.0f;
+        for (int w = 0; w < MT / 32; ++w) l = __fadd_rn(l, sm.red[w]);
+        G[NPARAM] = l;
+    }
+    // dW3[o][k] = sum_s dY[s][o] relu(A2[s][k]); db3
+    {
+        const int o = t >> 6, k = t & 63;
+        float acc = 0.0f;
+        for (int s = 0; s < TB; ++s) acc = __fadd_rn(acc, __fmul_rn(sm.Y[s][o], relu(sm.A2[s][k])));
+        G[OFF_W3 + o * NH + k] = acc;
+        if (t < NO) {
+            float b = 0.0f;
+            for (int s = 0; s < TB; ++s) b = __fadd_rn(b, sm.Y[s][t]);
+            G[OFF_B3 + t] = b;
+        }
+    }
+    // dA2[s][j] = (sum_o dY[s][o] W3[o][j]) [A2 > 0]
+    for (int i = 0; i < TB / 4; ++i) {
+        const int s = g * (TB / 4) + i;
+        float a = 0.0f;
+#pragma unroll
+        for (int o = 0; o < NO; ++o) a = __fadd_rn(a, __fmul_rn(sm.Y[s][o], sm.W3[o][j]));
+        sm.D[s][j] = sm.A2[s][j] > 0.0f ? a : 0.0f;
+    }
+    __syncthreads();
+    // dW2[j][k] = sum_s dA2[s][j] relu(A1[s][k]) for k in this thread's 16; db2
+    {
+        float acc[NH / 4];
+#pragma unroll
+        for (int kk = 0; kk < NH / 4; ++kk) acc[kk] = 0.0f;
+        float b = 0.0f;
+        for (int s = 0; s < TB; ++s) {
+            const float a = sm.D[s][j];
+            b = __fadd_rn(b, a);
+#pragma unroll
+            for (int kk = 0; kk < NH / 4; ++kk)
+                acc[kk] = __fadd_rn(acc[kk], __fmul_rn(a, relu(sm.A1[s][g * (NH / 4) + kk])));
+        }
+#pragma unroll
+        for (int kk = 0; kk < NH / 4; ++kk) G[OFF_W2 + j * NH + g * (NH / 4) + kk] = acc[kk];
+        if (g == 0) G[OFF_B2 + j] = b;
+    }
+    // dA1[s][k] = (sum_j dA2[s][j] W2[j][k]) [A1 > 0], into A2's storage (k = this thread's j)
+    {
+        float acc[TB / 4];
+#pragma unroll
+        for (int i = 0; i < TB / 4; ++i) acc[i] = 0.0f;
+        for (int jj = 0; jj < NH; ++jj) {
+            const float w = sm.W2[jj][j];
+#pragma unroll
+            for (int i = 0; i < TB / 4; ++i)
+                acc[i] = __fadd_rn(acc[i], __fmul_rn(sm.D[g * (TB / 4) + i][jj], w));
+        }
+        __syncthreads();  // A2 (read above for dA2) is dead from here on
+#pragma unroll
+        for (int i = 0; i < TB / 4; ++i) {
+            const int s = g * (TB / 4) + i;
+            sm.A2[s][j] = sm.A1[s][j] > 0.0f ? acc[i] : 0.0f;
+        }
+    }
+    __syncthreads();
+    // dW1[j][k] = sum_s dA1[s][j] X[s][k] for k in this thread's 4; db1
+    {
+        float acc[NI / 4];
+#pragma unroll
+        for (int kk = 0; kk < NI / 4; ++kk) acc[kk] = 0.0f;
+        float b = 0.0f;
+        for (int s = 0; s < TB; ++s) {
+            const float a = sm.A2[s][j];
+            b = __fadd_rn(b, a);
+#pragma unroll
+            for (int kk = 0; kk < NI / 4; ++kk)
+                acc[kk] = __fadd_rn(acc[kk], __fmul_rn(a, sm.X[s][g * (NI / 4) + kk]));
+        }
+#pragma unroll
+        for (int kk = 0; kk < NI / 4; ++kk) G[j * NI + g * (NI / 4) + kk] = acc[kk];
+        if (g == 0) G[OFF_B1 + j] = b;
+    }
+}
+
+// Sums the CTAs' partial gradients in CTA order (deterministic).
+__global__ void k_mlp_reduce(const float* partial, int nct, int B, float* grad, float* loss)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > NPARAM) return;
+    float acc = 0.0f;
+    for (int c = 0; c < nct; ++c) acc = __fadd_rn(acc, partial[(size_t)c * NPAD + p]);
+    if (p < NPARAM) grad[p] = acc;
+    else if (loss != nullptr) *loss = acc / (float)(B * NO);
+}
+
+// v <- momentum v + g; p <- p - lr v.
+__global__ void k_mlp_sgd(float* P, float* V, const float* G, float lr, float momentum)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NPARAM) return;
+    const float v = __fadd_rn(__fmul_rn(momentum, V[p]), G[p]);
+    V[p] = v;
+    P[p] = __fsub_rn(P[p], __fmul_rn(lr, v));
+}
+
+// ---- selection: one thread per item -------------------------------------------------
+struct SelectArgs {
+    float link, c[4], c_raw, judge;
+};
+
+__global__ void k_select(Item* items, unsigned n_items, const float* feat, const float* pred,
+                         SelectArgs a, int* choice, unsigned* counts)
+{
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_items) return;
+    Item& it = items[i];
+    const float nf = (float)it.n;
+    const float bytes_in = nf * (it.x_dtype == ZC_F32 ? 4.0f : 2.0f);
+    const float* f = feat + (size_t)i * N_STATS;
+    const float cost_raw = __fadd_rn(__fmul_rn(bytes_in, a.c_raw), __fdiv_rn(__fadd_rn(32.0f, bytes_in), a.link));
+    // the heuristic: L = 32 unless the sampled estimate says coding does not pay
+    int h = 0;
+    if (isfinite(f[1])) {
+        const float c32 = __fadd_rn(__fmul_rn(bytes_in, a.c[1]),
+                                    __fdiv_rn(__fdiv_rn(__fmul_rn(nf, f[1]), 8.0f), a.link));
+        h = c32 < cost_raw ? 32 : 0;
+    }
+    int c = h;
+    bool fell_back = false;
+    if (pred != nullptr) {
+        const float* y = pred + (size_t)i * NO;
+        bool ok = true;
+        for (int k = 0; k < 4; ++k) ok = ok && isfinite(y[k]) && isfinite(f[k]);
+        if (ok) {
+            int kb = 0;
+            float best = 0.0f;
+            for (int k = 0; k < 4; ++k) {
+                const float bits = exp2f(y[k]);
+                const float ck = __fadd_rn(__fmul_rn(bytes_in, a.c[k]),
+                                           __fdiv_rn(__fdiv_rn(__fmul_rn(nf, bits), 8.0f), a.link));
+                if (k == 0 || ck < best) {
+                    best = ck;
+                    kb = k;
+                }
+            }
+            if (fabsf(__fsub_rn(y[kb], log2f(f[kb]))) > a.judge) fell_back = true;
+            else c = best < cost_raw ? (16 << kb) : 0;
+        } else {
+            fell_back = true;
+        }
+    }
+    if (!(it.two_eb > 0.0f)) c = 0;  // planned without a bound: raw only
+    it.log2L = c == 16 ? 4 : c == 32 ? 5 : c == 64 ? 6 : c == 128 ? 7 : -1;
+    if (choice != nullptr) choice[i] = c;
+    if (counts != nullptr) {
+        if (fell_back) atomicAdd(counts, 1u);
+        if (c == 0) atomicAdd(counts + 1, 1u);
+    }
+}
+
+}  // namespace zc
+
+using namespace zc;
+
+extern "C" {
+
+int zc_batch_chunk_stats(const zc_batch* plan, float* d_feat, zc_stream_t s)
+{
+    if (plan == nullptr || plan->d_table == nullptr || plan->n_msgs < 1 || plan->decompress != 0 ||
+        d_feat == nullptr || (reinterpret_cast<uintptr_t>(d_feat) & 3) != 0)
+        return ZC_ERR_ARG;
+    const unsigned n = (unsigned)plan->n_msgs;
+    k_chunk_stats<<<(n + 7) / 8, 256, 0, (cudaStream_t)s>>>((const Item*)plan->d_table, n, d_feat);
+    return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
+}
+
+static cudaError_t mlp_prepare()
+{
+    static const cudaError_t e1 = cudaFuncSetAttribute(
+        k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem));
+    static const cudaError_t e2 = cudaFuncSetAttribute(
+        k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem));
+    return e1 != cudaSuccess ? e1 : e2;
+}
+
+int zc_mlp_forward(const float* d_params, const float* d_norm, const float* d_x, int B,
+                   float* d_y, zc_stream_t s)
+{
+    if (d_params == nullptr || d_norm == nullptr || B < 0 || (B > 0 && (d_x == nullptr || d_y == nullptr)))
+        return ZC_ERR_ARG;
+    if (B == 0) return ZC_OK;
+    if (mlp_prepare() != cudaSuccess) return ZC_ERR_CUDA;
+    k_mlp_forward<<<(B + TB - 1) / TB, MT, sizeof(MlpSmem), (cudaStream_t)s>>>(d_params, d_norm,
+                                                                               d_x, B, d_y);
+    return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
+}
+
+size_t zc_mlp_scratch_bytes(int B)
+{
+    if (B < 1) return 0;
+    return (size_t)((B + TB - 1) / TB) * NPAD * sizeof(float);
+}
+
+int zc_mlp_grad(const float* d_params, const float* d_norm, const float* d_x, const float* d_t,
+                const int* d_idx, int B, float* d_grad, float* d_loss, void* d_scratch,
+                size_t scratch_bytes, zc_stream_t s)
+{
+    if (d_params == nullptr || d_norm == nullptr || d_x == nullptr || d_t == nullptr || B < 1 ||
+        d_grad == nullptr || d_scratch == nullptr || scratch_bytes < zc_mlp_scratch_bytes(B) ||
+        (reinterpret_cast<uintptr_t>(d_scratch) & 3) != 0)
+        return ZC_ERR_ARG;
+    if (mlp_prepare() != cudaSuccess) return ZC_ERR_CUDA;
+    const int nct = (B + TB - 1) / TB;
+    k_mlp_grad<<<nct, MT, sizeof(MlpSmem), (cudaStream_t)s>>>(d_params, d_norm, d_x, d_t, d_idx, B,
+                                                             (float*)d_scratch);
+    if (cudaGetLastError() != cudaSuccess) return ZC_ERR_CUDA;
+    k_mlp_reduce<<<(NPARAM + 1 + 255) / 256, 256, 0, (cudaStream_t)s>>>((const float*)d_scratch, nct,
+                                                                       B, d_grad, d_loss);
+    return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
+}
+
+int zc_mlp_sgd(float* d_params, float* d_vel, const float* d_grad, float lr, float momentum,
+               zc_stream_t s)
+{
+    if (d_params == nullptr || d_vel == nullptr || d_grad == nullptr) return ZC_ERR_ARG;
+    k_mlp_sgd<<<(NPARAM + 255) / 256, 256, 0, (cudaStream_t)s>>>(d_params, d_vel, d_grad, lr,
+                                                                 momentum);
+    return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
+}
+
+int zc_batch_select(const zc_batch* plan, const float* d_feat, const float* d_pred,
+                    const zc_select_cfg* cfg, int* d_choice, unsigned* d_counts, zc_stream_t s)
+{
+    if (plan == nullptr || plan->d_table == nullptr || plan->n_msgs < 1 || plan->decompress != 0 ||
+        d_feat == nullptr || cfg == nullptr || !(cfg->link_gbs > 0.0f) || !(cfg->judge_log2 >= 0.0f))
+        return ZC_ERR_ARG;
+    SelectArgs a;
+    a.link = cfg->link_gbs;
+    for (int k = 0; k < 4; ++k) a.c[k] = cfg->ns_per_byte[k];
+    a.c_raw = cfg->raw_ns_per_byte;
+    a.judge = cfg->judge_log2;
+    if (d_counts != nullptr &&
+        cudaMemsetAsync(d_counts, 0, 2 * sizeof(unsigned), (cudaStream_t)s) != cudaSuccess)
+        return ZC_ERR_CUDA;
+    const unsigned n = (unsigned)plan->n_msgs;
+    k_select<<<(n + 255) / 256, 256, 0, (cudaStream_t)s>>>((Item*)plan->d_table, n, d_feat, d_pred,
+                                                           a, d_choice, d_counts);
+    return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
+}
+
+}  // extern "C"

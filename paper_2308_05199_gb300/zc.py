@@ -73,6 +73,15 @@ class ZcTunePoint(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ZcSelectCfg(ctypes.Structure):
+    _fields_ = [("link_gbs", ctypes.c_float), ("ns_per_byte", ctypes.c_float * 4),
+                ("raw_ns_per_byte", ctypes.c_float), ("judge_log2", ctypes.c_float)]
+
+
+N_STATS = 16
+MLP_PARAMS = 5508
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -121,6 +130,13 @@ def _declare(L):
         "zc_autotune_batch": (i32, [i32, c.POINTER(ZcMessage), i32, dbl, i32, vp, sz, vp, vp, sz,
                                     vp, sz, vp, c.POINTER(ZcTunePoint), i32, c.POINTER(i32),
                                     c.POINTER(ZcTunePoint)]),
+        "zc_batch_chunk_stats": (i32, [c.POINTER(ZcBatch), vp, vp]),
+        "zc_mlp_forward": (i32, [vp, vp, vp, i32, vp, vp]),
+        "zc_mlp_scratch_bytes": (sz, [i32]),
+        "zc_mlp_grad": (i32, [vp, vp, vp, vp, vp, i32, vp, vp, vp, sz, vp]),
+        "zc_mlp_sgd": (i32, [vp, vp, vp, c.c_float, c.c_float, vp]),
+        "zc_batch_select": (i32, [c.POINTER(ZcBatch), vp, vp, c.POINTER(ZcSelectCfg), vp, vp,
+                                  vp]),
         "zc_graph_begin": (i32, [vp]),
         "zc_graph_end": (i32, [vp, c.POINTER(vp)]),
         "zc_graph_launch": (i32, [vp, vp]),
@@ -144,7 +160,9 @@ def exported_names():
             "zc_plan_table_bytes", "zc_plan_reduce", "zc_reduce_step_batch", "zc_scatter_pack",
             "zc_compress_noalloc", "zc_batch_table_bytes", "zc_batch_max_bytes",
             "zc_plan_compress_batch", "zc_compress_batch", "zc_plan_decompress_batch",
-            "zc_decompress_batch", "zc_autotune_batch", "zc_graph_begin", "zc_graph_end",
+            "zc_decompress_batch", "zc_autotune_batch", "zc_batch_chunk_stats", "zc_mlp_forward",
+            "zc_mlp_scratch_bytes", "zc_mlp_grad", "zc_mlp_sgd", "zc_batch_select",
+            "zc_graph_begin", "zc_graph_end",
             "zc_graph_launch", "zc_graph_destroy",
             "zc_get_device_status", "zc_clear_device_status", "zc_set_wait_limit_ns",
             "zc_debug_withhold_tile", "zc_set_tile_chunks", "zc_version"]
@@ -272,6 +290,33 @@ def zc_autotune_batch(n_msgs, h_msgs, tune_block, link_gbs, reps, d_packed, pack
     return lib().zc_autotune_batch(n_msgs, h_msgs, tune_block, link_gbs, reps, d_packed,
                                    packed_cap, d_msg_off, d_table, table_bytes, d_ws, ws_bytes,
                                    stream, h_points, max_points, n_points, best)
+
+
+def zc_batch_chunk_stats(plan, d_feat, stream) -> int:
+    return lib().zc_batch_chunk_stats(ctypes.byref(plan), d_feat, stream)
+
+
+def zc_mlp_forward(d_params, d_norm, d_x, B, d_y, stream) -> int:
+    return lib().zc_mlp_forward(d_params, d_norm, d_x, B, d_y, stream)
+
+
+def zc_mlp_scratch_bytes(B: int) -> int:
+    return lib().zc_mlp_scratch_bytes(B)
+
+
+def zc_mlp_grad(d_params, d_norm, d_x, d_t, d_idx, B, d_grad, d_loss, d_scratch, scratch_bytes,
+                stream) -> int:
+    return lib().zc_mlp_grad(d_params, d_norm, d_x, d_t, d_idx, B, d_grad, d_loss, d_scratch,
+                             scratch_bytes, stream)
+
+
+def zc_mlp_sgd(d_params, d_vel, d_grad, lr, momentum, stream) -> int:
+    return lib().zc_mlp_sgd(d_params, d_vel, d_grad, lr, momentum, stream)
+
+
+def zc_batch_select(plan, d_feat, d_pred, cfg, d_choice, d_counts, stream) -> int:
+    return lib().zc_batch_select(ctypes.byref(plan), d_feat, d_pred, ctypes.byref(cfg), d_choice,
+                                 d_counts, stream)
 
 
 def zc_graph_begin(stream) -> int:
