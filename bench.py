@@ -1,22 +1,32 @@
 """Benchmark of the codec hot path on one GB300 (replicas across GPUs).
 
-Workload: the 512^3 FP32 Gaussian random field (P(k) ~ k^-3, scaled to
-[-1, 1], 512 MiB), relative error bound 1e-3, block size 32.  One step runs
-every hot-path kernel once over that field, each from its own inputs:
+One step runs every hot-path kernel once, each from its own inputs already
+resident in HBM:
 
-  range + compress   field -> stream (the bound resolved on the device)
-  decompress         stream -> FP32 field
-  ring step          8 chunks: decode received stream + add local chunk +
-                     re-encode (one batched launch, the fixed ring bound)
+  range + compress   512^3 FP32 Gaussian random field (P(k) ~ k^-3, scaled to
+                     [-1, 1], 512 MiB), relative bound 1e-3, L = 32
+  decompress         that stream -> FP32 field
+  ring step          8 chunks of the field: decode received stream + add the
+                     local chunk + re-encode (one batched launch, fixed bound)
   scatter pack       8 segments compressed as independent packed streams
+  batched compress   1000 messages, 4 KiB - 64 MiB log-uniform, half FP32 /
+                     half BF16, Student-t(3) x sigma, eb = 1e-3 sigma: one
+                     persistent launch (autotuned tile and grid) from a CUDA
+                     graph
+  selector path      a held-out mixed workload (about 4 GiB of the four
+                     workload kinds) cut into 64 KiB chunks: statistics, MLP,
+                     selection of block size or raw, batched compression, all
+                     from one CUDA graph (network trained at set-up on 10^5
+                     chunks by the library's own gradient and SGD kernels)
 
 ``value`` is the algorithmic bytes of one step (every kernel's input read
 plus output written, the extra input read of the relative bound included)
 divided by the device time of the step (CUDA events on the launch stream),
-summed over ranks.  Inputs (1 GiB) exceed the 129 MB L2, so no flush is
-needed between steps.  ``e2e`` repeats the step through the same C ABI with
-the inputs copied from pinned host memory and the compressed stream copied
-back inside the timed region.
+summed over ranks.  Inputs exceed the 129 MB L2, so no flush is needed.
+``e2e`` repeats the step through the same C ABI with every input copied from
+pinned host memory and every compressed output copied back, in the timed
+region.  ``batched`` and ``selector`` report the comparisons of those two
+paths with the plain per-message form.
 
 --impl reference times the CPU oracle (test infrastructure, the only other
 place this file runs it) on a bounded sample of the same workload.
@@ -52,6 +62,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--chunks", type=int, default=0, help="2048-element chunks per CTA tile")
+    ap.add_argument("--train-chunks", type=int, default=100000,
+                    help="64 KiB chunks the selector's network is trained on")
+    ap.add_argument("--heldout-gib", type=float, default=4.0,
+                    help="size of the selector's held-out mixed workload")
+    ap.add_argument("--epochs", type=int, default=60)
     return ap.parse_args()
 
 
@@ -155,9 +170,9 @@ class Workload:
         self.field = workloads.grf_3d(side=side, seed=2000, device=device)
         self.local = workloads.grf_3d(side=side, seed=2001, device=device)
         t = torch
-        self.stream = t.cuda.current_stream()
+        self.stream = t.cuda.Stream(device=device)  # capturable (not the legacy stream)
         self.s = self.stream.cuda_stream
-        self.ws = zc.Workspace(n, P_RING + 1)
+        self.ws = zc.Workspace(n, P_RING + 1, device, self.stream)
         self.cap = zc.zc_max_compressed_bytes(n, BLOCK)
         self.cmp = t.empty(self.cap, dtype=t.uint8, device=device)
         self.cmp_n = t.zeros(1, dtype=t.int64, device=device)
@@ -166,6 +181,7 @@ class Workload:
         mm = t.zeros(2, dtype=t.float32, device=device)
         assert zc.zc_minmax(self.field.data_ptr(), n, 0, mm.data_ptr(), self.ws.ptr,
                             self.ws.nbytes, self.s) == 0
+        self.stream.synchronize()
         lo, hi = mm.tolist()
         self.eb_abs = REL * (float(hi) - float(lo))
         # ring step inputs: the field's chunks compressed (the received streams)
@@ -199,30 +215,38 @@ class Workload:
         self.pcap = P_RING * self.ccap
         self.packed = t.empty(self.pcap, dtype=t.uint8, device=device)
         self.seg = t.zeros(P_RING + 1, dtype=t.int64, device=device)
-        # range, compress, width scan, decompress, width scan, ring step, scatter pack
-        self.launches_per_step = 7
+        # range, compress, width scan, decompress, width scan, ring step, scatter pack,
+        # batched compress, selector (statistics, MLP, selection, batched compress)
+        self.launches_per_step = 12
 
     def step(self, ev=None):
         zc, s, ws = self.zc, self.s, self.ws
+        st = self.stream
         if ev:
-            ev[0].record()
+            ev[0].record(st)
         assert zc.zc_compress(self.field.data_ptr(), self.n, 0, zc.EB_REL, REL, BLOCK,
                               self.cmp.data_ptr(), self.cap, self.cmp_n.data_ptr(), ws.ptr,
                               ws.nbytes, s) == 0
         if ev:
-            ev[1].record()
+            ev[1].record(st)
         assert zc.zc_decompress(self.cmp.data_ptr(), self.cap, self.dec.data_ptr(), self.n, 0,
                                 ws.ptr, ws.nbytes, s) == 0
         if ev:
-            ev[2].record()
+            ev[2].record(st)
         assert zc.zc_reduce_step_batch(self.plan, ws.ptr, ws.nbytes, s) == 0
         if ev:
-            ev[3].record()
+            ev[3].record(st)
         assert zc.zc_scatter_pack(self.field.data_ptr(), 0, P_RING, self.hc, self.hd, zc.EB_ABS,
                                   self.eb_abs, BLOCK, self.packed.data_ptr(), self.pcap,
                                   self.seg.data_ptr(), ws.ptr, ws.nbytes, s) == 0
         if ev:
-            ev[4].record()
+            ev[4].record(st)
+        self.batch_row.graph.launch()
+        if ev:
+            ev[5].record(st)
+        self.sel_row.graph.launch()
+        if ev:
+            ev[6].record(st)
 
     def sizes(self):
         C = int(self.cmp_n.item())
@@ -235,8 +259,221 @@ class Workload:
             "decompress": C + n4,
             "ring_step": cin + n4 + cout,
             "scatter_pack": n4 + packed,
+            "batched_compress": self.batch_row.step_bytes(),
+            "selector_compress": self.sel_row.step_bytes(),
         }
         return C, parts
+
+
+class BatchRow:
+    """Batched compression of the 1000-message workload: one persistent
+    launch (tile size and grid from the library's autotuner) in a CUDA graph,
+    against the plain form (one zc_compress per message)."""
+
+    M = 1000
+
+    def __init__(self, torch, zc, workloads, stream, device):
+        self.torch, self.zc, self.stream = torch, zc, stream
+        specs = workloads.message_specs(self.M)
+        with torch.cuda.stream(stream):
+            self.xs = [workloads.message(sp, device=device) for sp in specs]
+        stream.synchronize()
+        self.ebs = [sp["eb"] for sp in specs]
+        self.raw = sum(x.numel() * x.element_size() for x in self.xs)
+        self.n_f32 = sum(1 for sp in specs if sp["dtype"] == "f32")
+        self.b = zc.BatchCompress(self.xs, [32] * self.M, self.ebs, stream=stream)
+        self.best, self.points = self.b.autotune(tune_block=False, link_gbs=0.0, reps=3,
+                                                 stream=stream)
+        self.b.run(stream)
+        stream.synchronize()
+        self.graph = zc.Graph(stream)
+        with self.graph.capture():
+            self.b.run(stream)
+
+    def step_bytes(self):
+        return self.raw + int(self.b.msg_off[-1].item())
+
+    def compare(self, reps=5):
+        """Device ms of the graph launch vs the per-message loop (same streams
+        byte for byte: checked on the total length)."""
+        torch, zc, st = self.torch, self.zc, self.stream
+        outs = [torch.empty(zc.zc_max_compressed_bytes(x.numel(), 32), dtype=torch.uint8,
+                            device=x.device) for x in self.xs]
+        obs = torch.zeros(self.M, dtype=torch.int64, device=self.xs[0].device)
+        ws = self.b.ws
+
+        def loop():
+            for i, x in enumerate(self.xs):
+                zc._check(zc.zc_compress(x.data_ptr(), x.numel(), zc.dtype_code(x), zc.EB_ABS,
+                                         self.ebs[i], 32, outs[i].data_ptr(), outs[i].numel(),
+                                         obs.data_ptr() + 8 * i, ws.ptr, ws.nbytes,
+                                         st.cuda_stream), "zc_compress")
+
+        def timed(f):
+            f()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                f()
+            e1.record(st)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        loop_ms = timed(loop)
+        batch_ms = timed(self.graph.launch)
+        same = int(obs.sum().item()) == int(self.b.msg_off[-1].item())
+        del outs
+        return {"messages": self.M, "fp32_messages": self.n_f32, "raw_bytes": self.raw,
+                "ratio": round(self.raw / int(self.b.msg_off[-1].item()), 4),
+                "per_message_loop_ms": round(loop_ms, 3), "batched_graph_ms": round(batch_ms, 3),
+                "speedup": round(loop_ms / batch_ms, 2),
+                "per_message_loop_gbs": round(self.step_bytes() / loop_ms / 1e6, 1),
+                "batched_gbs": round(self.step_bytes() / batch_ms / 1e6, 1),
+                "same_total_bytes": same,
+                "autotuned": {"tile_chunks": self.best["tile_chunks"], "grid": self.best["grid"],
+                              "candidates": len(self.points)}}
+
+
+class SelectorRow:
+    """The learned per-chunk selector on a held-out mixed workload: network
+    trained at set-up (10^5 chunks of the four workload kinds, labels from the
+    codec at every L), then statistics + MLP + selection + batched compression
+    from one CUDA graph."""
+
+    LINK_GBS = 12.5  # the paper's 100 Gb/s network, as a model parameter
+
+    def __init__(self, torch, zc, stream, device, train_chunks, heldout_bytes, epochs):
+        from paper_2308_05199_gb300 import selector as S
+        self.torch, self.zc, self.S, self.stream = torch, zc, S, stream
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            tv, te, _ = S.mixed_chunks(train_chunks, seed=1, device=device)
+        tr = S.ChunkBatch(tv, te, stream=stream)
+        self.cfg = {}
+        for link in (self.LINK_GBS, 100.0):
+            self.cfg[link] = tr.cost_model(link_gbs=link)
+        X, T, keep, _ = S.dataset(tr)
+        self.mlp = S.Mlp(seed=0)
+        self.mlp.set_norm(X)
+        t1 = time.perf_counter()
+        self.hist = self.mlp.fit(X, T, epochs=epochs, batch=256, lr=0.02, momentum=0.9, seed=0,
+                                 stream=stream)
+        stream.synchronize()
+        self.train_s = time.perf_counter() - t1
+        self.n_train = int(keep.sum())
+        self.setup_s = t1 - t0
+        del tr, tv, te, X, T
+        torch.cuda.empty_cache()
+        with torch.cuda.stream(stream):
+            xs, ebs, kinds = S.mixed_messages(heldout_bytes, seed=7, device=device)
+        stream.synchronize()
+        self.xs, self.ebs = xs, ebs
+        hv, he = S.split_chunks(xs, ebs)
+        self.cb = S.ChunkBatch(hv, he, stream=stream)
+        cfg = self.cfg[self.LINK_GBS]
+        self.cb.run_selected(cfg, self.mlp)
+        stream.synchronize()
+        self.graph = zc.Graph(stream)
+        with self.graph.capture():
+            self.cb.run_selected(cfg, self.mlp)
+
+    def step_bytes(self):
+        # sampled statistics read + codec read + packed write (the network and
+        # the selection touch a few bytes per chunk)
+        sample = int(sum(min(v.numel(), 2048) * v.element_size() for v in self.cb.views))
+        return sample + self.cb.raw_bytes + int(self.cb.batch.msg_off[-1].item())
+
+    def breakdown(self, cfg, reps=3):
+        """Device ms of each launch of the learned selector path, and of the
+        batched decompression of its output."""
+        torch, zc, st, cb = self.torch, self.zc, self.stream, self.cb
+        parts = [("stats", cb.stats),
+                 ("mlp_forward", lambda: self.mlp.forward(cb.feat, out=cb.pred, stream=st)),
+                 ("select", lambda: cb.select(cfg, cb.pred)),
+                 ("compress", lambda: cb.batch.run(st)),
+                 ("decompress", lambda: cb.dec.run(st))]
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)]
+               for _ in range(reps + 1)]
+        for r in range(reps + 1):
+            evs[r][0].record(st)
+            for i, (_, f) in enumerate(parts):
+                f()
+                evs[r][i + 1].record(st)
+        st.synchronize()
+        return {nm: round(statistics.median(evs[r][i].elapsed_time(evs[r][i + 1])
+                                            for r in range(1, reps + 1)), 4)
+                for i, (nm, _) in enumerate(parts)}
+
+    def report(self, reps=3):
+        """Mispredicts and modelled end-to-end GB/s of the plain per-message
+        form, the batched heuristic and the batched learned selector."""
+        torch, zc, S, st = self.torch, self.zc, self.S, self.stream
+        cb = self.cb
+        bits = cb.true_bits()
+        ev = lambda: torch.cuda.Event(enable_timing=True)
+        out = {"train_chunks": self.n_train, "epochs": len(self.hist),
+               "loss_first": round(self.hist[0], 5), "loss_last": round(self.hist[-1], 5),
+               "train_s": round(self.train_s, 2), "heldout_chunks": cb.M,
+               "heldout_bytes": cb.raw_bytes, "messages": len(self.xs), "links": {}}
+        # plain per-message form: one zc_compress + one zc_decompress per whole message, L = 32
+        outs = [torch.empty(zc.zc_max_compressed_bytes(x.numel(), 32), dtype=torch.uint8,
+                            device=x.device) for x in self.xs]
+        decs = [torch.empty_like(x) for x in self.xs]
+        obs = torch.zeros(len(self.xs), dtype=torch.int64, device=self.xs[0].device)
+        ws = cb.batch.ws
+
+        def plain():
+            for i, x in enumerate(self.xs):
+                zc._check(zc.zc_compress(x.data_ptr(), x.numel(), zc.dtype_code(x), zc.EB_ABS,
+                                         self.ebs[i], 32, outs[i].data_ptr(), outs[i].numel(),
+                                         obs.data_ptr() + 8 * i, ws.ptr, ws.nbytes,
+                                         st.cuda_stream), "zc_compress")
+            for i, x in enumerate(self.xs):
+                zc._check(zc.zc_decompress(outs[i].data_ptr(), outs[i].numel(), decs[i].data_ptr(),
+                                           x.numel(), zc.dtype_code(x), ws.ptr, ws.nbytes,
+                                           st.cuda_stream), "zc_decompress")
+
+        def timed(f):
+            f()
+            e0, e1 = ev(), ev()
+            e0.record(st)
+            for _ in range(reps):
+                f()
+            e1.record(st)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        plain_ms = timed(plain)
+        plain_bytes = int(obs.sum().item())
+        raw = cb.raw_bytes
+        for link, cfg in self.cfg.items():
+            rec = {"plain_per_message": {
+                "device_ms": round(plain_ms, 3), "bytes": plain_bytes,
+                "e2e_gbs": round(raw / (plain_ms * 1e6 + plain_bytes / link), 3)}}
+            for name, mlp in (("batched_heuristic", None), ("batched_learned", self.mlp)):
+                ms = timed(lambda: (cb.run_selected(cfg, mlp), cb.dec.run(st)))
+                choice = cb.choice.cpu().numpy().copy()
+                counts = cb.counts.cpu().numpy()
+                ev_ = S.evaluate(choice, cb.n, cb.es, bits, cfg)
+                packed = int(cb.batch.msg_off[-1].item())
+                rec[name] = {"device_ms": round(ms, 3), "bytes": packed,
+                             "e2e_gbs": round(raw / (ms * 1e6 + packed / link), 3),
+                             "mispredict": round(ev_["mispredict"], 4),
+                             "regret": round(ev_["regret"], 5),
+                             "raw_frac": round(ev_["raw_frac"], 4),
+                             "fallbacks": int(counts[0]) if mlp is not None else None,
+                             "blocks": {str(b): int((choice == b).sum())
+                                        for b in (16, 32, 64, 128, 0)}}
+            rec["cost_model_ns_per_byte"] = {"L16": cfg.ns_per_byte[0], "L32": cfg.ns_per_byte[1],
+                                              "L64": cfg.ns_per_byte[2], "L128": cfg.ns_per_byte[3],
+                                              "raw": cfg.raw_ns_per_byte}
+            out["links"][str(link)] = rec
+        out["breakdown_ms"] = self.breakdown(self.cfg[self.LINK_GBS])
+        # leave the plan as the graph expects it
+        cb.run_selected(self.cfg[self.LINK_GBS], self.mlp)
+        st.synchronize()
+        del outs, decs
+        return out
 
 
 def run_ours(args, rank, world):
@@ -249,9 +486,15 @@ def run_ours(args, rank, world):
     if args.chunks:
         assert zc.zc_set_tile_chunks(args.chunks) == 0
     W = Workload(torch, zc, workloads, args.side, dev)
+    W.batch_row = BatchRow(torch, zc, workloads, W.stream, dev)
+    W.sel_row = SelectorRow(torch, zc, W.stream, dev, args.train_chunks,
+                            int(args.heldout_gib * (1 << 30)), args.epochs)
     args.warmup = max(args.warmup, 3)
     for _ in range(args.warmup):
         W.step()
+    torch.cuda.synchronize()
+    batched = W.batch_row.compare()
+    selector = W.sel_row.report()
     torch.cuda.synchronize()
     st, det = W.ws.status()
     if st != 0:
@@ -261,7 +504,7 @@ def run_ours(args, rank, world):
 
     # timed region: K steps, per-kernel events on the launch stream
     K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(K)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(K)]
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -269,10 +512,10 @@ def run_ours(args, rank, world):
     with ClockSampler(dev.index) as clk:
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
-        t0.record()
+        t0.record(W.stream)
         for k in range(K):
             W.step(evs[k])
-        t1.record()
+        t1.record(W.stream)
         torch.cuda.synchronize()
     total_ms = t0.elapsed_time(t1)
     if world > 1:
@@ -283,7 +526,8 @@ def run_ours(args, rank, world):
     st, det = W.ws.status()
     if st != 0:
         raise RuntimeError("device status %d at %d in the timed region" % (st, det))
-    names = ["compress", "decompress", "ring_step", "scatter_pack"]
+    names = ["compress", "decompress", "ring_step", "scatter_pack", "batched_compress",
+             "selector_compress"]
     per = {nm: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K))
            for i, nm in enumerate(names)}
     ms_per_step = total_ms / K
@@ -301,11 +545,16 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic (seeded 512^3 Gaussian random field, P(k)~k^-3, in place of the "
-                "paper's RTM volumes)",
-        "config": {"workload": "grf512_rel1e-3_L32", "n": W.n, "rel_eb": REL,
+        "data": "synthetic, seeded: 512^3 Gaussian random field (P(k)~k^-3) in place of the "
+                "paper's RTM volumes; Student-t messages; mixed held-out workload of the four "
+                "kinds",
+        "config": {"workload": "grf512_rel1e-3_L32+batch1000+selector_heldout",
+                   "n": W.n, "rel_eb": REL,
                    "eb_abs_ring": W.eb_abs, "block": BLOCK, "ring_ranks": P_RING,
-                   "scatter_segments": P_RING, "l2": "inputs larger than L2 (no flush)"},
+                   "scatter_segments": P_RING, "batch_messages": BatchRow.M,
+                   "selector_heldout_bytes": W.sel_row.cb.raw_bytes,
+                   "selector_chunks": W.sel_row.cb.M,
+                   "l2": "inputs larger than L2 (no flush)"},
         "ratio": round(4 * W.n / C, 3),
         "kernels_gbs": {k: round(v, 1) for k, v in kern_gbs.items()},
         "kernels_ms": {k: round(v, 4) for k, v in per.items()},
@@ -313,6 +562,8 @@ def run_ours(args, rank, world):
         "roofline": roofline,
         "gpu_launches": W.launches_per_step * K,
         "clocks": clk.summary(),
+        "batched": batched,
+        "selector": selector,
     }
     if not args.no_e2e:
         out["e2e"] = e2e_ours(torch, W, args, step_bytes, world)
@@ -320,23 +571,35 @@ def run_ours(args, rank, world):
 
 
 def e2e_ours(torch, W, args, step_bytes, world):
-    """Same step with the two input fields copied in from pinned host memory
-    and the compressed stream copied back, inside the timed region."""
-    hf = W.field.cpu().pin_memory()
-    hl = W.local.cpu().pin_memory()
-    hout = torch.empty(W.cap, dtype=torch.uint8).pin_memory()
-    hn = torch.zeros(1, dtype=torch.int64).pin_memory()
-    K = max(3, args.steps // 2)
-    C = int(W.cmp_n.item())
+    """The same step with every input (the two fields, the 1000 messages, the
+    held-out workload) copied in from pinned host memory and every compressed
+    output (the field's stream, both packed batches) copied back, inside the
+    timed region, all on the step's stream."""
+    st = W.stream
+    dev_in = [W.field, W.local] + W.batch_row.xs + W.sel_row.xs
+    host_in = [t.cpu().pin_memory() for t in dev_in]
+    outs = [(W.cmp, W.cmp_n[0:1]), (W.batch_row.b.packed, W.batch_row.b.msg_off[-1:]),
+            (W.sel_row.cb.batch.packed, W.sel_row.cb.batch.msg_off[-1:])]
+    host_out = [torch.empty(o.numel(), dtype=torch.uint8).pin_memory() for o, _ in outs]
+    host_len = torch.zeros(len(outs), dtype=torch.int64).pin_memory()
+    K = max(3, args.steps // 4)
+    stats = {"d2h": 0}
 
     def one():
-        W.field.copy_(hf, non_blocking=True)
-        W.local.copy_(hl, non_blocking=True)
-        W.step()
-        hn.copy_(W.cmp_n, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        c = int(hn.item())
-        hout[:c].copy_(W.cmp[:c], non_blocking=True)
+        with torch.cuda.stream(st):
+            for d, h in zip(dev_in, host_in):
+                d.copy_(h, non_blocking=True)
+            W.step()
+            for i, (_, ln) in enumerate(outs):
+                host_len[i:i + 1].copy_(ln, non_blocking=True)
+            st.synchronize()
+            d2h = 0
+            for i, (o, _) in enumerate(outs):
+                c = int(host_len[i])
+                host_out[i][:c].copy_(o[:c], non_blocking=True)
+                d2h += c + 8
+            st.synchronize()
+        stats["d2h"] = d2h
 
     for _ in range(2):
         one()
@@ -346,19 +609,27 @@ def e2e_ours(torch, W, args, step_bytes, world):
         one()
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t) / K
+    h2d = sum(h.numel() * h.element_size() for h in host_in)
     return {"value": round(step_bytes * world / dt / 1e9, 1), "unit": "GB/s",
-            "h2d_bytes_per_step": 8 * W.n, "d2h_bytes_per_step": C + 8,
-            "ms_per_step": round(dt * 1e3, 3)}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": stats["d2h"],
+            "ms_per_step": round(dt * 1e3, 3), "steps": K}
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and --impl reference)
 
-def oracle_step(x, loc, sample_n):
-    """The bench step on the first sample_n elements, run by the CPU oracle;
-    returns (seconds, algorithmic bytes).  The ring step's received streams
-    are prepared outside the timed part (they are that step's input)."""
+def oracle_step(x, loc, sample_n, msgs, chunks):
+    """The bench step on bounded samples, run by the CPU oracle; returns
+    (seconds, algorithmic bytes).  Samples: the first sample_n elements of
+    the field (range, compress, decompress, ring step over 8 chunks, scatter
+    pack of 8 segments), the first messages of the 1000-message workload
+    (one compression each), and 64 KiB chunks through the selector
+    (statistics, network, choice, compression).  The ring step's received
+    streams are prepared outside the timed part (they are that step's
+    input)."""
+    import numpy as np
     import oracle
+    from oracle import selector as OS
     xs, ls = x[:sample_n], loc[:sample_n]
     m = sample_n // P_RING
     t0 = time.perf_counter()
@@ -371,42 +642,78 @@ def oracle_step(x, loc, sample_n):
     t2 = time.perf_counter()
     cout = [oracle.reduce_step(cin[r], ls[r * m:(r + 1) * m], eb, 5)[0] for r in range(P_RING)]
     packed, _ = oracle.scatter_pack(xs, [m] * P_RING, [r * m for r in range(P_RING)], eb, 5)
+    batch_out = sum(len(oracle.compress(a, e, 5)) for a, e in msgs)
+    feats = np.array([OS.chunk_stats(a, e) for a, e in chunks])
+    params = OS.init_params(0).astype(np.float64)
+    norm = np.concatenate([np.zeros(16), np.ones(16)])
+    pred = OS.forward(params, norm, np.nan_to_num(feats))
+    cfg = {"link_gbs": 12.5, "ns_per_byte": [0.0] * 4, "raw_ns_per_byte": 0.0, "judge_log2": 1.0}
+    sel_out = 0
+    for (a, e), f, y in zip(chunks, feats, pred):
+        c, _ = OS.mlp_choice(a.size, a.itemsize, f, y, cfg)
+        sel_out += len(oracle.compress_raw(a) if c == 0 else oracle.compress(a, e, c.bit_length() - 1))
     t3 = time.perf_counter()
     secs = (t1 - t0) + (t3 - t2)
     n4 = 4 * sample_n
+    raw_msgs = sum(a.nbytes for a, _ in msgs)
+    raw_chunks = sum(a.nbytes for a, _ in chunks)
     nbytes = (n4 + n4 + len(s)) + (len(s) + n4) + \
-        (sum(map(len, cin)) + n4 + sum(map(len, cout))) + (n4 + len(packed))
+        (sum(map(len, cin)) + n4 + sum(map(len, cout))) + (n4 + len(packed)) + \
+        (raw_msgs + batch_out) + (raw_chunks + sel_out)
     return secs, nbytes
 
 
 def cpu_fields(side):
+    """The field, the local field, a sample of the 1000-message workload (the
+    first messages that fit in 16 MiB together, at most 64) and 16 chunks of 64 KiB (8 of the field, 8 of
+    the messages), as numpy arrays (BF16 as uint16 bits)."""
     import torch
     from paper_2308_05199_gb300 import workloads
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     x = workloads.grf_3d(side=side, seed=2000, device=dev).cpu().numpy()
     loc = workloads.grf_3d(side=side, seed=2001, device=dev).cpu().numpy()
-    return x, loc
+    msgs, tot = [], 0
+    for sp in workloads.message_specs(1000):
+        t = workloads.message(sp, device=dev)
+        a = t.cpu().numpy() if t.dtype == torch.float32 else workloads.bf16_bits(t)
+        if tot + a.nbytes > 16 << 20:
+            continue  # keep the sample bounded: skip what does not fit
+        msgs.append((a, sp["eb"]))
+        tot += a.nbytes
+        if len(msgs) >= 64:
+            break
+    eb_x = REL * float(x.max() - x.min())
+    chunks = [(x[i * (x.size // 8):i * (x.size // 8) + 16384], eb_x) for i in range(8)]
+    for a, e in msgs:
+        if len(chunks) >= 16:
+            break
+        per = 65536 // a.itemsize
+        chunks.append((a[:per], e))
+    return x, loc, msgs, chunks
 
 
 def cpu_baseline(side, sample_n=1 << 25):
-    x, loc = cpu_fields(side)
+    x, loc, msgs, chunks = cpu_fields(side)
     sample_n = min(sample_n, x.size)
-    secs, nbytes = oracle_step(x, loc, sample_n)
+    secs, nbytes = oracle_step(x, loc, sample_n, msgs, chunks)
     return {"value": round(nbytes / secs / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": "first %d elements of the same field (one step: range, compress, "
-                      "decompress, ring step over 8 chunks, scatter pack of 8 segments), "
-                      "single-threaded plain C" % sample_n,
+            "sample": "first %d elements of the same field (range, compress, decompress, "
+                      "ring step over 8 chunks, scatter pack of 8 segments), the first %d of the "
+                      "1000 messages, %d chunks of 64 KiB through the selector; single-threaded "
+                      "plain C and numpy" % (sample_n, len(msgs), len(chunks)),
             "seconds": round(secs, 2)}
 
 
 def run_reference(args):
-    x, loc = cpu_fields(args.side)
+    x, loc, msgs, chunks = cpu_fields(args.side)
     sample_n = min(1 << 22, x.size)
+    msgs = msgs[:4]
+    chunks = chunks[:4]
     for _ in range(args.warmup):
-        oracle_step(x, loc, sample_n)
+        oracle_step(x, loc, sample_n, msgs, chunks)
     tot_s, tot_b = 0.0, 0
     for _ in range(args.steps):
-        s, b = oracle_step(x, loc, sample_n)
+        s, b = oracle_step(x, loc, sample_n, msgs, chunks)
         tot_s += s
         tot_b += b
     v = tot_b / tot_s / 1e9
@@ -415,11 +722,13 @@ def run_reference(args):
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded 512^3 Gaussian random field)",
-            "config": {"workload": "grf512_rel1e-3_L32", "n": x.size, "rel_eb": REL,
-                       "block": BLOCK, "ring_ranks": P_RING, "scatter_segments": P_RING},
+            "config": {"workload": "grf512_rel1e-3_L32+batch1000+selector_heldout",
+                       "n": x.size, "rel_eb": REL, "block": BLOCK, "ring_ranks": P_RING,
+                       "scatter_segments": P_RING, "batch_messages": 1000},
             "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": "first %d elements per step, single-threaded plain C"
-                                       % sample_n},
+                             "sample": "per step: first %d elements of the field, %d messages, "
+                                       "%d selector chunks; single-threaded plain C and numpy"
+                                       % (sample_n, len(msgs), len(chunks))},
             "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 

@@ -85,6 +85,24 @@ def mixed_chunks(n_chunks: int, seed: int, device="cuda", scale: int = 256):
     return views[:n_chunks], ebs[:n_chunks], kinds[:n_chunks]
 
 
+def mixed_messages(total_bytes: int, seed: int, device="cuda", scale: int = 256):
+    """Whole messages of the four workload kinds, taken in turn until about
+    total_bytes are reached (a mixed workload).  Returns (xs, ebs, kinds)."""
+    xs, ebs, kinds = [], [], []
+    tot, s, kind = 0, seed * 100, 1
+    while tot < total_bytes:
+        mx, me = _kind_messages(kind, s + kind * 10000, device, scale)
+        for x, e in zip(mx, me):
+            xs.append(x)
+            ebs.append(e)
+            kinds.append(kind)
+            tot += x.numel() * x.element_size()
+        kind = kind % 4 + 1
+        if kind == 1:
+            s += 1
+    return xs, ebs, kinds
+
+
 # ---- the codec's own measurements ------------------------------------------------------
 
 def packed_capacity(views) -> int:
@@ -178,6 +196,16 @@ class ChunkBatch:
         cfg.raw_ns_per_byte = (c + d) * 1e6 / self.raw_bytes
         self.set_all(32)
         return cfg
+
+    def run_selected(self, cfg, mlp: "Mlp | None"):
+        """The selector path: statistics, (network,) selection into the
+        plan, batched compression -- all launches on the plan's stream."""
+        self.stats()
+        pred = None
+        if mlp is not None:
+            pred = mlp.forward(self.feat, out=self.pred, stream=self.stream)
+        self.select(cfg, pred)
+        self.batch.run(self.stream)
 
     def select(self, cfg, pred: torch.Tensor | None):
         zc._check(zc.zc_batch_select(self.batch.plan, self.feat.data_ptr(),
