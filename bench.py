@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--heldout-gib", type=float, default=4.0,
                     help="size of the selector's held-out mixed workload")
     ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--batch-messages", type=int, default=1000,
+                    help="messages of the batched-compression workload (1000 = the full one)")
     return ap.parse_args()
 
 
@@ -270,10 +272,9 @@ class BatchRow:
     launch (tile size and grid from the library's autotuner) in a CUDA graph,
     against the plain form (one zc_compress per message)."""
 
-    M = 1000
-
-    def __init__(self, torch, zc, workloads, stream, device):
+    def __init__(self, torch, zc, workloads, stream, device, M=1000):
         self.torch, self.zc, self.stream = torch, zc, stream
+        self.M = M
         specs = workloads.message_specs(self.M)
         with torch.cuda.stream(stream):
             self.xs = [workloads.message(sp, device=device) for sp in specs]
@@ -486,7 +487,7 @@ def run_ours(args, rank, world):
     if args.chunks:
         assert zc.zc_set_tile_chunks(args.chunks) == 0
     W = Workload(torch, zc, workloads, args.side, dev)
-    W.batch_row = BatchRow(torch, zc, workloads, W.stream, dev)
+    W.batch_row = BatchRow(torch, zc, workloads, W.stream, dev, args.batch_messages)
     W.sel_row = SelectorRow(torch, zc, W.stream, dev, args.train_chunks,
                             int(args.heldout_gib * (1 << 30)), args.epochs)
     args.warmup = max(args.warmup, 3)
@@ -512,11 +513,13 @@ def run_ours(args, rank, world):
     with ClockSampler(dev.index) as clk:
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed")  # profilers can select the timed launches
         t0.record(W.stream)
         for k in range(K):
             W.step(evs[k])
         t1.record(W.stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     total_ms = t0.elapsed_time(t1)
     if world > 1:
         import torch.distributed as dist
@@ -551,7 +554,7 @@ def run_ours(args, rank, world):
         "config": {"workload": "grf512_rel1e-3_L32+batch1000+selector_heldout",
                    "n": W.n, "rel_eb": REL,
                    "eb_abs_ring": W.eb_abs, "block": BLOCK, "ring_ranks": P_RING,
-                   "scatter_segments": P_RING, "batch_messages": BatchRow.M,
+                   "scatter_segments": P_RING, "batch_messages": W.batch_row.M,
                    "selector_heldout_bytes": W.sel_row.cb.raw_bytes,
                    "selector_chunks": W.sel_row.cb.M,
                    "l2": "inputs larger than L2 (no flush)"},
