@@ -303,3 +303,101 @@ def chunk_bounds(n: int, P: int):
     for c in range(P):
         b.append(b[-1] + base + (1 if c < rem else 0))
     return b
+
+
+def ring_allreduce(ranks, eb_abs: float, log2L: int = 5):
+    """Simulated ring Allreduce (Sec. 3.3.3): the reduce-scatter of
+    ``ring_reduce_scatter`` whose last step also re-encodes the full sum (the
+    Allgather stage's one compression), then the Allgather stage: every rank
+    decodes the P - 1 chunks it does not own; it keeps its own chunk as the
+    FP32 sum.  Returns the P result buffers and the P final chunk streams
+    (stream c encodes chunk c)."""
+    P = len(ranks)
+    n = ranks[0].size
+    bounds = chunk_bounds(n, P)
+    chunk = lambda r, c: ranks[r][bounds[c]:bounds[c + 1]]
+    sent = [reduce_step(None, chunk(r, r), eb_abs, log2L)[0] for r in range(P)]
+    own = [None] * P
+    final = [None] * P
+    for t in range(P - 1):
+        last = t == P - 2
+        new = [None] * P
+        for r in range(P):
+            c = (r - 1 - t) % P
+            s, sm = reduce_step(sent[(r - 1) % P], chunk(r, c), eb_abs, log2L, want_stream=True,
+                                want_sum=last)
+            new[r] = s
+            if last:
+                own[r] = sm
+                final[c] = s
+        sent = new
+    if P == 1:
+        own[0] = np.asarray(ranks[0], np.float32).copy()
+        final[0] = sent[0]
+    out = []
+    for r in range(P):
+        mine = (r + 1) % P if P > 1 else 0
+        buf = np.empty(n, np.float32)
+        for c in range(P):
+            m = bounds[c + 1] - bounds[c]
+            buf[bounds[c]:bounds[c + 1]] = own[r] if c == mine else decompress(final[c], m)
+        out.append(buf)
+    return out, final
+
+
+def redoub_plan(N: int):
+    """The recursive-doubling schedule of Sec. 3.3.4 for N ranks: k = floor(log2
+    N), r = N - 2^k.  Returns (k, r, active) where active[j] is the original
+    rank playing new rank j in the 2^k-rank stage: the odd ranks below 2r
+    (which absorbed their even neighbour) and the ranks from 2r on."""
+    k = N.bit_length() - 1
+    r = N - (1 << k)
+    active = [i for i in range(2 * r) if i % 2 == 1] + list(range(2 * r, N))
+    return k, r, active
+
+
+def redoub_allreduce(ranks, eb_abs: float, log2L: int = 5):
+    """Simulated recursive-doubling Allreduce (Sec. 3.3.4, gZ-Allreduce
+    ReDoub).  Stage 1: each even rank i < 2r compresses its whole buffer and
+    sends it to rank i + 1, which decodes it and adds it to its own.  Stage
+    2, among the 2^k remaining ranks, log2(2^k) steps: every rank compresses
+    its whole current buffer and sends it to its partner (new rank xor 2^s),
+    then decodes the partner's and adds it to its own (one fused ring-style
+    step: decode, add, re-encode for the next send).  Final stage: rank i + 1
+    sends its result, compressed, back to rank i < 2r (even), which decodes
+    it.  Returns the N result buffers."""
+    N = len(ranks)
+    k, r, active = redoub_plan(N)
+    cur = [np.asarray(x, np.float32).copy() for x in ranks]
+    n = cur[0].size
+    for i in range(0, 2 * r, 2):  # stage 1
+        s = compress(cur[i], eb_abs, log2L)
+        cur[i + 1] = reduce_step(s, cur[i + 1], eb_abs, log2L, want_stream=False,
+                                 want_sum=True)[1]
+    sent = {j: compress(cur[active[j]], eb_abs, log2L) for j in range(1 << k)}
+    for step in range(k):
+        last = step == k - 1
+        new = {}
+        for j in range(1 << k):
+            p = j ^ (1 << step)
+            s, sm = reduce_step(sent[p], cur[active[j]], eb_abs, log2L, want_stream=not last,
+                                want_sum=True)
+            cur[active[j]] = sm
+            new[j] = s
+        sent = new
+    for i in range(0, 2 * r, 2):  # final stage: results back to the folded even ranks
+        cur[i] = decompress(compress(cur[i + 1], eb_abs, log2L), n)
+    return cur
+
+
+def redoub_bound(N: int, rank: int, eb: float) -> float:
+    """Worst-case quantization error of rank's recursive-doubling result (FP32
+    add roundings excluded): a step adds the partner's error and one fresh
+    quantization to its own, e_s = 2 e_(s-1) + eb over k steps; ranks that
+    absorbed a neighbour start at eb; a folded rank adds one more eb."""
+    k, r, active = redoub_plan(N)
+    e0 = eb if r > 0 else 0.0
+    e = (1 << k) * e0 + ((1 << k) - 1) * eb
+    if rank < 2 * r and rank % 2 == 0:
+        e += eb
+    return e
