@@ -6,8 +6,11 @@ resident in HBM:
   range + compress   512^3 FP32 Gaussian random field (P(k) ~ k^-3, scaled to
                      [-1, 1], 512 MiB), relative bound 1e-3, L = 32
   decompress         that stream -> FP32 field
-  ring step          8 chunks of the field: decode received stream + add the
-                     local chunk + re-encode (one batched launch, fixed bound)
+  ring Allreduce     8 rank images of 8192^2 FP32 (shared base + per-rank
+                     Poisson noise), bound fixed at 1e-3 of the range: initial
+                     compression, 7 fused decode + add + re-encode steps (one
+                     batched launch each), the Allgather stage's batched
+                     decompression
   scatter pack       8 segments compressed as independent packed streams
   batched compress   1000 messages, 4 KiB - 64 MiB log-uniform, half FP32 /
                      half BF16, Student-t(3) x sigma, eb = 1e-3 sigma: one
@@ -67,6 +70,12 @@ def parse():
     ap.add_argument("--heldout-gib", type=float, default=4.0,
                     help="size of the selector's held-out mixed workload")
     ap.add_argument("--epochs", type=int, default=60)
+    ap.add_argument("--ring-ranks", type=int, default=8)
+    ap.add_argument("--ring-side", type=int, default=8192, help="rank image side (8192 = 64 Mi)")
+    ap.add_argument("--no-sweep", dest="sweep", action="store_false",
+                    help="skip the compressor's size sweep")
+    ap.add_argument("--collective-ranks", default="8,32,64",
+                    help="rank counts of the ring vs recursive-doubling report ('' = none)")
     ap.add_argument("--batch-messages", type=int, default=1000,
                     help="messages of the batched-compression workload (1000 = the full one)")
     return ap.parse_args()
@@ -170,7 +179,6 @@ class Workload:
         self.torch, self.zc = torch, zc
         self.n = n = side ** 3
         self.field = workloads.grf_3d(side=side, seed=2000, device=device)
-        self.local = workloads.grf_3d(side=side, seed=2001, device=device)
         t = torch
         self.stream = t.cuda.Stream(device=device)  # capturable (not the legacy stream)
         self.s = self.stream.cuda_stream
@@ -186,28 +194,8 @@ class Workload:
         self.stream.synchronize()
         lo, hi = mm.tolist()
         self.eb_abs = REL * (float(hi) - float(lo))
-        # ring step inputs: the field's chunks compressed (the received streams)
         self.m = n // P_RING
         self.ccap = zc.zc_max_compressed_bytes(self.m, BLOCK)
-        self.cin = t.empty(P_RING, self.ccap, dtype=t.uint8, device=device)
-        self.cin_n = t.zeros(P_RING, dtype=t.int64, device=device)
-        self.cout = t.empty(P_RING, self.ccap, dtype=t.uint8, device=device)
-        self.cout_n = t.zeros(P_RING, dtype=t.int64, device=device)
-        for r in range(P_RING):
-            ch = self.field[r * self.m:(r + 1) * self.m]
-            assert zc.zc_compress(ch.data_ptr(), self.m, 0, 0, self.eb_abs, BLOCK,
-                                  self.cin[r].data_ptr(), self.ccap, self.cin_n[r].data_ptr(),
-                                  self.ws.ptr, self.ws.nbytes, self.s) == 0
-        items = (zc.ZcReduceItem * P_RING)()
-        for r in range(P_RING):
-            loc = self.local[r * self.m:(r + 1) * self.m]
-            items[r] = zc.ZcReduceItem(self.cin[r].data_ptr(), loc.data_ptr(),
-                                       self.cout[r].data_ptr(), None,
-                                       self.cout_n[r].data_ptr(), self.m, self.ccap, self.ccap)
-        self.plan = zc.ZcPlan()
-        self.table = t.empty(zc.zc_plan_table_bytes(P_RING), dtype=t.uint8, device=device)
-        assert zc.zc_plan_reduce(self.plan, P_RING, items, self.eb_abs, BLOCK,
-                                 self.table.data_ptr(), self.table.numel()) == 0
         # scatter pack: 8 segments of the field
         self.counts = [self.m] * P_RING
         self.displs = [r * self.m for r in range(P_RING)]
@@ -217,9 +205,9 @@ class Workload:
         self.pcap = P_RING * self.ccap
         self.packed = t.empty(self.pcap, dtype=t.uint8, device=device)
         self.seg = t.zeros(P_RING + 1, dtype=t.int64, device=device)
-        # range, compress, width scan, decompress, width scan, ring step, scatter pack,
-        # batched compress, selector (statistics, MLP, selection, batched compress)
-        self.launches_per_step = 12
+        # range, compress, width scan, decompress, scatter pack, batched compress,
+        # selector (statistics, MLP, selection, batched compress); the ring adds its own
+        self.launches_per_step = 9
 
     def step(self, ev=None):
         zc, s, ws = self.zc, self.s, self.ws
@@ -235,7 +223,7 @@ class Workload:
                                 ws.ptr, ws.nbytes, s) == 0
         if ev:
             ev[2].record(st)
-        assert zc.zc_reduce_step_batch(self.plan, ws.ptr, ws.nbytes, s) == 0
+        self.ring_row.ring.run()
         if ev:
             ev[3].record(st)
         assert zc.zc_scatter_pack(self.field.data_ptr(), 0, P_RING, self.hc, self.hd, zc.EB_ABS,
@@ -252,19 +240,72 @@ class Workload:
 
     def sizes(self):
         C = int(self.cmp_n.item())
-        cin = int(self.cin_n.sum().item())
-        cout = int(self.cout_n.sum().item())
         packed = int(self.seg[-1].item())
         n4 = 4 * self.n
         parts = {
             "compress": n4 + n4 + C,          # range read + compress read + stream write
             "decompress": C + n4,
-            "ring_step": cin + n4 + cout,
+            "ring_allreduce": self.ring_row.step_bytes(),
             "scatter_pack": n4 + packed,
             "batched_compress": self.batch_row.step_bytes(),
             "selector_compress": self.sel_row.step_bytes(),
         }
         return C, parts
+
+
+class RingRow:
+    """The image-stacking ring Allreduce: P rank images of 8192^2 FP32 (a
+    shared base of 8 plane waves plus per-rank standardized Poisson(50) noise
+    at 1e-2), the bound fixed once as 1e-3 of the largest rank range; initial
+    compression, P - 1 fused steps, the Allgather stage's batched
+    decompression."""
+
+    def __init__(self, torch, zc, workloads, stream, device, P=8, side=8192):
+        from paper_2308_05199_gb300.collectives import RingAllreduce
+        self.torch, self.P = torch, P
+        with torch.cuda.stream(stream):
+            base = workloads.stacking_base(side=side, seed=3000, device=device)
+            self.ranks = [workloads.stacking_rank(base, r, seed=3000) for r in range(P)]
+            rng = max(float(x.max() - x.min()) for x in self.ranks)
+        stream.synchronize()
+        del base
+        self.eb_abs = REL * rng
+        self.ring = RingAllreduce(self.ranks, self.eb_abs, BLOCK, stream=stream)
+        self.n = self.ranks[0].numel()
+        # launches: initial compression, P - 1 steps (width scan + fused kernel),
+        # Allgather (width scan + decompression)
+        self.launches = 1 + 2 * (P - 1) + 2
+
+    def step_bytes(self):
+        """Algorithmic bytes of one Allreduce: every stream read and written,
+        every local chunk read, every FP32 result written."""
+        sz = self.ring.sizes.cpu()
+        P, n = self.P, self.n
+        tot = 4 * n * P + int(sz[0].sum())                       # initial compression
+        for t in range(P - 1):
+            tot += int(sz[t].sum()) + 4 * n + int(sz[t + 1].sum())  # steps (local chunks: n per rank / P * P)
+        tot += 4 * n                                             # last step's FP32 sums
+        fin = int(sz[P - 1].sum())
+        tot += (P - 1) * fin + 4 * n * (P - 1)                   # Allgather: P - 1 decodes per chunk
+        return tot
+
+    def errors(self):
+        """Largest |result - exact FP64 sum| over all ranks, against the ring's
+        bounds ((P - 1) eb for the owned chunk, P eb for the others; the FP32
+        additions add at most P ulp(|x| sum) / 2)."""
+        torch = self.torch
+        exact = torch.zeros(self.n, dtype=torch.float64, device=self.ranks[0].device)
+        absum = torch.zeros_like(exact)
+        for x in self.ranks:
+            exact += x.double()
+            absum += x.double().abs()
+        worst = 0.0
+        for r in range(self.P):
+            err = (self.ring.out[r].double() - exact).abs()
+            slack = self.P * 2.0 ** -24 * absum
+            worst = max(worst, float(((err - slack) / self.eb_abs).max()))
+        return {"max_err_over_eb": round(worst, 4), "bound_over_eb": self.P,
+                "eb_abs": self.eb_abs}
 
 
 class BatchRow:
@@ -477,6 +518,124 @@ class SelectorRow:
         return out
 
 
+def size_sweep(torch, zc, workloads, stream, device, max_bytes=646 << 20, reps=5):
+    """Compression / decompression time over message sizes (the paper's
+    characterization of its GPU compressor, Sec. 3.2.2, on uniform synthetic
+    data up to 646 MB): one plain call per message against the same bytes cut
+    into messages of that size and compressed in one batched launch.  Absolute
+    bound 1e-3, L = 32, FP32."""
+    out = []
+    total = max_bytes // 4
+    with torch.cuda.stream(stream):
+        x = workloads.uniform(total, seed=6000, device=device)
+    stream.synchronize()
+    ws = zc.Workspace(total, 4096, device, stream)
+    cap = zc.zc_max_compressed_bytes(total, BLOCK)
+    cmp = torch.empty(cap, dtype=torch.uint8, device=device)
+    dec = torch.empty(total, dtype=torch.float32, device=device)
+    nb = torch.zeros(1, dtype=torch.int64, device=device)
+    s = stream.cuda_stream
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(f):
+        f()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        for _ in range(reps):
+            f()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    size = 4096
+    while size <= max_bytes:
+        n = size // 4
+        c = lambda: zc._check(zc.zc_compress(x.data_ptr(), n, zc.F32, zc.EB_ABS, 1e-3, BLOCK,
+                                             cmp.data_ptr(), cap, nb.data_ptr(), ws.ptr,
+                                             ws.nbytes, s), "zc_compress")
+        d = lambda: zc._check(zc.zc_decompress(cmp.data_ptr(), cap, dec.data_ptr(), n, zc.F32,
+                                               ws.ptr, ws.nbytes, s), "zc_decompress")
+        tc = timed(c)
+        td = timed(d)
+        M = min(total // n, 4096)
+        views = [x[i * n:(i + 1) * n] for i in range(M)]
+        b = zc.BatchCompress(views, [BLOCK] * M, [1e-3] * M, ws=ws, stream=stream)
+        bd = zc.BatchDecompress(b.packed, b.msg_off, [dec[i * n:(i + 1) * n] for i in range(M)],
+                                ws=ws, stream=stream)
+        tb = timed(lambda: b.run(stream))
+        tbd = timed(lambda: bd.run(stream))
+        out.append({"bytes": size, "plain_compress_us": round(tc * 1e3, 2),
+                    "plain_decompress_us": round(td * 1e3, 2),
+                    "plain_compress_gbs": round(size / tc / 1e6, 1),
+                    "plain_decompress_gbs": round(size / td / 1e6, 1),
+                    "batched_messages": M,
+                    "batched_compress_us_per_message": round(tb * 1e3 / M, 3),
+                    "batched_decompress_us_per_message": round(tbd * 1e3 / M, 3),
+                    "batched_compress_gbs": round(size * M / tb / 1e6, 1),
+                    "batched_decompress_gbs": round(size * M / tbd / 1e6, 1)})
+        del b, bd, views
+        size = size * 4 if size * 4 <= max_bytes or size == max_bytes else max_bytes
+    st, _ = ws.status(stream)
+    del x, cmp, dec
+    torch.cuda.empty_cache()
+    return {"status": st, "points": out}
+
+
+def collectives_report(torch, workloads, stream, device, ranks_list, side, reps=2):
+    """Ring vs recursive-doubling Allreduce on the image-stacking workload for
+    each rank count: measured device time, the modelled per-rank time with one
+    GPU per rank at 12.5 and 100 GB/s links, the largest error against the
+    exact FP64 sum in units of eb (with the FP32-addition slack removed), and
+    the algorithm the model picks (the paper's ring / recursive-doubling
+    choice, Sec. 3.3.3)."""
+    from paper_2308_05199_gb300 import collectives as C
+    out = []
+    for P in ranks_list:
+        with torch.cuda.stream(stream):
+            base = workloads.stacking_base(side=side, seed=3000, device=device)
+            ranks = [workloads.stacking_rank(base, r, seed=3000) for r in range(P)]
+            del base
+            eb = REL * max(float(x.max() - x.min()) for x in ranks)
+            exact = torch.zeros(ranks[0].numel(), dtype=torch.float64, device=device)
+            absum = torch.zeros_like(exact)
+            for x in ranks:
+                exact += x.double()
+                absum += x.double().abs()
+        stream.synchronize()
+        rec = {"ranks": P, "n_per_rank": ranks[0].numel(), "eb_abs": eb}
+        k = P.bit_length() - 1
+        for name, cls in (("ring", C.RingAllreduce), ("recursive_doubling",
+                                                     C.RecursiveDoublingAllreduce)):
+            alg = cls(ranks, eb, BLOCK, stream=stream)
+            alg.run()
+            stream.synchronize()
+            worst = 0.0
+            for r in range(P):
+                err = (alg.out[r].double() - exact).abs() - P * 2.0 ** -24 * absum
+                worst = max(worst, float((err / eb).max()))
+            st, _ = alg.ws.status(stream)
+            m12 = alg.model(12.5, reps)
+            m100 = alg.model(100.0, reps)
+            # worst-case bounds: ring (P - 1) eb owned, P eb decoded; recursive
+            # doubling e = (2^k - 1) eb (+ 2^k eb with remainder ranks, + eb folded)
+            bound = P if name == "ring" else ((1 << k) - 1 + ((1 << k) + 1 if P > (1 << k) else 0))
+            rec[name] = {"status": st, "max_err_over_eb": round(worst, 3), "bound_over_eb": bound,
+                         "device_ms": m12["device_ms"], "launches": m12["launches"],
+                         "per_rank_ms_link12.5": m12["per_rank_ms"],
+                         "per_rank_ms_link100": m100["per_rank_ms"],
+                         "bytes_sent_per_rank": m12["bytes_sent_per_rank"]}
+            del alg
+            torch.cuda.empty_cache()
+        for link in ("12.5", "100"):
+            key = "per_rank_ms_link" + link
+            rec["choice_link" + link] = min(("ring", "recursive_doubling"),
+                                            key=lambda a: rec[a][key])
+        out.append(rec)
+        del ranks, exact, absum
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2308_05199_gb300 import build, workloads, zc
@@ -488,6 +647,9 @@ def run_ours(args, rank, world):
         assert zc.zc_set_tile_chunks(args.chunks) == 0
     W = Workload(torch, zc, workloads, args.side, dev)
     W.batch_row = BatchRow(torch, zc, workloads, W.stream, dev, args.batch_messages)
+    W.ring_row = RingRow(torch, zc, workloads, W.stream, dev, P=args.ring_ranks,
+                         side=args.ring_side)
+    W.launches_per_step += W.ring_row.launches
     W.sel_row = SelectorRow(torch, zc, W.stream, dev, args.train_chunks,
                             int(args.heldout_gib * (1 << 30)), args.epochs)
     args.warmup = max(args.warmup, 3)
@@ -496,6 +658,10 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     batched = W.batch_row.compare()
     selector = W.sel_row.report()
+    sweep = size_sweep(torch, zc, workloads, W.stream, dev) if args.sweep else None
+    coll = collectives_report(torch, workloads, W.stream, dev,
+                              [int(v) for v in args.collective_ranks.split(",") if v],
+                              args.ring_side) if args.collective_ranks else None
     torch.cuda.synchronize()
     st, det = W.ws.status()
     if st != 0:
@@ -529,7 +695,7 @@ def run_ours(args, rank, world):
     st, det = W.ws.status()
     if st != 0:
         raise RuntimeError("device status %d at %d in the timed region" % (st, det))
-    names = ["compress", "decompress", "ring_step", "scatter_pack", "batched_compress",
+    names = ["compress", "decompress", "ring_allreduce", "scatter_pack", "batched_compress",
              "selector_compress"]
     per = {nm: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K))
            for i, nm in enumerate(names)}
@@ -551,9 +717,11 @@ def run_ours(args, rank, world):
         "data": "synthetic, seeded: 512^3 Gaussian random field (P(k)~k^-3) in place of the "
                 "paper's RTM volumes; Student-t messages; mixed held-out workload of the four "
                 "kinds",
-        "config": {"workload": "grf512_rel1e-3_L32+batch1000+selector_heldout",
+        "config": {"workload": "grf512_rel1e-3_L32+stacking_ring8x8192sq+batch1000"
+                               "+selector_heldout",
                    "n": W.n, "rel_eb": REL,
-                   "eb_abs_ring": W.eb_abs, "block": BLOCK, "ring_ranks": P_RING,
+                   "eb_abs_ring": W.ring_row.eb_abs, "block": BLOCK,
+                   "ring_ranks": W.ring_row.P, "ring_n_per_rank": W.ring_row.n,
                    "scatter_segments": P_RING, "batch_messages": W.batch_row.M,
                    "selector_heldout_bytes": W.sel_row.cb.raw_bytes,
                    "selector_chunks": W.sel_row.cb.M,
@@ -567,6 +735,9 @@ def run_ours(args, rank, world):
         "clocks": clk.summary(),
         "batched": batched,
         "selector": selector,
+        "ring": dict(W.ring_row.errors(), ranks=W.ring_row.P, n_per_rank=W.ring_row.n),
+        "collectives": coll,
+        "size_sweep": sweep,
     }
     if not args.no_e2e:
         out["e2e"] = e2e_ours(torch, W, args, step_bytes, world)
@@ -579,7 +750,7 @@ def e2e_ours(torch, W, args, step_bytes, world):
     output (the field's stream, both packed batches) copied back, inside the
     timed region, all on the step's stream."""
     st = W.stream
-    dev_in = [W.field, W.local] + W.batch_row.xs + W.sel_row.xs
+    dev_in = [W.field] + W.ring_row.ranks + W.batch_row.xs + W.sel_row.xs
     host_in = [t.cpu().pin_memory() for t in dev_in]
     outs = [(W.cmp, W.cmp_n[0:1]), (W.batch_row.b.packed, W.batch_row.b.msg_off[-1:]),
             (W.sel_row.cb.batch.packed, W.sel_row.cb.batch.msg_off[-1:])]
@@ -621,29 +792,26 @@ def e2e_ours(torch, W, args, step_bytes, world):
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and --impl reference)
 
-def oracle_step(x, loc, sample_n, msgs, chunks):
+def oracle_step(x, ring_ranks, sample_n, msgs, chunks):
     """The bench step on bounded samples, run by the CPU oracle; returns
     (seconds, algorithmic bytes).  Samples: the first sample_n elements of
     the field (range, compress, decompress, ring step over 8 chunks, scatter
     pack of 8 segments), the first messages of the 1000-message workload
     (one compression each), and 64 KiB chunks through the selector
-    (statistics, network, choice, compression).  The ring step's received
-    streams are prepared outside the timed part (they are that step's
-    input)."""
+    (statistics, network, choice, compression); the ring Allreduce on
+    smaller rank images of the same recipe."""
     import numpy as np
     import oracle
     from oracle import selector as OS
-    xs, ls = x[:sample_n], loc[:sample_n]
+    xs = x[:sample_n]
     m = sample_n // P_RING
     t0 = time.perf_counter()
     mn, mx = oracle.minmax(xs)
     eb = oracle.eb_from_rel(REL, mn, mx)
     s = oracle.compress(xs, eb, 5)
     oracle.decompress(s, sample_n)
-    t1 = time.perf_counter()
-    cin = [oracle.compress(xs[r * m:(r + 1) * m], eb, 5) for r in range(P_RING)]
-    t2 = time.perf_counter()
-    cout = [oracle.reduce_step(cin[r], ls[r * m:(r + 1) * m], eb, 5)[0] for r in range(P_RING)]
+    ring_eb = REL * max(float(r.max() - r.min()) for r in ring_ranks)
+    ring_out, ring_final = oracle.ring_allreduce(ring_ranks, ring_eb, 5)
     packed, _ = oracle.scatter_pack(xs, [m] * P_RING, [r * m for r in range(P_RING)], eb, 5)
     batch_out = sum(len(oracle.compress(a, e, 5)) for a, e in msgs)
     feats = np.array([OS.chunk_stats(a, e) for a, e in chunks])
@@ -656,25 +824,28 @@ def oracle_step(x, loc, sample_n, msgs, chunks):
         c, _ = OS.mlp_choice(a.size, a.itemsize, f, y, cfg)
         sel_out += len(oracle.compress_raw(a) if c == 0 else oracle.compress(a, e, c.bit_length() - 1))
     t3 = time.perf_counter()
-    secs = (t1 - t0) + (t3 - t2)
+    secs = t3 - t0
     n4 = 4 * sample_n
+    P, nr = len(ring_ranks), ring_ranks[0].size
+    ring_bytes = 4 * nr * P * 2 + (2 * P - 1) * sum(map(len, ring_final)) + 4 * nr * P
     raw_msgs = sum(a.nbytes for a, _ in msgs)
     raw_chunks = sum(a.nbytes for a, _ in chunks)
     nbytes = (n4 + n4 + len(s)) + (len(s) + n4) + \
-        (sum(map(len, cin)) + n4 + sum(map(len, cout))) + (n4 + len(packed)) + \
+        ring_bytes + (n4 + len(packed)) + \
         (raw_msgs + batch_out) + (raw_chunks + sel_out)
     return secs, nbytes
 
 
 def cpu_fields(side):
-    """The field, the local field, a sample of the 1000-message workload (the
+    """The field, 8 rank images of 512^2 (the ring's recipe), a sample of the 1000-message workload (the
     first messages that fit in 16 MiB together, at most 64) and 16 chunks of 64 KiB (8 of the field, 8 of
     the messages), as numpy arrays (BF16 as uint16 bits)."""
     import torch
     from paper_2308_05199_gb300 import workloads
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     x = workloads.grf_3d(side=side, seed=2000, device=dev).cpu().numpy()
-    loc = workloads.grf_3d(side=side, seed=2001, device=dev).cpu().numpy()
+    base = workloads.stacking_base(side=512, seed=3000, device=dev)
+    ring = [workloads.stacking_rank(base, r, seed=3000).cpu().numpy() for r in range(P_RING)]
     msgs, tot = [], 0
     for sp in workloads.message_specs(1000):
         t = workloads.message(sp, device=dev)
@@ -692,31 +863,33 @@ def cpu_fields(side):
             break
         per = 65536 // a.itemsize
         chunks.append((a[:per], e))
-    return x, loc, msgs, chunks
+    return x, ring, msgs, chunks
 
 
 def cpu_baseline(side, sample_n=1 << 25):
-    x, loc, msgs, chunks = cpu_fields(side)
+    x, ring, msgs, chunks = cpu_fields(side)
     sample_n = min(sample_n, x.size)
-    secs, nbytes = oracle_step(x, loc, sample_n, msgs, chunks)
+    secs, nbytes = oracle_step(x, ring, sample_n, msgs, chunks)
     return {"value": round(nbytes / secs / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": "first %d elements of the same field (range, compress, decompress, "
-                      "ring step over 8 chunks, scatter pack of 8 segments), the first %d of the "
+                      "scatter pack of 8 segments), the ring Allreduce of 8 rank images of "
+                      "512^2, the first %d of the "
                       "1000 messages, %d chunks of 64 KiB through the selector; single-threaded "
                       "plain C and numpy" % (sample_n, len(msgs), len(chunks)),
             "seconds": round(secs, 2)}
 
 
 def run_reference(args):
-    x, loc, msgs, chunks = cpu_fields(args.side)
+    x, ring, msgs, chunks = cpu_fields(args.side)
     sample_n = min(1 << 22, x.size)
+    ring = [r[:1 << 15] for r in ring]
     msgs = msgs[:4]
     chunks = chunks[:4]
     for _ in range(args.warmup):
-        oracle_step(x, loc, sample_n, msgs, chunks)
+        oracle_step(x, ring, sample_n, msgs, chunks)
     tot_s, tot_b = 0.0, 0
     for _ in range(args.steps):
-        s, b = oracle_step(x, loc, sample_n, msgs, chunks)
+        s, b = oracle_step(x, ring, sample_n, msgs, chunks)
         tot_s += s
         tot_b += b
     v = tot_b / tot_s / 1e9
@@ -725,7 +898,8 @@ def run_reference(args):
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded 512^3 Gaussian random field)",
-            "config": {"workload": "grf512_rel1e-3_L32+batch1000+selector_heldout",
+            "config": {"workload": "grf512_rel1e-3_L32+stacking_ring8x8192sq+batch1000"
+                                   "+selector_heldout",
                        "n": x.size, "rel_eb": REL, "block": BLOCK, "ring_ranks": P_RING,
                        "scatter_segments": P_RING, "batch_messages": 1000},
             "cpu_baseline": {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",

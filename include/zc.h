@@ -268,6 +268,16 @@ int zc_plan_decompress_batch(zc_batch* plan, int n_msgs, const zc_message* h_msg
                              const void* d_packed, size_t packed_cap, const uint64_t* d_msg_off,
                              void* d_table, size_t table_bytes);
 
+/* Plan the decompression of M streams at any device addresses (the
+ * Allgather stage of a ring Allreduce, Sec. 3.3.3: every rank decodes the
+ * chunks it does not own, one decompression per received chunk): stream i at
+ * h_streams[i] (16-byte aligned, h_caps[i] readable bytes) decodes into
+ * h_msgs[i].out as h_msgs[i].n elements of h_msgs[i].dtype (other fields
+ * unused).  Launch with zc_decompress_batch. */
+int zc_plan_decompress_streams(zc_batch* plan, int n_msgs, const void* const* h_streams,
+                               const uint64_t* h_caps, const zc_message* h_msgs, void* d_table,
+                               size_t table_bytes);
+
 /* Launch a decompression plan on s (a width-scan and a decode kernel). */
 int zc_decompress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_stream_t s);
 
@@ -335,7 +345,7 @@ int zc_autotune_batch(int n_msgs, const zc_message* h_msgs, int tune_block, doub
  *   14    raw bits per element / 32;    15 log2(n) / 16;
  * d = q_i - q_{i-1} within a span.  A message with no elements, no bound, or
  * a sampled value the codec cannot quantize gets a row of NaN.  One kernel,
- * one warp per message. */
+ * one CTA per message (a warp per two spans). */
 int zc_batch_chunk_stats(const zc_batch* plan, float* d_feat, zc_stream_t s);
 
 /* MLP forward: y[b] = W3 relu(W2 relu(W1 x'[b] + b1) + b2) + b3 with

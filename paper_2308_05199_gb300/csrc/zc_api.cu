@@ -648,6 +648,50 @@ int zc_plan_decompress_batch(zc_batch* plan, int n_msgs, const zc_message* h_msg
     return ZC_OK;
 }
 
+int zc_plan_decompress_streams(zc_batch* plan, int n_msgs, const void* const* h_streams,
+                               const uint64_t* h_caps, const zc_message* h_msgs, void* d_table,
+                               size_t table_bytes)
+{
+    if (plan == nullptr || n_msgs < 1 || h_streams == nullptr || h_caps == nullptr ||
+        h_msgs == nullptr || d_table == nullptr || !aligned(d_table, 16) ||
+        table_bytes < zc_batch_table_bytes(n_msgs))
+        return ZC_ERR_ARG;
+    std::vector<Item> items((size_t)n_msgs);
+    uint64_t tile = 0, chunk = 0;
+    for (int i = 0; i < n_msgs; ++i) {
+        const zc_message& m = h_msgs[i];
+        if (!dtype_ok(m.dtype) || (m.n > 0 && m.out == nullptr) ||
+            !aligned(m.out, elem_bytes(m.dtype)) || h_streams[i] == nullptr ||
+            !aligned(h_streams[i], 16) || h_caps[i] < 32)
+            return ZC_ERR_ARG;
+        Item& it = items[(size_t)i];
+        std::memset(&it, 0, sizeof(it));
+        it.cin = (const uint8_t*)h_streams[i];
+        it.cin_cap = h_caps[i];
+        it.raw_out = m.out;
+        it.n = m.n;
+        it.tile_begin = (unsigned)tile;
+        it.ntiles = (unsigned)tiles_for(m.n, DEC_U);
+        it.chunk_begin = (unsigned)chunk;
+        it.nchunks = (unsigned)chunks_for(it.ntiles);
+        it.x_dtype = m.dtype;
+        it.out_dtype = m.dtype;
+        tile += it.ntiles;
+        chunk += it.nchunks;
+        if (tile > 0x7fffffffull) return ZC_ERR_ARG;
+    }
+    if (cudaMemcpy(d_table, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return ZC_ERR_CUDA;
+    std::memset(plan, 0, sizeof(*plan));
+    plan->n_msgs = n_msgs;
+    plan->decompress = 1;
+    plan->total_tiles = tile;
+    plan->total_chunks = chunk;
+    plan->d_table = d_table;
+    return ZC_OK;
+}
+
 int zc_decompress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_stream_t s)
 {
     if (plan == nullptr || plan->d_table == nullptr || plan->n_msgs < 1 || plan->decompress != 1)

@@ -40,33 +40,41 @@ __device__ __forceinline__ float load_elem(const Item& it, unsigned long long i)
                                 : bf16_to_f32(__ldg((const unsigned short*)it.x + i));
 }
 
-// ---- chunk statistics: one warp per item ------------------------------------------
+// ---- chunk statistics: one CTA per item, one warp per two sampled spans ----------
+// Per-warp partial sums of the span statistics, combined by thread 0.
+struct SpanPart {
+    unsigned long long bits[4];  // codec block bits at L = 16, 32, 64, 128
+    unsigned long long sad, saq, sad2;
+    unsigned mad, nzd, nzq, nsc, hb;
+    int qmin, qmax, bad;
+};
+
 __global__ void __launch_bounds__(256) k_chunk_stats(const Item* items, unsigned n_items,
                                                      float* feat)
 {
-    __shared__ double span_v[8][ST_SPANS];
+    __shared__ SpanPart part[8];
+    __shared__ unsigned span_b32[ST_SPANS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned idx = blockIdx.x * 8 + warp;
-    if (idx >= n_items) return;  // warp-uniform; only warp-level sync below
+    const unsigned idx = blockIdx.x;
+    if (idx >= n_items) return;  // CTA-uniform
     const Item it = items[idx];
     float* out = feat + (size_t)idx * N_STATS;
     const unsigned long long n = it.n;
     if (n == 0 || it.x == nullptr || !(it.two_eb > 0.0f)) {
-        if (lane < N_STATS) out[lane] = __int_as_float(0x7fc00000);  // NaN row
+        if (threadIdx.x < N_STATS) out[threadIdx.x] = __int_as_float(0x7fc00000);  // NaN row
         return;
     }
     const unsigned long long m = n / ST_SPAN;
     const int S = m == 0 ? 1 : (int)(m < ST_SPANS ? m : ST_SPANS);
+    const int cnt = m == 0 ? (int)n : ST_SPAN;  // elements of every sampled span
     unsigned b16 = 0, b32 = 0, b64 = 0, b128 = 0;  // lane-partial block bits
     unsigned long long sum_ad = 0, sum_aq = 0, sum_ad2 = 0;
     unsigned max_ad = 0, nz_d = 0, nz_q = 0, n_sc = 0, head_bits = 0;
     int qmin = 0x7fffffff, qmax = -0x7fffffff - 1;
     int bad = 0;
-    unsigned long long tot = 0, nd = 0, nd2 = 0, nheads = 0;
-    for (int j = 0; j < S; ++j) {
+    for (int j = warp; j < S; j += 8) {
         const unsigned long long s0 =
             (m == 0 || S == 1) ? 0ull : (unsigned long long)ST_SPAN * (((unsigned long long)j * (m - 1)) / (S - 1));
-        const int cnt = m == 0 ? (int)n : ST_SPAN;
         int q[4], d[4], pd[4];
         bool v[4];
 #pragma unroll
@@ -119,7 +127,7 @@ __global__ void __launch_bounds__(256) k_chunk_stats(const Item* items, unsigned
             }
         }
         // the codec's block bits at every L: the block head's delta is |q|
-        unsigned span_b32 = 0;
+        unsigned sb32 = 0;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             unsigned a = (lane & 15) == 0 ? aq[r] : ad[r];
@@ -127,7 +135,7 @@ __global__ void __launch_bounds__(256) k_chunk_stats(const Item* items, unsigned
             for (int off = 8; off; off >>= 1) a = max(a, __shfl_xor_sync(FULL, a, off));
             if ((lane & 15) == 0 && a) b16 += (bitlen_u(a) + 1) * 16;
             const unsigned m32 = __reduce_max_sync(FULL, lane == 0 ? aq[r] : ad[r]);
-            if (m32) span_b32 += (bitlen_u(m32) + 1) * 32;
+            if (m32) sb32 += (bitlen_u(m32) + 1) * 32;
             if (lane == 0 && v[r]) head_bits += bitlen_u(aq[r]);
         }
 #pragma unroll
@@ -141,56 +149,99 @@ __global__ void __launch_bounds__(256) k_chunk_stats(const Item* items, unsigned
             if (lane == 0 && m128) b128 += (bitlen_u(m128) + 1) * 128;
         }
         if (lane == 0) {
-            b32 += span_b32;
-            span_v[warp][j] = (double)span_b32 / (double)cnt;
+            b32 += sb32;
+            span_b32[j] = sb32;
         }
-        tot += cnt;
-        nd += cnt - 1;
-        nd2 += cnt >= 2 ? cnt - 2 : 0;
-        nheads += (cnt + 31) / 32;
     }
-    if (__any_sync(FULL, bad)) {
-        if (lane < N_STATS) out[lane] = __int_as_float(0x7fc00000);
+    {
+        const unsigned long long B16 = warp_sum_u64(b16), B32 = warp_sum_u64(b32);
+        const unsigned long long B64 = warp_sum_u64(b64), B128 = warp_sum_u64(b128);
+        const unsigned long long SAD = warp_sum_u64(sum_ad), SAQ = warp_sum_u64(sum_aq);
+        const unsigned long long SAD2 = warp_sum_u64(sum_ad2);
+        const unsigned long long NZD = warp_sum_u64(nz_d), NZQ = warp_sum_u64(nz_q);
+        const unsigned long long NSC = warp_sum_u64(n_sc), HB = warp_sum_u64(head_bits);
+        const unsigned MAD = __reduce_max_sync(FULL, max_ad);
+        const int QMN = __reduce_min_sync(FULL, qmin), QMX = __reduce_max_sync(FULL, qmax);
+        const int BAD = __any_sync(FULL, bad);
+        if (lane == 0) {
+            SpanPart& P = part[warp];
+            P.bits[0] = B16;
+            P.bits[1] = B32;
+            P.bits[2] = B64;
+            P.bits[3] = B128;
+            P.sad = SAD;
+            P.saq = SAQ;
+            P.sad2 = SAD2;
+            P.mad = MAD;
+            P.nzd = (unsigned)NZD;
+            P.nzq = (unsigned)NZQ;
+            P.nsc = (unsigned)NSC;
+            P.hb = (unsigned)HB;
+            P.qmin = QMN;
+            P.qmax = QMX;
+            P.bad = BAD;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    unsigned long long bits[4] = {0, 0, 0, 0}, SAD = 0, SAQ = 0, SAD2 = 0, NZD = 0, NZQ = 0,
+                       NSC = 0, HB = 0;
+    unsigned MAD = 0;
+    int QMN = 0x7fffffff, QMX = -0x7fffffff - 1, BAD = 0;
+    for (int w = 0; w < 8; ++w) {
+        const SpanPart& P = part[w];
+        for (int k = 0; k < 4; ++k) bits[k] += P.bits[k];
+        SAD += P.sad;
+        SAQ += P.saq;
+        SAD2 += P.sad2;
+        NZD += P.nzd;
+        NZQ += P.nzq;
+        NSC += P.nsc;
+        HB += P.hb;
+        MAD = max(MAD, P.mad);
+        QMN = min(QMN, P.qmin);
+        QMX = max(QMX, P.qmax);
+        BAD |= P.bad;
+    }
+    if (BAD) {
+        for (int k = 0; k < N_STATS; ++k) out[k] = __int_as_float(0x7fc00000);
         return;
     }
-    const unsigned long long B16 = warp_sum_u64(b16), B32 = warp_sum_u64(b32);
-    const unsigned long long B64 = warp_sum_u64(b64), B128 = warp_sum_u64(b128);
-    const unsigned long long SAD = warp_sum_u64(sum_ad), SAQ = warp_sum_u64(sum_aq);
-    const unsigned long long SAD2 = warp_sum_u64(sum_ad2);
-    const unsigned long long NZD = warp_sum_u64(nz_d), NZQ = warp_sum_u64(nz_q);
-    const unsigned long long NSC = warp_sum_u64(n_sc), HB = warp_sum_u64(head_bits);
-    const unsigned MAD = __reduce_max_sync(FULL, max_ad);
-    const int QMN = __reduce_min_sync(FULL, qmin), QMX = __reduce_max_sync(FULL, qmax);
-    __syncwarp();
-    if (lane != 0) return;
-    const double dt = (double)tot, dn = (double)n;
-    double f[N_STATS];
-    f[0] = (double)B16 / dt + 8.0 / 16 + 256.0 / dn;
-    f[1] = (double)B32 / dt + 8.0 / 32 + 256.0 / dn;
-    f[2] = (double)B64 / dt + 8.0 / 64 + 256.0 / dn;
-    f[3] = (double)B128 / dt + 8.0 / 128 + 256.0 / dn;
-    f[4] = log2(1.0 + (double)((long long)QMX - (long long)QMN));
-    f[5] = nd ? log2(1.0 + (double)SAD / (double)nd) : 0.0;
-    f[6] = nd ? log2(1.0 + (double)MAD) : 0.0;
-    f[7] = nd ? (double)NZD / (double)nd : 0.0;
-    f[8] = (double)NZQ / dt;
-    f[9] = log2(1.0 + (double)SAQ / dt);
-    f[10] = nd2 ? log2(1.0 + (double)SAD2 / (double)nd2) : 0.0;
-    f[11] = nd2 ? (double)NSC / (double)nd2 : 0.0;
-    f[12] = (double)HB / (double)nheads / 24.0;
-    double mean = 0.0;
-    for (int j = 0; j < S; ++j) mean += span_v[warp][j];
-    mean /= S;
-    double var = 0.0;
+    // The features in FP32 (this GPU's FP64 rate is a small fraction of its
+    // FP32 rate): counts are exact integers below 2^24, each quotient is one
+    // correctly rounded division, each logarithm CUDA's log2f.
+    const float tot = (float)(S * cnt), fn = (float)n;
+    const float nd = (float)(S * (cnt - 1));
+    const float nd2 = cnt >= 2 ? (float)(S * (cnt - 2)) : 0.0f;
+    const float nheads = (float)(S * ((cnt + 31) / 32));
+    const float hdr = __fdiv_rn(256.0f, fn);
+    float f[N_STATS];
+    f[0] = __fadd_rn(__fadd_rn(__fdiv_rn((float)bits[0], tot), 0.5f), hdr);
+    f[1] = __fadd_rn(__fadd_rn(__fdiv_rn((float)bits[1], tot), 0.25f), hdr);
+    f[2] = __fadd_rn(__fadd_rn(__fdiv_rn((float)bits[2], tot), 0.125f), hdr);
+    f[3] = __fadd_rn(__fadd_rn(__fdiv_rn((float)bits[3], tot), 0.0625f), hdr);
+    f[4] = log2f(1.0f + (float)((long long)QMX - (long long)QMN));
+    f[5] = nd > 0.0f ? log2f(1.0f + __fdiv_rn((float)SAD, nd)) : 0.0f;
+    f[6] = nd > 0.0f ? log2f(1.0f + (float)MAD) : 0.0f;
+    f[7] = nd > 0.0f ? __fdiv_rn((float)NZD, nd) : 0.0f;
+    f[8] = __fdiv_rn((float)NZQ, tot);
+    f[9] = log2f(1.0f + __fdiv_rn((float)SAQ, tot));
+    f[10] = nd2 > 0.0f ? log2f(1.0f + __fdiv_rn((float)SAD2, nd2)) : 0.0f;
+    f[11] = nd2 > 0.0f ? __fdiv_rn((float)NSC, nd2) : 0.0f;
+    f[12] = __fdiv_rn(__fdiv_rn((float)HB, nheads), 24.0f);
+    float mean = 0.0f;
+    for (int j = 0; j < S; ++j) mean = __fadd_rn(mean, __fdiv_rn((float)span_b32[j], (float)cnt));
+    mean = __fdiv_rn(mean, (float)S);
+    float var = 0.0f;
     for (int j = 0; j < S; ++j) {
-        const double e = span_v[warp][j] - mean;
-        var += e * e;
+        const float e = __fsub_rn(__fdiv_rn((float)span_b32[j], (float)cnt), mean);
+        var = __fadd_rn(var, __fmul_rn(e, e));
     }
-    f[13] = sqrt(var / S);
-    f[14] = it.x_dtype == ZC_F32 ? 1.0 : 0.5;
-    f[15] = log2(dn) / 16.0;
+    f[13] = sqrtf(__fdiv_rn(var, (float)S));
+    f[14] = it.x_dtype == ZC_F32 ? 1.0f : 0.5f;
+    f[15] = __fdiv_rn(log2f(fn), 16.0f);
 #pragma unroll
-    for (int k = 0; k < N_STATS; ++k) out[k] = (float)f[k];
+    for (int k = 0; k < N_STATS; ++k) out[k] = f[k];
 }
 
 // ---- MLP ------------------------------------------------------------------------------
@@ -488,7 +539,7 @@ int zc_batch_chunk_stats(const zc_batch* plan, float* d_feat, zc_stream_t s)
         d_feat == nullptr || (reinterpret_cast<uintptr_t>(d_feat) & 3) != 0)
         return ZC_ERR_ARG;
     const unsigned n = (unsigned)plan->n_msgs;
-    k_chunk_stats<<<(n + 7) / 8, 256, 0, (cudaStream_t)s>>>((const Item*)plan->d_table, n, d_feat);
+    k_chunk_stats<<<n, 256, 0, (cudaStream_t)s>>>((const Item*)plan->d_table, n, d_feat);
     return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
 }
 

@@ -120,6 +120,12 @@ def message_specs(m: int = 1000, lo_bytes: int = 4096, hi_bytes: int = 64 << 20,
     return specs
 
 
+def uniform(n: int, seed: int, device="cpu") -> torch.Tensor:
+    """U[0, 1) FP32: the uniformly distributed synthetic data of the paper's
+    compressor characterization over message sizes (Sec. 3.2.2)."""
+    return torch.rand(n, generator=_tgen(device, seed), dtype=torch.float32, device=device)
+
+
 def student_t3(n: int, sigma: float, seed: int, device="cpu",
                dtype=torch.float32) -> torch.Tensor:
     """sigma * T with T ~ Student-t(3) = Z / sqrt(chi2_3 / 3)."""

@@ -127,6 +127,8 @@ def _declare(L):
         "zc_plan_decompress_batch": (i32, [c.POINTER(ZcBatch), i32, c.POINTER(ZcMessage), vp, sz,
                                            vp, vp, sz]),
         "zc_decompress_batch": (i32, [c.POINTER(ZcBatch), vp, sz, vp]),
+        "zc_plan_decompress_streams": (i32, [c.POINTER(ZcBatch), i32, vp, vp,
+                                             c.POINTER(ZcMessage), vp, sz]),
         "zc_autotune_batch": (i32, [i32, c.POINTER(ZcMessage), i32, dbl, i32, vp, sz, vp, vp, sz,
                                     vp, sz, vp, c.POINTER(ZcTunePoint), i32, c.POINTER(i32),
                                     c.POINTER(ZcTunePoint)]),
@@ -160,7 +162,7 @@ def exported_names():
             "zc_plan_table_bytes", "zc_plan_reduce", "zc_reduce_step_batch", "zc_scatter_pack",
             "zc_compress_noalloc", "zc_batch_table_bytes", "zc_batch_max_bytes",
             "zc_plan_compress_batch", "zc_compress_batch", "zc_plan_decompress_batch",
-            "zc_decompress_batch", "zc_autotune_batch", "zc_batch_chunk_stats", "zc_mlp_forward",
+            "zc_decompress_batch", "zc_plan_decompress_streams", "zc_autotune_batch", "zc_batch_chunk_stats", "zc_mlp_forward",
             "zc_mlp_scratch_bytes", "zc_mlp_grad", "zc_mlp_sgd", "zc_batch_select",
             "zc_graph_begin", "zc_graph_end",
             "zc_graph_launch", "zc_graph_destroy",
@@ -278,6 +280,12 @@ def zc_plan_decompress_batch(plan, n_msgs, h_msgs, d_packed, packed_cap, d_msg_o
                              table_bytes) -> int:
     return lib().zc_plan_decompress_batch(ctypes.byref(plan), n_msgs, h_msgs, d_packed,
                                           packed_cap, d_msg_off, d_table, table_bytes)
+
+
+def zc_plan_decompress_streams(plan, n_msgs, h_streams, h_caps, h_msgs, d_table,
+                               table_bytes) -> int:
+    return lib().zc_plan_decompress_streams(ctypes.byref(plan), n_msgs, h_streams, h_caps,
+                                            h_msgs, d_table, table_bytes)
 
 
 def zc_decompress_batch(plan, d_ws, ws_bytes, stream) -> int:

@@ -70,7 +70,9 @@ def test_chunk_stats_match_oracle(zc):
         ref = OS.chunk_stats(np_of(x), eb)
         assert np.array_equal(np.isnan(got[i]), np.isnan(ref)), i
         ok = ~np.isnan(ref)
-        np.testing.assert_allclose(got[i][ok], ref[ok], rtol=2e-7, atol=1e-7, err_msg=str(i))
+        # FP32 on the GPU: a few roundings (divisions, sums, log2f) on values the
+        # oracle computes in FP64 from the same exact integer counts
+        np.testing.assert_allclose(got[i][ok], ref[ok], rtol=1e-6, atol=2e-6, err_msg=str(i))
 
 
 def _mlp_problem(B, seed):
