@@ -205,9 +205,10 @@ class Workload:
         self.pcap = P_RING * self.ccap
         self.packed = t.empty(self.pcap, dtype=t.uint8, device=device)
         self.seg = t.zeros(P_RING + 1, dtype=t.int64, device=device)
-        # range, compress, width scan, decompress, scatter pack, batched compress,
-        # selector (statistics, MLP, selection, batched compress); the ring adds its own
-        self.launches_per_step = 9
+        # range, compress; width scan, decompress; scatter pack; batched compress
+        # (tile map, persistent kernel); selector (statistics, MLP, selection, tile
+        # map, batched compress); the ring adds its own
+        self.launches_per_step = 12
 
     def step(self, ev=None):
         zc, s, ws = self.zc, self.s, self.ws
@@ -272,9 +273,10 @@ class RingRow:
         self.eb_abs = REL * rng
         self.ring = RingAllreduce(self.ranks, self.eb_abs, BLOCK, stream=stream)
         self.n = self.ranks[0].numel()
-        # launches: initial compression, P - 1 steps (width scan + fused kernel),
-        # Allgather (width scan + decompression)
-        self.launches = 1 + 2 * (P - 1) + 2
+        # launches: initial compression (tile map + fused kernel), P - 1 steps
+        # (width scan + tile map + fused kernel), Allgather (width scan + tile map +
+        # decompression)
+        self.launches = 2 + 3 * (P - 1) + 3
 
     def step_bytes(self):
         """Algorithmic bytes of one Allreduce: every stream read and written,
@@ -394,6 +396,7 @@ class SelectorRow:
         self.cfg = {}
         for link in (self.LINK_GBS, 100.0):
             self.cfg[link] = tr.cost_model(link_gbs=link)
+        self.uniform_ns = [round(v, 6) for v in tr.uniform_ns_per_byte]
         X, T, keep, _ = S.dataset(tr)
         self.mlp = S.Mlp(seed=0)
         self.mlp.set_norm(X)
@@ -506,9 +509,9 @@ class SelectorRow:
                              "fallbacks": int(counts[0]) if mlp is not None else None,
                              "blocks": {str(b): int((choice == b).sum())
                                         for b in (16, 32, 64, 128, 0)}}
-            rec["cost_model_ns_per_byte"] = {"L16": cfg.ns_per_byte[0], "L32": cfg.ns_per_byte[1],
-                                              "L64": cfg.ns_per_byte[2], "L128": cfg.ns_per_byte[3],
-                                              "raw": cfg.raw_ns_per_byte}
+            rec["cost_model_ns_per_byte"] = {"coded_mixed": cfg.ns_per_byte[0],
+                                              "raw": cfg.raw_ns_per_byte,
+                                              "uniform_L16_L32_L64_L128": self.uniform_ns}
             out["links"][str(link)] = rec
         out["breakdown_ms"] = self.breakdown(self.cfg[self.LINK_GBS])
         # leave the plan as the graph expects it

@@ -61,10 +61,11 @@ int qparams(double eb_abs, float* eb, float* two, float* inv)
     return ZC_OK;
 }
 
-// Workspace: control block, range partials, then 8 arrays of `cap` u64:
+// Workspace: control block, range partials, then 9 arrays of `cap` u64:
 // decode-tile offsets, encoder look-back (flag, wide aggregate, prefix),
-// width-scan look-back (same three), per-item stream-start flags.
-constexpr uint64_t WS_ARRAYS = 8;
+// width-scan look-back (same three), per-item stream-start flags, and the
+// tile-to-item map of multi-item encoder launches (u32 entries).
+constexpr uint64_t WS_ARRAYS = 9;
 
 struct WsView {
     Ctl* ctl;
@@ -72,6 +73,7 @@ struct WsView {
     unsigned long long* offs;
     Chain chB, chC;
     unsigned long long* seg_flag;
+    unsigned* tile_map;
     uint64_t cap;  // decode tiles (and tiles, chunks, items) the workspace can hold
 };
 
@@ -88,6 +90,7 @@ int ws_view(void* ws, size_t bytes, WsView& v)
     v.chB = Chain{base + cap, base + 2 * cap, base + 3 * cap};
     v.chC = Chain{base + 4 * cap, base + 5 * cap, base + 6 * cap};
     v.seg_flag = base + 7 * cap;
+    v.tile_map = (unsigned*)(base + 8 * cap);
     v.cap = cap;
     return ZC_OK;
 }
@@ -431,6 +434,12 @@ int zc_reduce_step_batch(const zc_plan* plan, void* d_ws, size_t ws_bytes, zc_st
             return ZC_ERR_CUDA;
     }
     P.total_tiles = (unsigned)plan->total_tiles;
+    if (plan->n_items > 1) {
+        if (launch_tile_map(P.items, P.n_items, P.total_tiles, w.tile_map, (cudaStream_t)s) !=
+            cudaSuccess)
+            return ZC_ERR_CUDA;
+        P.tile_map = w.tile_map;
+    }
     return cuda_status(launch_reduce_any(lg, C, P, (unsigned)plan->total_tiles, (cudaStream_t)s));
 }
 
@@ -598,6 +607,12 @@ int zc_compress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_stre
     P.total_tiles = (unsigned)plan->total_tiles;
     uint64_t grid = plan->grid > 0 ? (uint64_t)plan->grid : plan->total_tiles;
     if (grid > plan->total_tiles) grid = plan->total_tiles;
+    if (plan->n_msgs > 1) {
+        if (launch_tile_map(P.items, P.n_items, P.total_tiles, w.tile_map, (cudaStream_t)s) !=
+            cudaSuccess)
+            return ZC_ERR_CUDA;
+        P.tile_map = w.tile_map;
+    }
     return cuda_status(launch_batch(C, P, (unsigned)grid, (cudaStream_t)s));
 }
 
@@ -711,6 +726,12 @@ int zc_decompress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_st
     if (launch_wscan(P, (unsigned)plan->total_chunks, (cudaStream_t)s) != cudaSuccess)
         return ZC_ERR_CUDA;
     P.total_tiles = (unsigned)plan->total_tiles;
+    if (plan->n_msgs > 1) {
+        if (launch_tile_map(P.items, P.n_items, P.total_tiles, w.tile_map, (cudaStream_t)s) !=
+            cudaSuccess)
+            return ZC_ERR_CUDA;
+        P.tile_map = w.tile_map;
+    }
     return cuda_status(launch_decompress(P, (unsigned)plan->total_tiles, (cudaStream_t)s));
 }
 

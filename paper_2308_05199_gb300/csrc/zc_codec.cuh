@@ -74,6 +74,9 @@ struct Launch {
     const uint8_t* in_base;
     const unsigned long long* in_off;
     unsigned long long in_cap;
+    // item of every tile (written by k_tile_map before the launch), or null:
+    // then the item is found by a binary search over tile_begin
+    const unsigned* tile_map;
 };
 
 struct Smem {
@@ -798,6 +801,7 @@ struct ItemsSrc {
     __device__ unsigned find(unsigned g) const
     {
         if (P.items == nullptr) return 0u;
+        if (P.tile_map != nullptr) return P.tile_map[g];
         unsigned lo = 0, hi = P.n_items;
         while (hi - lo > 1) {
             const unsigned mid = (lo + hi) >> 1;
@@ -1032,6 +1036,22 @@ __device__ __forceinline__ void resolve_packed(const Launch& P, Item& it, unsign
 
 #ifdef ZC_DECODE_KERNELS  // defined by the one translation unit that launches them
 
+// Item of every encoder tile of a multi-item launch, so that a CTA finds its
+// tile's item with one load instead of a binary search of dependent loads.
+__global__ void __launch_bounds__(NTHREADS) k_tile_map(const Item* items, unsigned n_items,
+                                                      unsigned total_tiles, unsigned* map)
+{
+    const unsigned g = blockIdx.x * NTHREADS + threadIdx.x;
+    if (g >= total_tiles) return;
+    unsigned lo = 0, hi = n_items;
+    while (hi - lo > 1) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (__ldg(&items[mid].tile_begin) <= g) lo = mid;
+        else hi = mid;
+    }
+    map[g] = lo;
+}
+
 // ---- width scan: payload offset of every decode tile --------------------------
 // One CTA per chunk of WSCAN warp units of one item; thread i sums the plane
 // bytes of unit i from its width bytes; a CTA scan and a look-back over the
@@ -1199,7 +1219,9 @@ __global__ void __launch_bounds__(NTHREADS) k_decompress(const Launch P)
     __shared__ __align__(16) int2 meta[NWARPS][DEC_U * 2];
     const unsigned tile = blockIdx.x;
     unsigned idx = 0;
-    if (P.items != nullptr) {
+    if (P.tile_map != nullptr) {
+        idx = P.tile_map[tile];
+    } else if (P.items != nullptr) {
         unsigned lo = 0, hi = P.n_items;
         while (hi - lo > 1) {
             const unsigned mid = (lo + hi) >> 1;

@@ -10,6 +10,14 @@ cudaError_t launch_wscan(const Launch& P, unsigned grid, cudaStream_t s)
     return cudaGetLastError();
 }
 
+cudaError_t launch_tile_map(const Item* items, unsigned n_items, unsigned total_tiles,
+                            unsigned* map, cudaStream_t s)
+{
+    k_tile_map<<<(total_tiles + NTHREADS - 1) / NTHREADS, NTHREADS, 0, s>>>(items, n_items,
+                                                                           total_tiles, map);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_decompress(const Launch& P, unsigned grid, cudaStream_t s)
 {
     k_decompress<<<grid, NTHREADS, 0, s>>>(P);

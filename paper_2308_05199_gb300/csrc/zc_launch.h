@@ -37,6 +37,8 @@ cudaError_t launch_batch_u(const Launch& P, unsigned grid, cudaStream_t s)
 
 cudaError_t launch_wscan(const Launch& P, unsigned grid, cudaStream_t s);
 cudaError_t launch_decompress(const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_tile_map(const Item* items, unsigned n_items, unsigned total_tiles,
+                            unsigned* map, cudaStream_t s);
 
 // Range: extremes of the listed segments, then (rel > 0) the bound they imply.
 struct RangeSeg {
