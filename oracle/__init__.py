@@ -71,6 +71,8 @@ def _declare(L):
     L.zco_compress.argtypes = [c.c_void_p, c.c_uint64, c.c_int, c.c_double, c.c_int, c.c_void_p,
                                c.c_uint64, u64p, u64p]
     L.zco_compress_raw.argtypes = [c.c_void_p, c.c_uint64, c.c_int, c.c_void_p, c.c_uint64, u64p]
+    L.zco_encode_q_heads.argtypes = L.zco_encode_q.argtypes
+    L.zco_compress_heads.argtypes = L.zco_compress.argtypes
     L.zco_decode_q.argtypes = [c.c_void_p, c.c_uint64, c.c_void_p, c.c_uint64]
     L.zco_decompress.argtypes = [c.c_void_p, c.c_uint64, c.c_void_p, c.c_uint64, c.c_int]
     L.zco_parse_header.argtypes = [c.c_void_p, c.c_uint64, c.POINTER(c.c_int),
@@ -174,6 +176,35 @@ def compress(x: np.ndarray, eb_abs: float, log2L: int = 5) -> bytes:
                             cap, ctypes.byref(n_out), ctypes.byref(bad))
     if st:
         raise OracleError(st, "compress at %d" % bad.value)
+    return out[: n_out.value].tobytes()
+
+
+def compress_heads(x: np.ndarray, eb_abs: float, log2L: int = 5) -> bytes:
+    """Stream with the block heads stored apart (flag bit 1): a 24-bit field
+    per block head, widths over the in-block deltas only."""
+    x = np.ascontiguousarray(x)
+    L = 1 << log2L
+    nb = (x.size + L - 1) // L
+    cap = max_stream_bytes(x.size, log2L) + pad16(3 * nb) + 64
+    out = np.zeros(cap, np.uint8)
+    n_out, bad = ctypes.c_uint64(0), ctypes.c_uint64(0)
+    st = lib().zco_compress_heads(_ptr(x), x.size, _dtype_code(x), float(eb_abs), log2L,
+                                  _ptr(out), cap, ctypes.byref(n_out), ctypes.byref(bad))
+    if st:
+        raise OracleError(st, "compress_heads at %d" % bad.value)
+    return out[: n_out.value].tobytes()
+
+
+def encode_q_heads(q: np.ndarray, eb_f32: float, log2L: int, dtype: int = F32) -> bytes:
+    q = np.ascontiguousarray(q, dtype=np.int32)
+    L = 1 << log2L
+    cap = max_stream_bytes(q.size, log2L) + pad16(3 * ((q.size + L - 1) // L)) + 64
+    out = np.zeros(cap, np.uint8)
+    n_out = ctypes.c_uint64(0)
+    st = lib().zco_encode_q_heads(_ptr(q), q.size, dtype, float(eb_f32), log2L, _ptr(out), cap,
+                                  ctypes.byref(n_out))
+    if st:
+        raise OracleError(st, "encode_q_heads")
     return out[: n_out.value].tobytes()
 
 

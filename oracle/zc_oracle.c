@@ -28,12 +28,20 @@
  * Stream layout (little-endian):
  *   [0,4)   magic 'Z','C','v','1'
  *   [4]     dtype (0 = f32, 1 = bf16)      [5] log2(L)
- *   [6]     flags (bit 0: raw payload)     [7] 0
+ *   [6]     flags (bit 0: raw payload, bit 1: block heads stored apart)
+ *   [7]     0
  *   [8,16)  n (u64)   [16,20) eb (f32)   [20,24) nb (u32)
  *   [24,32) payload bytes before padding (u64)
  *   [32, 32+pad16(nb))            width byte per block, zero padded
- *   [32+pad16(nb), +pad16(P))     block payloads back to back, zero padded
+ *   [.., +pad16(3 nb))            heads-apart streams only: q of every block
+ *                                 head, 24-bit two's complement, little-endian
+ *   [.., +pad16(P))               block payloads back to back, zero padded
  * where pad16(v) rounds v up to a multiple of 16.
+ *
+ * Heads apart (flag bit 1; SURVEY's "format v2"): the block head is stored in
+ * its fixed 3-byte field and its own delta is taken as 0, so the width covers
+ * only d_1 .. d_{L-1}.  Data on a large offset then costs 24 bits per block
+ * instead of the offset's bit length on every element.
  *
  * Parity pins live in tests/test_oracle_*.py: hand-derived streams, the closed
  * form of the stream length, exact-rational checks of the quantizer, the
@@ -224,43 +232,44 @@ static void write_header(uint8_t* out, int dtype, int log2L, int flags, uint64_t
     put_u64(out + 24, payload);
 }
 
+/* Delta of element i (0 <= i < L) of block j: the head predicted from 0, or
+ * (heads apart) taken as 0; tail padding 0. */
+static int32_t block_delta(const int32_t* q, uint64_t n, uint64_t L, uint64_t j, uint64_t i,
+                           int heads)
+{
+    uint64_t e = j * L + i;
+    if (e >= n) return 0;
+    if (i == 0) return heads ? 0 : q[e];
+    return q[e] - q[e - 1];
+}
+
 /* Encode the quantized integers q[0..n) into a stream.  eb is only recorded
  * in the header.  Blocks are encoded one after another; the offset of block j
  * is the running (prefix) sum of the sizes of blocks 0..j-1. */
-int zco_encode_q(const int32_t* q, uint64_t n, int dtype, float eb, int log2L, uint8_t* out,
-                 uint64_t cap, uint64_t* out_len)
+static int encode_q(const int32_t* q, uint64_t n, int dtype, float eb, int log2L, int heads,
+                    uint8_t* out, uint64_t cap, uint64_t* out_len)
 {
     if (log2L < 4 || log2L > 7 || (dtype != O_F32 && dtype != O_BF16)) return O_ERR_ARG;
     const uint64_t L = 1ull << log2L;
     const uint64_t nb = (n + L - 1) / L;
     if (nb > 0xffffffffull) return O_ERR_ARG;
     const uint64_t wbytes = pad16(nb);
-    const uint64_t payload_at = O_HEADER + wbytes;
+    const uint64_t hbytes = heads ? pad16(3 * nb) : 0;
+    const uint64_t payload_at = O_HEADER + wbytes + hbytes;
 
     /* Pass 1: widths and payload size. */
     uint64_t payload = 0;
-    int32_t* d = (int32_t*)malloc(sizeof(int32_t) * L);
     uint8_t* width = (uint8_t*)malloc(nb ? nb : 1);
-    if (!d || !width) {
-        free(d);
-        free(width);
-        return O_ERR_ARG;
-    }
+    if (!width) return O_ERR_ARG;
     for (uint64_t j = 0; j < nb; ++j) {
         uint32_t maxabs = 0;
         for (uint64_t i = 0; i < L; ++i) {
-            uint64_t e = j * L + i;
-            int32_t di;
-            if (e >= n) di = 0; /* tail padding: delta 0 */
-            else if (i == 0) di = q[e]; /* block head predicted from 0 */
-            else di = q[e] - q[e - 1];
-            d[i] = di;
+            int32_t di = block_delta(q, n, L, j, i, heads);
             uint32_t a = (uint32_t)(di < 0 ? -(int64_t)di : di);
             if (a > maxabs) maxabs = a;
         }
         int w = bit_length(maxabs);
         if (w > O_MAX_WIDTH) {
-            free(d);
             free(width);
             return O_ERR_RANGE;
         }
@@ -270,13 +279,21 @@ int zco_encode_q(const int32_t* q, uint64_t n, int dtype, float eb, int log2L, u
     const uint64_t total = payload_at + pad16(payload);
     *out_len = total;
     if (total > cap) {
-        free(d);
         free(width);
         return O_ERR_CAPACITY;
     }
     memset(out, 0, total);
-    write_header(out, dtype, log2L, 0, n, eb, (uint32_t)nb, payload);
+    write_header(out, dtype, log2L, heads ? 2 : 0, n, eb, (uint32_t)nb, payload);
     for (uint64_t j = 0; j < nb; ++j) out[O_HEADER + j] = width[j];
+    if (heads) {
+        for (uint64_t j = 0; j < nb; ++j) {
+            uint32_t h = (uint32_t)q[j * L] & 0xffffffu;  /* |q| <= 2^22: fits 24 bits */
+            uint8_t* p = out + O_HEADER + wbytes + 3 * j;
+            p[0] = (uint8_t)h;
+            p[1] = (uint8_t)(h >> 8);
+            p[2] = (uint8_t)(h >> 16);
+        }
+    }
 
     /* Pass 2: bit planes. */
     uint64_t off = payload_at;
@@ -285,11 +302,7 @@ int zco_encode_q(const int32_t* q, uint64_t n, int dtype, float eb, int log2L, u
         int w = width[j];
         if (w == 0) continue;
         for (uint64_t i = 0; i < L; ++i) {
-            uint64_t e = j * L + i;
-            int32_t di;
-            if (e >= n) di = 0;
-            else if (i == 0) di = q[e];
-            else di = q[e] - q[e - 1];
+            int32_t di = block_delta(q, n, L, j, i, heads);
             uint32_t a = (uint32_t)(di < 0 ? -(int64_t)di : di);
             /* sign plane */
             if (di < 0) out[off + i / 8] |= (uint8_t)(1u << (i % 8));
@@ -300,9 +313,21 @@ int zco_encode_q(const int32_t* q, uint64_t n, int dtype, float eb, int log2L, u
         }
         off += (uint64_t)(w + 1) * plane_bytes;
     }
-    free(d);
     free(width);
     return O_OK;
+}
+
+int zco_encode_q(const int32_t* q, uint64_t n, int dtype, float eb, int log2L, uint8_t* out,
+                 uint64_t cap, uint64_t* out_len)
+{
+    return encode_q(q, n, dtype, eb, log2L, 0, out, cap, out_len);
+}
+
+/* The same with block heads stored apart (stream flag bit 1). */
+int zco_encode_q_heads(const int32_t* q, uint64_t n, int dtype, float eb, int log2L,
+                       uint8_t* out, uint64_t cap, uint64_t* out_len)
+{
+    return encode_q(q, n, dtype, eb, log2L, 1, out, cap, out_len);
 }
 
 int zco_compress(const void* x, uint64_t n, int dtype, double eb_abs, int log2L, uint8_t* out,
@@ -316,6 +341,21 @@ int zco_compress(const void* x, uint64_t n, int dtype, double eb_abs, int log2L,
     if (!q) return O_ERR_ARG;
     st = zco_quantize(x, n, dtype, eb_abs, q, bad_index);
     if (!st) st = zco_encode_q(q, n, dtype, eb, log2L, out, cap, out_len);
+    free(q);
+    return st;
+}
+
+int zco_compress_heads(const void* x, uint64_t n, int dtype, double eb_abs, int log2L,
+                       uint8_t* out, uint64_t cap, uint64_t* out_len, uint64_t* bad_index)
+{
+    float eb, two_eb;
+    int st = zco_qparams(eb_abs, &eb, &two_eb);
+    if (st) return st;
+    if (log2L < 4 || log2L > 7 || (dtype != O_F32 && dtype != O_BF16)) return O_ERR_ARG;
+    int32_t* q = (int32_t*)malloc(sizeof(int32_t) * (n ? n : 1));
+    if (!q) return O_ERR_ARG;
+    st = zco_quantize(x, n, dtype, eb_abs, q, bad_index);
+    if (!st) st = encode_q(q, n, dtype, eb, log2L, 1, out, cap, out_len);
     free(q);
     return st;
 }
@@ -351,7 +391,7 @@ static int parse_header(const uint8_t* s, uint64_t len, o_header* h)
     h->dtype = s[4];
     h->log2L = s[5];
     h->flags = s[6];
-    if (s[7] != 0 || (h->flags & ~1) != 0) return O_ERR_FORMAT;
+    if (s[7] != 0 || (h->flags & ~3) != 0 || h->flags == 3) return O_ERR_FORMAT;
     if (h->dtype != O_F32 && h->dtype != O_BF16) return O_ERR_FORMAT;
     h->n = get_u64(s + 8);
     uint32_t ebits = get_u32(s + 16);
@@ -368,7 +408,8 @@ static int parse_header(const uint8_t* s, uint64_t len, o_header* h)
     if ((uint64_t)h->nb != (h->n + L - 1) / L) return O_ERR_FORMAT;
     float e = h->eb;
     if (h->nb > 0 && (!isnormal(e) || e <= 0.0f || !isfinite(e + e))) return O_ERR_FORMAT;
-    if (O_HEADER + pad16(h->nb) + pad16(h->payload) > len) return O_ERR_FORMAT;
+    const uint64_t hbytes = (h->flags & 2) ? pad16(3 * (uint64_t)h->nb) : 0;
+    if (O_HEADER + pad16(h->nb) + hbytes + pad16(h->payload) > len) return O_ERR_FORMAT;
     uint64_t sum = 0;
     for (uint64_t j = 0; j < h->nb; ++j) {
         int w = s[O_HEADER + j];
@@ -389,10 +430,17 @@ int zco_decode_q(const uint8_t* s, uint64_t len, int32_t* q, uint64_t n)
     if (h.n != n || (h.flags & 1)) return O_ERR_FORMAT;
     const uint64_t L = 1ull << h.log2L;
     const uint64_t plane_bytes = L / 8;
-    uint64_t off = O_HEADER + pad16(h.nb);
+    const int heads = (h.flags & 2) != 0;
+    const uint64_t head_at = O_HEADER + pad16(h.nb);
+    uint64_t off = head_at + (heads ? pad16(3 * (uint64_t)h.nb) : 0);
     for (uint64_t j = 0; j < h.nb; ++j) {
         int w = s[O_HEADER + j];
         int32_t acc = 0;
+        if (heads) {  /* the stored head; its delta in the planes is 0 */
+            const uint8_t* p = s + head_at + 3 * j;
+            uint32_t v = (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16);
+            acc = (int32_t)v - ((v & 0x800000u) ? (int32_t)(1 << 24) : 0);  /* 24-bit signed */
+        }
         for (uint64_t i = 0; i < L; ++i) {
             int32_t di = 0;
             if (w > 0) {
