@@ -521,6 +521,55 @@ class SelectorRow:
         return out
 
 
+def heads_report(torch, zc, W, reps=5):
+    """The heads-apart format against the plain one on the 512^3 field and on
+    the same field shifted by +100 (a DC offset far above eb = 2e-3): ratio
+    and compression / decompression GB/s (L = 32, absolute bound of the REL
+    1e-3 field)."""
+    st = W.stream
+    s = st.cuda_stream
+    n = W.n
+    eb = REL * 2.0  # the field spans [-1, 1]
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(f):
+        f()
+        e0, e1 = ev(), ev()
+        e0.record(st)
+        for _ in range(reps):
+            f()
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    shifted = torch.empty_like(W.field)
+    with torch.cuda.stream(st):
+        shifted.copy_(W.field)
+        shifted.add_(100.0)
+    cap = zc.zc_max_compressed_bytes_heads(n, BLOCK)
+    buf = torch.empty(cap, dtype=torch.uint8, device=W.field.device)
+    nb = torch.zeros(1, dtype=torch.int64, device=W.field.device)
+    for name, x in (("field", W.field), ("field_plus_100", shifted)):
+        rec = {}
+        for fmt, fn in (("plain", zc.zc_compress), ("heads_apart", zc.zc_compress_heads)):
+            c = lambda: zc._check(fn(x.data_ptr(), n, zc.F32, zc.EB_ABS, eb, BLOCK, buf.data_ptr(),
+                                     cap, nb.data_ptr(), W.ws.ptr, W.ws.nbytes, s), "compress")
+            tc = timed(c)
+            C = int(nb.item())
+            d = lambda: zc._check(zc.zc_decompress(buf.data_ptr(), cap, W.dec.data_ptr(), n, zc.F32,
+                                                   W.ws.ptr, W.ws.nbytes, s), "decompress")
+            td = timed(d)
+            rec[fmt] = {"ratio": round(4 * n / C, 3), "compress_gbs": round((4 * n + C) / tc / 1e6, 1),
+                        "decompress_gbs": round((4 * n + C) / td / 1e6, 1)}
+        out[name] = rec
+    del shifted, buf
+    torch.cuda.empty_cache()
+    st_, _ = W.ws.status(st)
+    out["status"] = st_
+    return out
+
+
 def size_sweep(torch, zc, workloads, stream, device, max_bytes=646 << 20, reps=5):
     """Compression / decompression time over message sizes (the paper's
     characterization of its GPU compressor, Sec. 3.2.2, on uniform synthetic
@@ -662,6 +711,7 @@ def run_ours(args, rank, world):
     batched = W.batch_row.compare()
     selector = W.sel_row.report()
     sweep = size_sweep(torch, zc, workloads, W.stream, dev) if args.sweep else None
+    heads = heads_report(torch, zc, W)
     coll = collectives_report(torch, workloads, W.stream, dev,
                               [int(v) for v in args.collective_ranks.split(",") if v],
                               args.ring_side) if args.collective_ranks else None
@@ -741,6 +791,7 @@ def run_ours(args, rank, world):
         "ring": dict(W.ring_row.errors(), ranks=W.ring_row.P, n_per_rank=W.ring_row.n),
         "collectives": coll,
         "size_sweep": sweep,
+        "heads_apart": heads,
     }
     if not args.no_e2e:
         out["e2e"] = e2e_ours(torch, W, args, step_bytes, world)

@@ -123,6 +123,23 @@ int zc_compress(const void* d_in, uint64_t n, int dtype, int eb_mode, double eb_
                 void* d_out, size_t out_cap, uint64_t* d_out_bytes, void* d_ws, size_t ws_bytes,
                 zc_stream_t s);
 
+/* Compression into the heads-apart stream format (header flag bit 1): every
+ * block head q is stored in a fixed 24-bit little-endian two's-complement
+ * field after the width bytes (3 nb bytes, zero padded to 16) and its own
+ * delta is taken as 0, so a block's width covers only its in-block deltas.
+ * Data on a large offset (a DC level far above eb) then costs 24 bits per
+ * block instead of the offset's bit length on every element.  The paper's
+ * blockwise Lorenzo predicts the block head from 0 (zc_compress); this
+ * variant is this project's format extension, decoded by zc_decompress like
+ * any stream.  Arguments as zc_compress; out_cap must hold at least the
+ * header, width bytes and heads (32 + pad16(nb) + pad16(3 nb)), else
+ * ZC_ERR_CAPACITY; zc_max_compressed_bytes_heads is the worst case.  Always
+ * uses 8-chunk tiles. */
+int zc_compress_heads(const void* d_in, uint64_t n, int dtype, int eb_mode, double eb_value,
+                      int block, void* d_out, size_t out_cap, uint64_t* d_out_bytes, void* d_ws,
+                      size_t ws_bytes, zc_stream_t s);
+size_t zc_max_compressed_bytes_heads(uint64_t n, int block);
+
 /* Decompress a stream of n elements into d_out as FP32 or BF16 (RNE of the
  * FP32 reconstruction).  The stream's own header gives L and eb; a header
  * that does not match n, a width above 24 or a block that would read past

@@ -222,9 +222,24 @@ int zc_minmax(const void* d_in, uint64_t n, int dtype, float* d_minmax, void* d_
     return cuda_status(launch_range(R, range_grid(n), (cudaStream_t)s));
 }
 
-int zc_compress(const void* d_in, uint64_t n, int dtype, int eb_mode, double eb_value, int block,
-                void* d_out, size_t out_cap, uint64_t* d_out_bytes, void* d_ws, size_t ws_bytes,
-                zc_stream_t s)
+}  // extern "C"
+
+namespace {
+
+cudaError_t launch_compress_heads_any(int lg, int dt, const Launch& P, unsigned grid,
+                                      cudaStream_t s)
+{
+    switch (lg) {
+    case 4: return launch_compress_heads_l16(dt, P, grid, s);
+    case 5: return launch_compress_heads_l32(dt, P, grid, s);
+    case 6: return launch_compress_heads_l64(dt, P, grid, s);
+    default: return launch_compress_heads_l128(dt, P, grid, s);
+    }
+}
+
+int compress_impl(const void* d_in, uint64_t n, int dtype, int eb_mode, double eb_value,
+                  int block, void* d_out, size_t out_cap, uint64_t* d_out_bytes, void* d_ws,
+                  size_t ws_bytes, zc_stream_t s, bool heads)
 {
     const int lg = log2_block(block);
     if (lg < 0 || !dtype_ok(dtype) || (n > 0 && d_in == nullptr) || d_out == nullptr ||
@@ -234,11 +249,13 @@ int zc_compress(const void* d_in, uint64_t n, int dtype, int eb_mode, double eb_
     if (!(eb_value > 0.0) || !std::isfinite(eb_value)) return ZC_ERR_ARG;
     const uint64_t nb = (n + (1ull << lg) - 1) >> lg;
     if (nb > 0xffffffffull) return ZC_ERR_ARG;
-    if (out_cap < 32 + pad16(nb)) return ZC_ERR_CAPACITY;
+    // the heads (stored apart) are written straight to their place: all of
+    // their area must fit
+    if (out_cap < 32 + pad16(nb) + (heads ? pad16(3 * nb) : 0)) return ZC_ERR_CAPACITY;
     WsView w;
     int st = ws_view(d_ws, ws_bytes, w);
     if (st) return st;
-    const int C = g_chunks;
+    const int C = heads ? 8 : g_chunks;
     const uint64_t tiles = tiles_for(n, unit_rows(C));
     if (tiles > w.cap || tiles > 0x7fffffffull) return ZC_ERR_WORKSPACE;
     Launch P = base_launch(w);
@@ -269,7 +286,37 @@ int zc_compress(const void* d_in, uint64_t n, int dtype, int eb_mode, double eb_
     P.n_items = 1;
     P.total_tiles = (unsigned)tiles;
     P.urows = unit_rows(C);
+    if (heads)
+        return cuda_status(launch_compress_heads_any(lg, dtype, P, (unsigned)tiles, (cudaStream_t)s));
     return cuda_status(launch_compress_any(lg, C, dtype, P, (unsigned)tiles, (cudaStream_t)s));
+}
+
+}  // namespace
+
+extern "C" {
+
+int zc_compress(const void* d_in, uint64_t n, int dtype, int eb_mode, double eb_value, int block,
+                void* d_out, size_t out_cap, uint64_t* d_out_bytes, void* d_ws, size_t ws_bytes,
+                zc_stream_t s)
+{
+    return compress_impl(d_in, n, dtype, eb_mode, eb_value, block, d_out, out_cap, d_out_bytes,
+                         d_ws, ws_bytes, s, false);
+}
+
+int zc_compress_heads(const void* d_in, uint64_t n, int dtype, int eb_mode, double eb_value,
+                      int block, void* d_out, size_t out_cap, uint64_t* d_out_bytes, void* d_ws,
+                      size_t ws_bytes, zc_stream_t s)
+{
+    return compress_impl(d_in, n, dtype, eb_mode, eb_value, block, d_out, out_cap, d_out_bytes,
+                         d_ws, ws_bytes, s, true);
+}
+
+size_t zc_max_compressed_bytes_heads(uint64_t n, int block)
+{
+    const int lg = log2_block(block);
+    if (lg < 0) return 0;
+    const uint64_t nb = (n + (1ull << lg) - 1) >> lg;
+    return zc_max_compressed_bytes(n, block) + pad16(3 * nb);
 }
 
 int zc_decompress(const void* d_cmp, size_t cmp_cap, void* d_out, uint64_t n, int out_dtype,

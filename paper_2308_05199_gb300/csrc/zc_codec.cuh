@@ -132,9 +132,10 @@ __device__ __forceinline__ int warp_sum(int v)
     return v;
 }
 
-// Reads and checks an input stream header for `it`; returns its log2 L, -1
-// for a format error (reported when `report`), -2 / -3 for a raw FP32 / BF16
-// stream.
+// Reads and checks an input stream header for `it`; returns its log2 L (plus
+// 8 when its block heads are stored apart), -1 for a format error (reported
+// when `report`), -2 / -3 for a raw FP32 / BF16 stream.  A caller that names
+// the block size it expects (the fused ring step) takes plain streams only.
 __device__ __forceinline__ int check_header(const Item& it, Ctl* ctl, unsigned item_idx,
                                             int expect_log2L, float& eb_in, bool report)
 {
@@ -151,7 +152,7 @@ __device__ __forceinline__ int check_header(const Item& it, Ctl* ctl, unsigned i
     const unsigned long long payload = __ldg((const unsigned long long*)s + 3);
     const int dtype = w1 & 0xff, lg = (w1 >> 8) & 0xff, flags = (w1 >> 16) & 0xff;
     bool ok = w0 == 0x3176435au && (w1 >> 24) == 0u && (dtype == 0 || dtype == 1) &&
-              (flags & ~1) == 0 && n == it.n;
+              (flags & ~3) == 0 && flags != 3 && n == it.n;
     int ret = lg;
     if (ok && (flags & 1)) {
         const unsigned long long es = dtype == 0 ? 4ull : 2ull;
@@ -159,10 +160,13 @@ __device__ __forceinline__ int check_header(const Item& it, Ctl* ctl, unsigned i
              expect_log2L < 0;
         ret = -2 - dtype;
     } else if (ok) {
-        ok = lg >= 4 && lg <= 7 && (expect_log2L < 0 || lg == expect_log2L) &&
+        const bool heads = (flags & 2) != 0;
+        ok = lg >= 4 && lg <= 7 && (expect_log2L < 0 || (lg == expect_log2L && !heads)) &&
              (unsigned long long)nb == ((n + (1ull << lg) - 1) >> lg) &&
-             32ull + ceil16(nb) + ceil16(payload) <= it.cin_cap;
+             32ull + ceil16(nb) + (heads ? ceil16(3ull * nb) : 0ull) + ceil16(payload) <=
+                 it.cin_cap;
         if (ok && nb > 0) ok = is_normal(eb_in) && eb_in > 0.0f && isfinite(eb_in + eb_in);
+        if (heads) ret = lg + 8;
     }
     if (!ok) {
         if (report) fail(ctl, ZC_ERR_FORMAT, item_idx);
@@ -208,7 +212,7 @@ __device__ __forceinline__ float scan_incl_f16(float v)
 // meta[b] = (planes, byte offset from the unit's payload start) for the
 // unit's blocks.  Returns the unit's payload start in the stream; a unit whose
 // planes would lie beyond cin_cap is reported and gets zero planes.
-template <int LOG2L, int U>
+template <int LOG2L, int U, bool HEADS = false>
 __device__ __forceinline__ unsigned long long unit_meta(const Launch& P, const Item& it,
                                                         unsigned slot, unsigned long long ue0,
                                                         int2* meta, bool& narrow)
@@ -261,7 +265,8 @@ __device__ __forceinline__ unsigned long long unit_meta(const Launch& P, const I
     }
     int tot;
     int off = warp_excl_scan(sum, lane, tot);
-    const unsigned long long base = 32ull + ceil16(nb) + P.offs[slot];
+    const unsigned long long base =
+        32ull + ceil16(nb) + (HEADS ? ceil16(3ull * nb) : 0ull) + P.offs[slot];
     const bool ok = base + (unsigned long long)tot <= it.cin_cap;
     if (!ok && lane == 0) fail(P.ctl, ZC_ERR_FORMAT, slot);
     __syncwarp();  // earlier readers of meta are done
@@ -290,9 +295,18 @@ __device__ __forceinline__ float delta_f(uint32_t u)
 // loads overlap.  A pair of rows whose blocks have at most 16 planes shares
 // one transpose and is scanned in FP32 (every partial sum is an integer below
 // 2^22: exact); wider rows are scanned in integers.
-template <int LOG2L, bool NARROW>
+// Block head of the heads-apart format: 24-bit two's complement, little-endian.
+__device__ __forceinline__ int load_head(const uint8_t* p)
+{
+    const unsigned v = (unsigned)__ldg(p) | ((unsigned)__ldg(p + 1) << 8) |
+                       ((unsigned)__ldg(p + 2) << 16);
+    return (int)v - ((v & 0x800000u) ? (1 << 24) : 0);
+}
+
+template <int LOG2L, bool NARROW, bool HEADS = false>
 __device__ __forceinline__ void decode_group(const uint8_t* src, const int2* meta, int g,
-                                             float two_eb, float acc[GR], const TpC& tc)
+                                             float two_eb, float acc[GR], const TpC& tc,
+                                             const uint8_t* hsrc = nullptr)
 {
     constexpr int L = 1 << LOG2L;
     constexpr int RPB = L >= 32 ? L / 32 : 1;
@@ -303,7 +317,19 @@ __device__ __forceinline__ void decode_group(const uint8_t* src, const int2* met
     const bool hi = lane >= 16;
     const int fb = L >= 32 ? g * GR / RPB : g * GR * 2;  // first block of the group
     const int2* mt = meta + fb;
-    // ---- phase 1: metadata and plane loads of every step ----
+    // ---- phase 1: metadata, plane loads (and block heads) of every step ----
+    int hv[GR];  // heads apart: the head of this lane's block where this lane is one
+    if (HEADS) {
+#pragma unroll
+        for (int r = 0; r < GR; ++r) {
+            hv[r] = 0;
+            int b = -1;  // block of the unit whose head this lane holds in row r
+            if (L == 16 && k == 0) b = 2 * (g * GR + r) + (hi ? 1 : 0);
+            else if (L == 32 && lane == 0) b = g * GR + r;
+            else if (L >= 64 && lane == 0 && (r % RPB) == 0) b = (g * GR + r) / RPB;
+            if (b >= 0) hv[r] = load_head(hsrc + 3 * b);
+        }
+    }
     uint32_t wv[NS][NR];
     unsigned paired = 0;  // bit s: step s has at most 16 planes per block
 #pragma unroll
@@ -389,7 +415,9 @@ __device__ __forceinline__ void decode_group(const uint8_t* src, const int2* met
             float carry = 0.0f;
 #pragma unroll
             for (int h = 0; h < NR; ++h) {
-                float v = L == 16 ? scan_incl_f16(delta_f(u[h])) : scan_incl_f(delta_f(u[h]));
+                float dv = delta_f(u[h]);
+                if (HEADS) dv = __fadd_rn(dv, __int2float_rn(hv[r + h]));  // the head's delta is 0
+                float v = L == 16 ? scan_incl_f16(dv) : scan_incl_f(dv);
                 if (L >= 64 && ((r + h) % RPB) != 0) v = __fadd_rn(v, carry);
                 if (L >= 64 && ((r + h) % RPB) != RPB - 1) carry = __shfl_sync(FULL, v, 31);
                 acc[r + h] = __fmul_rn(v, two_eb);
@@ -399,8 +427,9 @@ __device__ __forceinline__ void decode_group(const uint8_t* src, const int2* met
 #pragma unroll
             for (int h = 0; h < NR; ++h) {
                 const int mag = (int)(u[h] >> 1);
-                int v = L == 16 ? scan_incl<16>((u[h] & 1u) ? -mag : mag)
-                                : scan_incl<32>((u[h] & 1u) ? -mag : mag);
+                int dv = (u[h] & 1u) ? -mag : mag;
+                if (HEADS) dv += hv[r + h];
+                int v = L == 16 ? scan_incl<16>(dv) : scan_incl<32>(dv);
                 if (L >= 64 && ((r + h) % RPB) != 0) v += carry;
                 if (L >= 64 && ((r + h) % RPB) != RPB - 1) carry = __shfl_sync(FULL, v, 31);
                 acc[r + h] = __fmul_rn(__int2float_rn(v), two_eb);
@@ -430,10 +459,10 @@ __device__ __forceinline__ int prev_lane(int q, int fill)
     return p;
 }
 
-template <int LOG2L, bool ALL>
+template <int LOG2L, bool ALL, bool HEADS = false>
 __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float eb, float two_eb,
                                             float inv, uint8_t* seg, int lo, uint8_t* wb, int& err,
-                                            const TpC& tc)
+                                            const TpC& tc, uint8_t* hout = nullptr)
 {
     constexpr int L = 1 << LOG2L;
     constexpr int RPB = L >= 32 ? L / 32 : 1;
@@ -464,6 +493,23 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
         if (L >= 64 && (r % RPB) != RPB - 1) carry = __shfl_sync(FULL, q[r], 31);
         int d = q[r] - prev;
         if (!ALL && r * 32 + lane >= nrem) d = 0;
+        if (HEADS) {
+            // heads apart: the block head goes to its 3-byte field (in the
+            // output, at block position), its own delta is 0
+            int b = -1;
+            if (L == 16 && k == 0) b = 2 * r + (hi ? 1 : 0);
+            else if (L == 32 && lane == 0) b = r;
+            else if (L >= 64 && lane == 0 && (r % RPB) == 0) b = r / RPB;
+            if (b >= 0) {
+                if (ALL || r * 32 + lane < nrem) {
+                    uint8_t* p = hout + 3 * b;
+                    p[0] = (uint8_t)q[r];
+                    p[1] = (uint8_t)(q[r] >> 8);
+                    p[2] = (uint8_t)(q[r] >> 16);
+                }
+                d = 0;
+            }
+        }
         const uint32_t ad = (uint32_t)(d < 0 ? -d : d);
         u[r] = __funnelshift_l((uint32_t)d, ad, 1);  // |d| << 1 | sign
         wide |= u[r];
@@ -613,11 +659,14 @@ __device__ __forceinline__ bool packed_start(const Launch& P, bool first, unsign
 // into its own shared-memory segment.  HAS_CIN: decode `it.cin` first (same
 // block size, unit offsets from k_wscan) and add the local chunk.  The FP32
 // sum goes to `it.raw_out` when that is set.  Null pointers switch a step off.
-template <int LOG2L, int U, bool HAS_CIN, typename TX>
+template <int LOG2L, int U, bool HAS_CIN, typename TX, bool HEADS = false>
 __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, unsigned item_idx,
                                             unsigned tile_in_item, unsigned g, Smem& sm,
                                             uint8_t* dsm)
 {
+    // HEADS (block heads stored apart) is for single, unpacked streams: the
+    // heads are written straight to their fixed place in the output.
+    static_assert(!HEADS || !HAS_CIN, "heads apart: compression only");
     constexpr int L = 1 << LOG2L;
     constexpr int PB = L / 8;
     constexpr int BU = U * 32 / L;  // blocks per warp unit
@@ -629,6 +678,7 @@ __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, uns
     const unsigned long long ue0 = te0 + (unsigned long long)warp * U * 32;
     const unsigned long long nb = (n + L - 1) >> LOG2L;
     const unsigned long long wbytes = ceil16(nb);
+    const unsigned long long hbytes = HEADS ? ceil16(3ull * nb) : 0ull;
     const bool first = tile_in_item == 0;
     const bool last = tile_in_item + 1 == it.ntiles;
     const bool do_cin = HAS_CIN && it.cin != nullptr;
@@ -715,12 +765,14 @@ __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, uns
             }
             if (do_enc) {
                 const int b0 = L >= 32 ? gi * GR / (L / 32) : gi * GR * 2;
+                uint8_t* hout = nullptr;
+                if (HEADS) hout = it.out + 32 + wbytes + 3ull * ((ue0 >> LOG2L) + b0);
                 if (nrem == GR * 32)
-                    lo = encode_group<LOG2L, true>(acc, nrem, eb, two_eb, inv, seg, lo, wb + b0,
-                                                   err, tc);
+                    lo = encode_group<LOG2L, true, HEADS>(acc, nrem, eb, two_eb, inv, seg, lo,
+                                                          wb + b0, err, tc, hout);
                 else
-                    lo = encode_group<LOG2L, false>(acc, nrem, eb, two_eb, inv, seg, lo, wb + b0,
-                                                    err, tc);
+                    lo = encode_group<LOG2L, false, HEADS>(acc, nrem, eb, two_eb, inv, seg, lo,
+                                                           wb + b0, err, tc, hout);
             }
         }
     }
@@ -740,13 +792,13 @@ __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, uns
         payload_i += segsz[w];
     }
     const unsigned long long payload = (unsigned long long)payload_i;
-    const unsigned long long agg = payload + (first ? 32ull + wbytes : 0ull);
+    const unsigned long long agg = payload + (first ? 32ull + wbytes + hbytes : 0ull);
     const unsigned g0 = P.packed ? 0u : g - tile_in_item;
     bool to = false;
     const unsigned long long ex = lookback_cta(P.chB, g, g0, agg, last, E, P.wc, ctl, to, sm.lb);
     unsigned long long start = 0ull;
     if (to || !packed_start(P, first, item_idx, ex, g, sm, start)) return;
-    const unsigned long long base = ex + (first ? 32ull + wbytes : 0ull);
+    const unsigned long long base = ex + (first ? 32ull + wbytes + hbytes : 0ull);
     const unsigned long long cap = it.out_cap;
     uint8_t* const out = it.out;
     const unsigned long long end = ex + agg;  // unpadded end of this tile's payload
@@ -767,9 +819,13 @@ __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, uns
     }
     if (last) {
         const unsigned long long total = ceil16(end);
-        const unsigned long long pl = end - start - 32 - wbytes;
+        const unsigned long long pl = end - start - 32 - wbytes - hbytes;
         for (unsigned long long p = start + 32 + nb + tid; p < start + 32 + wbytes; p += NTHREADS)
             if (p < cap) out[p] = 0;
+        if (HEADS)
+            for (unsigned long long p = start + 32 + wbytes + 3 * nb + tid;
+                 p < start + 32 + wbytes + hbytes; p += NTHREADS)
+                if (p < cap) out[p] = 0;
         for (unsigned long long p = end + tid; p < total; p += NTHREADS)
             if (p < cap) out[p] = 0;
         if (tid < 8 && start + 32 <= cap) {
@@ -777,7 +833,7 @@ __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, uns
             const int xdt = HAS_CIN ? ZC_F32 : it.x_dtype;
             switch (tid) {
             case 0: v = 0x3176435au; break;  // "ZCv1"
-            case 1: v = (uint32_t)xdt | ((uint32_t)LOG2L << 8); break;
+            case 1: v = (uint32_t)xdt | ((uint32_t)LOG2L << 8) | (HEADS ? (2u << 16) : 0u); break;
             case 2: v = (uint32_t)n; break;
             case 3: v = (uint32_t)(n >> 32); break;
             case 4: v = __float_as_uint(eb); break;
@@ -887,13 +943,13 @@ __device__ __forceinline__ void tile_loop(const Launch& P, const Src& src, Smem&
     }
 }
 
-template <int LOG2L, int U, typename TX>
+template <int LOG2L, int U, typename TX, bool HEADS = false>
 __global__ void __launch_bounds__(NTHREADS, 4) k_compress(const Launch P)
 {
     __shared__ Smem sm;
     extern __shared__ __align__(16) uint8_t dsm[];
     tile_loop(P, ItemsSrc{P}, sm, [&](const Item& it, unsigned idx, unsigned t, unsigned g) {
-        tile_encode<LOG2L, U, false, TX>(P, it, idx, t, g, sm, dsm);
+        tile_encode<LOG2L, U, false, TX, HEADS>(P, it, idx, t, g, sm, dsm);
     });
 }
 
@@ -1096,12 +1152,13 @@ __global__ void __launch_bounds__(NTHREADS) k_wscan(const Launch P)
         float eb_in;
         const int lg = check_header(it, P.ctl, sm.item, -1, eb_in, false);
         if (lg < 4) continue;  // raw or malformed: the decoder reports it
-        const unsigned long long L = 1ull << lg;
-        const unsigned long long nb = (it.n + L - 1) >> lg;
+        const int lgb = lg & 7;  // block size (heads apart or not: same widths)
+        const unsigned long long L = 1ull << lgb;
+        const unsigned long long nb = (it.n + L - 1) >> lgb;
         const int PB = (int)(L / 8);
         const unsigned long long ntile = (unsigned long long)it.ntiles * NWARPS;  // units
         const unsigned long long k = (unsigned long long)chunk * WSCAN + tid;    // unit in item
-        const int bpt = (P.urows * 32) >> lg;                                    // blocks per unit
+        const int bpt = (P.urows * 32) >> lgb;                                   // blocks per unit
         int sum = 0;
         if (k < ntile) {
             const unsigned long long b0 = k * bpt;
@@ -1177,22 +1234,27 @@ __device__ __forceinline__ void unit_raw_copy(const Item& it, int src_dtype, uns
     }
 }
 
-template <int LOG2L, typename TO>
+template <int LOG2L, typename TO, bool HEADS = false>
 __device__ __forceinline__ void unit_decode(const Launch& P, const Item& it, unsigned slot,
                                             unsigned long long ue0, float two_eb, int2* meta)
 {
     const int lane = threadIdx.x & 31;
     const TpC tc = tp_consts(lane);
     bool narrow;
-    const uint8_t* src = it.cin + unit_meta<LOG2L, DEC_U>(P, it, slot, ue0, meta, narrow);
+    const uint8_t* src = it.cin + unit_meta<LOG2L, DEC_U, HEADS>(P, it, slot, ue0, meta, narrow);
+    const uint8_t* hsrc = nullptr;  // heads apart: the heads of this unit's blocks
+    if (HEADS) {
+        const unsigned long long nb = (it.n + (1ull << LOG2L) - 1) >> LOG2L;
+        hsrc = it.cin + 32 + ceil16(nb) + 3ull * (ue0 >> LOG2L);
+    }
 #pragma unroll 1
     for (int gi = 0; gi < DEC_U / GR; ++gi) {
         const unsigned long long e0 = ue0 + (unsigned long long)gi * GR * 32;
         if (e0 >= it.n) break;
         const int nrem = (int)min(it.n - e0, (unsigned long long)(GR * 32));
         float acc[GR];
-        if (narrow) decode_group<LOG2L, true>(src, meta, gi, two_eb, acc, tc);
-        else decode_group<LOG2L, false>(src, meta, gi, two_eb, acc, tc);
+        if (narrow) decode_group<LOG2L, true, HEADS>(src, meta, gi, two_eb, acc, tc, hsrc);
+        else decode_group<LOG2L, false, HEADS>(src, meta, gi, two_eb, acc, tc, hsrc);
         TO* op = (TO*)it.raw_out + e0 + lane;
         if (nrem == GR * 32) {
 #pragma unroll
@@ -1246,6 +1308,10 @@ __global__ void __launch_bounds__(NTHREADS) k_decompress(const Launch P)
         case 5: unit_decode<5, float>(P, it, slot, ue0, two, meta[warp]); return;
         case 6: unit_decode<6, float>(P, it, slot, ue0, two, meta[warp]); return;
         case 7: unit_decode<7, float>(P, it, slot, ue0, two, meta[warp]); return;
+        case 12: unit_decode<4, float, true>(P, it, slot, ue0, two, meta[warp]); return;
+        case 13: unit_decode<5, float, true>(P, it, slot, ue0, two, meta[warp]); return;
+        case 14: unit_decode<6, float, true>(P, it, slot, ue0, two, meta[warp]); return;
+        case 15: unit_decode<7, float, true>(P, it, slot, ue0, two, meta[warp]); return;
         default: break;
         }
     } else {
@@ -1254,6 +1320,10 @@ __global__ void __launch_bounds__(NTHREADS) k_decompress(const Launch P)
         case 5: unit_decode<5, uint16_t>(P, it, slot, ue0, two, meta[warp]); return;
         case 6: unit_decode<6, uint16_t>(P, it, slot, ue0, two, meta[warp]); return;
         case 7: unit_decode<7, uint16_t>(P, it, slot, ue0, two, meta[warp]); return;
+        case 12: unit_decode<4, uint16_t, true>(P, it, slot, ue0, two, meta[warp]); return;
+        case 13: unit_decode<5, uint16_t, true>(P, it, slot, ue0, two, meta[warp]); return;
+        case 14: unit_decode<6, uint16_t, true>(P, it, slot, ue0, two, meta[warp]); return;
+        case 15: unit_decode<7, uint16_t, true>(P, it, slot, ue0, two, meta[warp]); return;
         default: break;
         }
     }

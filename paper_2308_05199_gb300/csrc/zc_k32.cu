@@ -21,6 +21,19 @@ static cudaError_t compress_u(int x_dtype, const Launch& P, unsigned grid, cudaS
     return cudaGetLastError();
 }
 
+// Block heads stored apart: 8-chunk tiles (64-row warp units) only.
+cudaError_t launch_compress_heads_l32(int x_dtype, const Launch& P, unsigned grid, cudaStream_t s)
+{
+    static const cudaError_t e32 = prepare(k_compress<5, 64, float, true>, 64);
+    static const cudaError_t e16 = prepare(k_compress<5, 64, uint16_t, true>, 64);
+    if (e32 != cudaSuccess || e16 != cudaSuccess) return e32 != cudaSuccess ? e32 : e16;
+    if (x_dtype == ZC_F32)
+        k_compress<5, 64, float, true><<<grid, NTHREADS, enc_smem_bytes(64), s>>>(P);
+    else
+        k_compress<5, 64, uint16_t, true><<<grid, NTHREADS, enc_smem_bytes(64), s>>>(P);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_compress_l32(int chunks, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s)
 {
     switch (chunks) {

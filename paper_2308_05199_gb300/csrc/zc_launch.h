@@ -12,6 +12,10 @@ cudaError_t launch_compress_l16(int S, int x_dtype, const Launch& P, unsigned gr
 cudaError_t launch_compress_l32(int S, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
 cudaError_t launch_compress_l64(int S, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
 cudaError_t launch_compress_l128(int S, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_compress_heads_l16(int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_compress_heads_l32(int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_compress_heads_l64(int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
+cudaError_t launch_compress_heads_l128(int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
 cudaError_t launch_reduce_l16(int S, const Launch& P, unsigned grid, cudaStream_t s);
 cudaError_t launch_reduce_l32(int S, const Launch& P, unsigned grid, cudaStream_t s);
 cudaError_t launch_reduce_l64(int S, const Launch& P, unsigned grid, cudaStream_t s);

@@ -111,6 +111,8 @@ def _declare(L):
         "zc_workspace_init": (i32, [vp, sz, vp]),
         "zc_minmax": (i32, [vp, u64, i32, vp, vp, sz, vp]),
         "zc_compress": (i32, [vp, u64, i32, i32, dbl, i32, vp, sz, vp, vp, sz, vp]),
+        "zc_compress_heads": (i32, [vp, u64, i32, i32, dbl, i32, vp, sz, vp, vp, sz, vp]),
+        "zc_max_compressed_bytes_heads": (sz, [u64, i32]),
         "zc_decompress": (i32, [vp, sz, vp, u64, i32, vp, sz, vp]),
         "zc_reduce_step": (i32, [vp, sz, vp, u64, dbl, i32, vp, sz, vp, vp, vp, sz, vp]),
         "zc_plan_table_bytes": (sz, [i32]),
@@ -158,7 +160,8 @@ def _declare(L):
 
 def exported_names():
     return ["zc_max_compressed_bytes", "zc_raw_stream_bytes", "zc_workspace_bytes",
-            "zc_workspace_init", "zc_minmax", "zc_compress", "zc_decompress", "zc_reduce_step",
+            "zc_workspace_init", "zc_minmax", "zc_compress", "zc_compress_heads",
+            "zc_max_compressed_bytes_heads", "zc_decompress", "zc_reduce_step",
             "zc_plan_table_bytes", "zc_plan_reduce", "zc_reduce_step_batch", "zc_scatter_pack",
             "zc_compress_noalloc", "zc_batch_table_bytes", "zc_batch_max_bytes",
             "zc_plan_compress_batch", "zc_compress_batch", "zc_plan_decompress_batch",
@@ -218,6 +221,16 @@ def zc_compress(d_in, n, dtype, eb_mode, eb_value, block, d_out, out_cap, d_out_
                 ws_bytes, stream) -> int:
     return lib().zc_compress(d_in, n, dtype, eb_mode, eb_value, block, d_out, out_cap,
                              d_out_bytes, d_ws, ws_bytes, stream)
+
+
+def zc_compress_heads(d_in, n, dtype, eb_mode, eb_value, block, d_out, out_cap, d_out_bytes,
+                      d_ws, ws_bytes, stream) -> int:
+    return lib().zc_compress_heads(d_in, n, dtype, eb_mode, eb_value, block, d_out, out_cap,
+                                   d_out_bytes, d_ws, ws_bytes, stream)
+
+
+def zc_max_compressed_bytes_heads(n: int, block: int) -> int:
+    return lib().zc_max_compressed_bytes_heads(n, block)
 
 
 def zc_decompress(d_cmp, cmp_cap, d_out, n, out_dtype, d_ws, ws_bytes, stream) -> int:
@@ -398,17 +411,20 @@ def empty_stream_buffer(n: int, block: int, device="cuda") -> torch.Tensor:
 
 def compress(x: torch.Tensor, eb: float, block: int = 32, mode: int = EB_ABS,
              ws: Workspace | None = None, out: torch.Tensor | None = None,
-             out_bytes: torch.Tensor | None = None, stream=None):
-    """Compress a contiguous FP32/BF16 tensor; returns (stream buffer, u64 length tensor)."""
+             out_bytes: torch.Tensor | None = None, stream=None, heads: bool = False):
+    """Compress a contiguous FP32/BF16 tensor; returns (stream buffer, u64 length
+    tensor).  heads: the heads-apart format (zc_compress_heads)."""
     x = x.contiguous()
     n = x.numel()
     ws = ws or Workspace(n, 1, x.device, stream)
-    out = out if out is not None else empty_stream_buffer(n, block, x.device)
+    if out is None:
+        cap = zc_max_compressed_bytes_heads(n, block) if heads else zc_max_compressed_bytes(n, block)
+        out = torch.empty(cap, dtype=torch.uint8, device=x.device)
     out_bytes = out_bytes if out_bytes is not None else torch.zeros(1, dtype=torch.int64,
                                                                     device=x.device)
-    _check(zc_compress(x.data_ptr(), n, dtype_code(x), mode, float(eb), block, out.data_ptr(),
-                       out.numel(), out_bytes.data_ptr(), ws.ptr, ws.nbytes, _stream(stream)),
-           "zc_compress")
+    fn, name = (zc_compress_heads, "zc_compress_heads") if heads else (zc_compress, "zc_compress")
+    _check(fn(x.data_ptr(), n, dtype_code(x), mode, float(eb), block, out.data_ptr(), out.numel(),
+              out_bytes.data_ptr(), ws.ptr, ws.nbytes, _stream(stream)), name)
     return out, out_bytes
 
 
