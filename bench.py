@@ -254,6 +254,24 @@ class Workload:
         return C, parts
 
 
+def pack_tensors(torch, ts, device):
+    """One device buffer holding every tensor of ts at 256-byte aligned offsets,
+    and views of it in place of the tensors (so a whole workload moves
+    between host and device in one copy)."""
+    offs, tot = [], 0
+    for t in ts:
+        offs.append(tot)
+        tot += (t.numel() * t.element_size() + 255) // 256 * 256
+    buf = torch.empty(max(tot, 256), dtype=torch.uint8, device=device)
+    views = []
+    for t, o in zip(ts, offs):
+        nbytes = t.numel() * t.element_size()
+        v = buf[o:o + nbytes].view(t.dtype)
+        v.copy_(t.reshape(-1))
+        views.append(v)
+    return buf, views
+
+
 class RingRow:
     """The image-stacking ring Allreduce: P rank images of 8192^2 FP32 (a
     shared base of 8 plane waves plus per-rank standardized Poisson(50) noise
@@ -266,10 +284,11 @@ class RingRow:
         self.torch, self.P = torch, P
         with torch.cuda.stream(stream):
             base = workloads.stacking_base(side=side, seed=3000, device=device)
-            self.ranks = [workloads.stacking_rank(base, r, seed=3000) for r in range(P)]
-            rng = max(float(x.max() - x.min()) for x in self.ranks)
+            ranks = [workloads.stacking_rank(base, r, seed=3000) for r in range(P)]
+            rng = max(float(x.max() - x.min()) for x in ranks)
+            self.buf, self.ranks = pack_tensors(torch, ranks, device)
         stream.synchronize()
-        del base
+        del base, ranks
         self.eb_abs = REL * rng
         self.ring = RingAllreduce(self.ranks, self.eb_abs, BLOCK, stream=stream)
         self.n = self.ranks[0].numel()
@@ -320,8 +339,10 @@ class BatchRow:
         self.M = M
         specs = workloads.message_specs(self.M)
         with torch.cuda.stream(stream):
-            self.xs = [workloads.message(sp, device=device) for sp in specs]
+            xs = [workloads.message(sp, device=device) for sp in specs]
+            self.buf, self.xs = pack_tensors(torch, xs, device)
         stream.synchronize()
+        del xs
         self.ebs = [sp["eb"] for sp in specs]
         self.raw = sum(x.numel() * x.element_size() for x in self.xs)
         self.n_f32 = sum(1 for sp in specs if sp["dtype"] == "f32")
@@ -411,6 +432,7 @@ class SelectorRow:
         torch.cuda.empty_cache()
         with torch.cuda.stream(stream):
             xs, ebs, kinds = S.mixed_messages(heldout_bytes, seed=7, device=device)
+            self.buf, xs = pack_tensors(torch, xs, device)
         stream.synchronize()
         self.xs, self.ebs = xs, ebs
         hv, he = S.split_chunks(xs, ebs)
@@ -633,6 +655,24 @@ def size_sweep(torch, zc, workloads, stream, device, max_bytes=646 << 20, reps=5
     return {"status": st, "points": out}
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value over all ranks: a replicated job's time is its
+    slowest rank's (NCCL on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gbs(step_bytes: int, world: int, ms_per_step: float) -> float:
+    """Whole-job GB/s of N replicas, each moving step_bytes per step (weak
+    scaling: the work per GPU is fixed)."""
+    return step_bytes * world / (ms_per_step * 1e-3) / 1e9
+
+
 def collectives_report(torch, workloads, stream, device, ranks_list, side, reps=2):
     """Ring vs recursive-doubling Allreduce on the image-stacking workload for
     each rank count: measured device time, the modelled per-rank time with one
@@ -739,12 +779,7 @@ def run_ours(args, rank, world):
         t1.record(W.stream)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-    total_ms = t0.elapsed_time(t1)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
     st, det = W.ws.status()
     if st != 0:
         raise RuntimeError("device status %d at %d in the timed region" % (st, det))
@@ -753,7 +788,7 @@ def run_ours(args, rank, world):
     per = {nm: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K))
            for i, nm in enumerate(names)}
     ms_per_step = total_ms / K
-    value = step_bytes * world / (ms_per_step * 1e-3) / 1e9
+    value = job_gbs(step_bytes, world, ms_per_step)
     hbm, peak_kind = peaks()
     kern_gbs = {nm: parts[nm] / (per[nm] * 1e-3) / 1e9 for nm in names}
     dom = max(names, key=lambda nm: per[nm])
@@ -804,7 +839,8 @@ def e2e_ours(torch, W, args, step_bytes, world):
     output (the field's stream, both packed batches) copied back, inside the
     timed region, all on the step's stream."""
     st = W.stream
-    dev_in = [W.field] + W.ring_row.ranks + W.batch_row.xs + W.sel_row.xs
+    # every workload lives in one buffer per row: four copies in, three out
+    dev_in = [W.field, W.ring_row.buf, W.batch_row.buf, W.sel_row.buf]
     host_in = [t.cpu().pin_memory() for t in dev_in]
     outs = [(W.cmp, W.cmp_n[0:1]), (W.batch_row.b.packed, W.batch_row.b.msg_off[-1:]),
             (W.sel_row.cb.batch.packed, W.sel_row.cb.batch.msg_off[-1:])]
