@@ -362,7 +362,7 @@ int zc_autotune_batch(int n_msgs, const zc_message* h_msgs, int tune_block, doub
  *   14    raw bits per element / 32;    15 log2(n) / 16;
  * d = q_i - q_{i-1} within a span.  A message with no elements, no bound, or
  * a sampled value the codec cannot quantize gets a row of NaN.  One kernel,
- * one CTA per message (a warp per two spans). */
+ * one warp per message. */
 int zc_batch_chunk_stats(const zc_batch* plan, float* d_feat, zc_stream_t s);
 
 /* MLP forward: y[b] = W3 relu(W2 relu(W1 x'[b] + b1) + b2) + b3 with

@@ -40,173 +40,149 @@ __device__ __forceinline__ float load_elem(const Item& it, unsigned long long i)
                                 : bf16_to_f32(__ldg((const unsigned short*)it.x + i));
 }
 
-// ---- chunk statistics: one CTA per item, one warp per two sampled spans ----------
-// Per-warp partial sums of the span statistics, combined by thread 0.
-struct SpanPart {
-    unsigned long long bits[4];  // codec block bits at L = 16, 32, 64, 128
-    unsigned long long sad, saq, sad2;
-    unsigned mad, nzd, nzq, nsc, hb;
-    int qmin, qmax, bad;
+// ---- chunk statistics: one warp per item ----------------------------------------
+// Lane-partial sums of one chunk's sampled spans.
+struct StatAcc {
+    unsigned b16 = 0, b32 = 0, b64 = 0, b128 = 0;  // codec block bits per L
+    unsigned long long sum_ad = 0, sum_aq = 0, sum_ad2 = 0;
+    unsigned max_ad = 0, nz_d = 0, nz_q = 0, n_sc = 0, head_bits = 0;
+    int qmin = 0x7fffffff, qmax = -0x7fffffff - 1;
+    int bad = 0;
 };
+
+// One span of cnt elements (lane i holds elements i, 32 + i, 64 + i, 96 + i;
+// xs already loaded): quantize, differences, block widths; returns the span's
+// L = 32 block bits (warp-uniform).
+__device__ __forceinline__ unsigned stat_span(const float xs[4], int cnt, const Item& it,
+                                              StatAcc& A)
+{
+    const int lane = threadIdx.x & 31;
+    int q[4], d[4], pd[4];
+    bool v[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = 32 * r + lane;
+        v[r] = i < cnt;
+        int qq = 0;
+        if (v[r] && quantize(xs[r], it.eb, it.two_eb, it.inv, qq) != 0) {
+            A.bad = 1;
+            qq = 0;
+        }
+        q[r] = qq;
+    }
+    // d_i = q_i - q_{i-1}, and d_{i-1} (for the second differences)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int up = __shfl_up_sync(FULL, q[r], 1);
+        const int prev_row = __shfl_sync(FULL, q[r > 0 ? r - 1 : 0], 31);
+        d[r] = q[r] - (lane ? up : (r ? prev_row : 0));
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int up = __shfl_up_sync(FULL, d[r], 1);
+        const int prev_row = __shfl_sync(FULL, d[r > 0 ? r - 1 : 0], 31);
+        pd[r] = lane ? up : (r ? prev_row : 0);
+    }
+    unsigned aq[4], ad[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = 32 * r + lane;
+        aq[r] = v[r] ? (unsigned)abs(q[r]) : 0u;
+        ad[r] = (v[r] && i >= 1) ? (unsigned)abs(d[r]) : 0u;
+        if (v[r]) {
+            A.nz_q += q[r] == 0;
+            A.sum_aq += aq[r];
+            A.qmin = min(A.qmin, q[r]);
+            A.qmax = max(A.qmax, q[r]);
+            if (i >= 1) {
+                A.sum_ad += ad[r];
+                A.max_ad = max(A.max_ad, ad[r]);
+                A.nz_d += d[r] == 0;
+            }
+            if (i >= 2) {
+                A.sum_ad2 += (unsigned)abs(d[r] - pd[r]);
+                A.n_sc += (d[r] > 0 && pd[r] < 0) || (d[r] < 0 && pd[r] > 0);
+            }
+        }
+    }
+    // the codec's block bits at every L: the block head's delta is |q|
+    unsigned sb32 = 0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        unsigned a = (lane & 15) == 0 ? aq[r] : ad[r];
+#pragma unroll
+        for (int off = 8; off; off >>= 1) a = max(a, __shfl_xor_sync(FULL, a, off));
+        if ((lane & 15) == 0 && a) A.b16 += (bitlen_u(a) + 1) * 16;
+        const unsigned m32 = __reduce_max_sync(FULL, lane == 0 ? aq[r] : ad[r]);
+        if (m32) sb32 += (bitlen_u(m32) + 1) * 32;
+        if (lane == 0 && v[r]) A.head_bits += bitlen_u(aq[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; r += 2) {
+        const unsigned m64 = __reduce_max_sync(FULL, max(lane == 0 ? aq[r] : ad[r], ad[r + 1]));
+        if (lane == 0 && m64) A.b64 += (bitlen_u(m64) + 1) * 64;
+    }
+    {
+        const unsigned a = max(max(lane == 0 ? aq[0] : ad[0], ad[1]), max(ad[2], ad[3]));
+        const unsigned m128 = __reduce_max_sync(FULL, a);
+        if (lane == 0 && m128) A.b128 += (bitlen_u(m128) + 1) * 128;
+    }
+    if (lane == 0) A.b32 += sb32;
+    return sb32;
+}
 
 __global__ void __launch_bounds__(256) k_chunk_stats(const Item* items, unsigned n_items,
                                                      float* feat)
 {
-    __shared__ SpanPart part[8];
-    __shared__ unsigned span_b32[ST_SPANS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned idx = blockIdx.x;
-    if (idx >= n_items) return;  // CTA-uniform
+    const unsigned idx = blockIdx.x * 8 + warp;
+    if (idx >= n_items) return;  // warp-uniform; only warp-level sync below
     const Item it = items[idx];
     float* out = feat + (size_t)idx * N_STATS;
     const unsigned long long n = it.n;
     if (n == 0 || it.x == nullptr || !(it.two_eb > 0.0f)) {
-        if (threadIdx.x < N_STATS) out[threadIdx.x] = __int_as_float(0x7fc00000);  // NaN row
+        if (lane < N_STATS) out[lane] = __int_as_float(0x7fc00000);  // NaN row
         return;
     }
     const unsigned long long m = n / ST_SPAN;
     const int S = m == 0 ? 1 : (int)(m < ST_SPANS ? m : ST_SPANS);
     const int cnt = m == 0 ? (int)n : ST_SPAN;  // elements of every sampled span
-    unsigned b16 = 0, b32 = 0, b64 = 0, b128 = 0;  // lane-partial block bits
-    unsigned long long sum_ad = 0, sum_aq = 0, sum_ad2 = 0;
-    unsigned max_ad = 0, nz_d = 0, nz_q = 0, n_sc = 0, head_bits = 0;
-    int qmin = 0x7fffffff, qmax = -0x7fffffff - 1;
-    int bad = 0;
-    for (int j = warp; j < S; j += 8) {
-        const unsigned long long s0 =
-            (m == 0 || S == 1) ? 0ull : (unsigned long long)ST_SPAN * (((unsigned long long)j * (m - 1)) / (S - 1));
-        int q[4], d[4], pd[4];
-        bool v[4];
+    StatAcc A;
+    unsigned span_b32[ST_SPANS];  // per-span L = 32 bits (warp-uniform; used by lane 0)
+    // two spans per step: both spans' loads are in flight together
+    for (int j = 0; j < S; j += 2) {
+        float xs[2][4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int i = 32 * r + lane;
-            v[r] = i < cnt;
-            int qq = 0;
-            if (v[r]) {
-                const float x = load_elem(it, s0 + i);
-                if (quantize(x, it.eb, it.two_eb, it.inv, qq) != 0) {
-                    bad = 1;
-                    qq = 0;
-                }
-            }
-            q[r] = qq;
-        }
-        // d_i = q_i - q_{i-1}, and d_{i-1} (for the second differences)
+        for (int h = 0; h < 2; ++h) {
+            const int jj = j + h;
+            const unsigned long long s0 =
+                (m == 0 || S == 1) ? 0ull
+                                   : (unsigned long long)ST_SPAN * (((unsigned long long)jj * (m - 1)) / (S - 1));
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int up = __shfl_up_sync(FULL, q[r], 1);
-            const int prev_row = __shfl_sync(FULL, q[r > 0 ? r - 1 : 0], 31);
-            d[r] = q[r] - (lane ? up : (r ? prev_row : 0));
-        }
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int up = __shfl_up_sync(FULL, d[r], 1);
-            const int prev_row = __shfl_sync(FULL, d[r > 0 ? r - 1 : 0], 31);
-            pd[r] = lane ? up : (r ? prev_row : 0);
-        }
-        unsigned aq[4], ad[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int i = 32 * r + lane;
-            aq[r] = v[r] ? (unsigned)abs(q[r]) : 0u;
-            ad[r] = (v[r] && i >= 1) ? (unsigned)abs(d[r]) : 0u;
-            if (v[r]) {
-                nz_q += q[r] == 0;
-                sum_aq += aq[r];
-                qmin = min(qmin, q[r]);
-                qmax = max(qmax, q[r]);
-                if (i >= 1) {
-                    sum_ad += ad[r];
-                    max_ad = max(max_ad, ad[r]);
-                    nz_d += d[r] == 0;
-                }
-                if (i >= 2) {
-                    sum_ad2 += (unsigned)abs(d[r] - pd[r]);
-                    n_sc += (d[r] > 0 && pd[r] < 0) || (d[r] < 0 && pd[r] > 0);
-                }
+            for (int r = 0; r < 4; ++r) {
+                const int i = 32 * r + lane;
+                xs[h][r] = (jj < S && i < cnt) ? load_elem(it, s0 + i) : 0.0f;
             }
         }
-        // the codec's block bits at every L: the block head's delta is |q|
-        unsigned sb32 = 0;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            unsigned a = (lane & 15) == 0 ? aq[r] : ad[r];
-#pragma unroll
-            for (int off = 8; off; off >>= 1) a = max(a, __shfl_xor_sync(FULL, a, off));
-            if ((lane & 15) == 0 && a) b16 += (bitlen_u(a) + 1) * 16;
-            const unsigned m32 = __reduce_max_sync(FULL, lane == 0 ? aq[r] : ad[r]);
-            if (m32) sb32 += (bitlen_u(m32) + 1) * 32;
-            if (lane == 0 && v[r]) head_bits += bitlen_u(aq[r]);
-        }
-#pragma unroll
-        for (int r = 0; r < 4; r += 2) {
-            const unsigned m64 = __reduce_max_sync(FULL, max(lane == 0 ? aq[r] : ad[r], ad[r + 1]));
-            if (lane == 0 && m64) b64 += (bitlen_u(m64) + 1) * 64;
-        }
-        {
-            const unsigned a = max(max(lane == 0 ? aq[0] : ad[0], ad[1]), max(ad[2], ad[3]));
-            const unsigned m128 = __reduce_max_sync(FULL, a);
-            if (lane == 0 && m128) b128 += (bitlen_u(m128) + 1) * 128;
-        }
-        if (lane == 0) {
-            b32 += sb32;
-            span_b32[j] = sb32;
-        }
+        for (int h = 0; h < 2; ++h)
+            if (j + h < S) span_b32[j + h] = stat_span(xs[h], cnt, it, A);
     }
-    {
-        const unsigned long long B16 = warp_sum_u64(b16), B32 = warp_sum_u64(b32);
-        const unsigned long long B64 = warp_sum_u64(b64), B128 = warp_sum_u64(b128);
-        const unsigned long long SAD = warp_sum_u64(sum_ad), SAQ = warp_sum_u64(sum_aq);
-        const unsigned long long SAD2 = warp_sum_u64(sum_ad2);
-        const unsigned long long NZD = warp_sum_u64(nz_d), NZQ = warp_sum_u64(nz_q);
-        const unsigned long long NSC = warp_sum_u64(n_sc), HB = warp_sum_u64(head_bits);
-        const unsigned MAD = __reduce_max_sync(FULL, max_ad);
-        const int QMN = __reduce_min_sync(FULL, qmin), QMX = __reduce_max_sync(FULL, qmax);
-        const int BAD = __any_sync(FULL, bad);
-        if (lane == 0) {
-            SpanPart& P = part[warp];
-            P.bits[0] = B16;
-            P.bits[1] = B32;
-            P.bits[2] = B64;
-            P.bits[3] = B128;
-            P.sad = SAD;
-            P.saq = SAQ;
-            P.sad2 = SAD2;
-            P.mad = MAD;
-            P.nzd = (unsigned)NZD;
-            P.nzq = (unsigned)NZQ;
-            P.nsc = (unsigned)NSC;
-            P.hb = (unsigned)HB;
-            P.qmin = QMN;
-            P.qmax = QMX;
-            P.bad = BAD;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    unsigned long long bits[4] = {0, 0, 0, 0}, SAD = 0, SAQ = 0, SAD2 = 0, NZD = 0, NZQ = 0,
-                       NSC = 0, HB = 0;
-    unsigned MAD = 0;
-    int QMN = 0x7fffffff, QMX = -0x7fffffff - 1, BAD = 0;
-    for (int w = 0; w < 8; ++w) {
-        const SpanPart& P = part[w];
-        for (int k = 0; k < 4; ++k) bits[k] += P.bits[k];
-        SAD += P.sad;
-        SAQ += P.saq;
-        SAD2 += P.sad2;
-        NZD += P.nzd;
-        NZQ += P.nzq;
-        NSC += P.nsc;
-        HB += P.hb;
-        MAD = max(MAD, P.mad);
-        QMN = min(QMN, P.qmin);
-        QMX = max(QMX, P.qmax);
-        BAD |= P.bad;
-    }
+    const unsigned long long B16 = warp_sum_u64(A.b16), B32 = warp_sum_u64(A.b32);
+    const unsigned long long B64 = warp_sum_u64(A.b64), B128 = warp_sum_u64(A.b128);
+    const unsigned long long SAD = warp_sum_u64(A.sum_ad), SAQ = warp_sum_u64(A.sum_aq);
+    const unsigned long long SAD2 = warp_sum_u64(A.sum_ad2);
+    const unsigned long long NZD = warp_sum_u64(A.nz_d), NZQ = warp_sum_u64(A.nz_q);
+    const unsigned long long NSC = warp_sum_u64(A.n_sc), HB = warp_sum_u64(A.head_bits);
+    const unsigned MAD = __reduce_max_sync(FULL, A.max_ad);
+    const int QMN = __reduce_min_sync(FULL, A.qmin), QMX = __reduce_max_sync(FULL, A.qmax);
+    const int BAD = __any_sync(FULL, A.bad);
+    if (lane != 0) return;
     if (BAD) {
         for (int k = 0; k < N_STATS; ++k) out[k] = __int_as_float(0x7fc00000);
         return;
     }
+    const unsigned long long bits[4] = {B16, B32, B64, B128};
     // The features in FP32 (this GPU's FP64 rate is a small fraction of its
     // FP32 rate): counts are exact integers below 2^24, each quotient is one
     // correctly rounded division, each logarithm CUDA's log2f.
@@ -539,7 +515,7 @@ int zc_batch_chunk_stats(const zc_batch* plan, float* d_feat, zc_stream_t s)
         d_feat == nullptr || (reinterpret_cast<uintptr_t>(d_feat) & 3) != 0)
         return ZC_ERR_ARG;
     const unsigned n = (unsigned)plan->n_msgs;
-    k_chunk_stats<<<n, 256, 0, (cudaStream_t)s>>>((const Item*)plan->d_table, n, d_feat);
+    k_chunk_stats<<<(n + 7) / 8, 256, 0, (cudaStream_t)s>>>((const Item*)plan->d_table, n, d_feat);
     return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
 }
 
