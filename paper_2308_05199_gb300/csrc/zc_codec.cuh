@@ -278,6 +278,16 @@ __device__ __forceinline__ unsigned long long unit_meta(const Launch& P, const I
         }
     }
     __syncwarp();
+    // the whole unit payload is requested into L2 at once (one bulk prefetch,
+    // 16-byte aligned inner range); the per-group plane loads then hit L2
+    if (ok && lane == 0 && tot > 0) {
+        const uintptr_t a0 = (uintptr_t)(it.cin + base), a1 = a0 + (uintptr_t)tot;
+        const uintptr_t s0 = (a0 + 15) & ~(uintptr_t)15, s1 = a1 & ~(uintptr_t)15;
+        if (s1 > s0)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s0),
+                         "r"((unsigned)(s1 - s0))
+                         : "memory");
+    }
     return ok ? base : 0ull;
 }
 
