@@ -64,8 +64,24 @@ int qparams(double eb_abs, float* eb, float* two, float* inv)
 // Workspace: control block, range partials, then 9 arrays of `cap` u64:
 // decode-tile offsets, encoder look-back (flag, wide aggregate, prefix),
 // width-scan look-back (same three), per-item stream-start flags, and the
-// tile-to-item map of multi-item encoder launches (u32 entries).
+// tile-to-item map of multi-item encoder launches (u32 entries); then the
+// encoder CTAs' tile rings: ring_ctas(cap) rings of the largest tile size.
 constexpr uint64_t WS_ARRAYS = 9;
+constexpr uint64_t RING_CTAS_MAX = 152 * ENC_CTAS_PER_SM;  // every resident encoder CTA
+constexpr uint64_t RING_UNIT = ring_cta_bytes(unit_rows(16));
+
+// Rings for a workspace of `cap` array entries: one per 32 entries (a tile
+// of 16 chunks needs 32 entries of decode slots), at least one.
+inline uint64_t ring_ctas(uint64_t cap)
+{
+    const uint64_t r = (cap + 31) / 32;
+    return r < 1 ? 1 : (r > RING_CTAS_MAX ? RING_CTAS_MAX : r);
+}
+inline uint64_t ring_offset(uint64_t cap)
+{
+    return (WS_CTL_BYTES + WS_RANGE_BYTES + cap * WS_ARRAYS * 8 + 255) & ~(uint64_t)255;
+}
+inline uint64_t ws_total(uint64_t cap) { return ring_offset(cap) + ring_ctas(cap) * RING_UNIT; }
 
 struct WsView {
     Ctl* ctl;
@@ -75,14 +91,15 @@ struct WsView {
     unsigned long long* seg_flag;
     unsigned* tile_map;
     uint64_t cap;  // decode tiles (and tiles, chunks, items) the workspace can hold
+    uint8_t* ring;
+    uint64_t ring_bytes;
+    uint64_t ring_off;
 };
 
-int ws_view(void* ws, size_t bytes, WsView& v)
+// The arrays at `ws` with `cap` entries, the rings given apart.
+void ws_carve(void* ws, uint64_t cap, uint8_t* ring, uint64_t ring_bytes, WsView& v)
 {
-    if (ws == nullptr || !aligned(ws, 16)) return ZC_ERR_ARG;
     const uint64_t fixed = WS_CTL_BYTES + WS_RANGE_BYTES;
-    if (bytes < fixed + WS_ARRAYS * 8 * 4) return ZC_ERR_WORKSPACE;
-    const uint64_t cap = (bytes - fixed) / (WS_ARRAYS * 8);
     unsigned long long* base = (unsigned long long*)((char*)ws + fixed);
     v.ctl = (Ctl*)ws;
     v.partial = (float2*)((char*)ws + WS_CTL_BYTES);
@@ -92,7 +109,46 @@ int ws_view(void* ws, size_t bytes, WsView& v)
     v.seg_flag = base + 7 * cap;
     v.tile_map = (unsigned*)(base + 8 * cap);
     v.cap = cap;
+    v.ring = ring;
+    v.ring_bytes = ring_bytes;
+    v.ring_off = ring_offset(cap);
+}
+
+// The layout of a workspace of `bytes`: the largest cap whose arrays and
+// rings fit (ws_total grows with cap, so a bisection finds it).
+int ws_view(void* ws, size_t bytes, WsView& v)
+{
+    if (ws == nullptr || !aligned(ws, 16)) return ZC_ERR_ARG;
+    if (bytes < ws_total(4)) return ZC_ERR_WORKSPACE;
+    uint64_t lo = 4, hi = bytes / (WS_ARRAYS * 8) + 1;  // ws_total(lo) <= bytes < ws_total(hi)
+    while (hi - lo > 1) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (ws_total(mid) <= bytes) lo = mid;
+        else hi = mid;
+    }
+    ws_carve(ws, lo, (uint8_t*)ws + ring_offset(lo), ring_ctas(lo) * RING_UNIT, v);
     return ZC_OK;
+}
+
+// Encoder CTAs for a launch that wants `want` (its tile count or a chosen
+// grid): at most one per ring and the resident CTAs of this GPU.
+uint64_t enc_grid(uint64_t want, int U, const WsView& w)
+{
+    static int sms[64];
+    int dev = 0;
+    int n_sm = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+        if (sms[dev] == 0 &&
+            cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms[dev] = 0;
+        if (sms[dev] > 0) n_sm = sms[dev];
+    }
+    uint64_t g = want;
+    const uint64_t rings = w.ring_bytes / ring_cta_bytes(U);
+    const uint64_t resident = (uint64_t)n_sm * ENC_CTAS_PER_SM;
+    if (g > rings) g = rings;
+    if (g > resident) g = resident;
+    return g;
 }
 
 Launch base_launch(const WsView& w)
@@ -105,6 +161,8 @@ Launch base_launch(const WsView& w)
     P.offs = w.offs;
     P.seg_flag = w.seg_flag;
     P.urows = DEC_U;
+    P.ring = w.ring;
+    P.ring_bytes = w.ring_bytes;
     P.wc.limit_ns = g_wait_ns;
     P.wc.withhold = g_withhold;
     return P;
@@ -190,8 +248,7 @@ size_t zc_workspace_bytes(uint64_t n_total, int n_items)
     // decode slots: one per warp unit of at least 32 rows (1024 elements),
     // plus the partial tiles of every item
     const uint64_t cap = n_total / 1024 + 16ull * (uint64_t)n_items + 2;
-    const uint64_t b = WS_CTL_BYTES + WS_RANGE_BYTES + cap * WS_ARRAYS * 8;
-    return (b + 255) & ~(uint64_t)255;
+    return ws_total(cap);
 }
 
 int zc_workspace_init(void* d_ws, size_t ws_bytes, zc_stream_t s)
@@ -199,7 +256,8 @@ int zc_workspace_init(void* d_ws, size_t ws_bytes, zc_stream_t s)
     WsView w;
     int st = ws_view(d_ws, ws_bytes, w);
     if (st) return st;
-    if (cudaMemsetAsync(d_ws, 0, ws_bytes, (cudaStream_t)s) != cudaSuccess) return ZC_ERR_CUDA;
+    // the rings need no initial contents
+    if (cudaMemsetAsync(d_ws, 0, w.ring_off, (cudaStream_t)s) != cudaSuccess) return ZC_ERR_CUDA;
     return cuda_status(launch_ws_init(w.ctl, (cudaStream_t)s));
 }
 
@@ -286,9 +344,14 @@ int compress_impl(const void* d_in, uint64_t n, int dtype, int eb_mode, double e
     P.n_items = 1;
     P.total_tiles = (unsigned)tiles;
     P.urows = unit_rows(C);
-    if (heads)
-        return cuda_status(launch_compress_heads_any(lg, dtype, P, (unsigned)tiles, (cudaStream_t)s));
-    return cuda_status(launch_compress_any(lg, C, dtype, P, (unsigned)tiles, (cudaStream_t)s));
+    if (heads) {
+        const uint64_t grid = enc_grid(tiles, unit_rows(8), w);
+        if (grid == 0) return ZC_ERR_WORKSPACE;
+        return cuda_status(launch_compress_heads_any(lg, dtype, P, (unsigned)grid, (cudaStream_t)s));
+    }
+    const uint64_t grid = enc_grid(tiles, unit_rows(C), w);
+    if (grid == 0) return ZC_ERR_WORKSPACE;
+    return cuda_status(launch_compress_any(lg, C, dtype, P, (unsigned)grid, (cudaStream_t)s));
 }
 
 }  // namespace
@@ -392,7 +455,9 @@ int zc_reduce_step(const void* d_cmp_in, size_t cmp_in_cap, const float* d_local
         if (launch_wscan(P, (unsigned)chunks, (cudaStream_t)s) != cudaSuccess) return ZC_ERR_CUDA;
     }
     P.total_tiles = (unsigned)tiles;
-    return cuda_status(launch_reduce_any(lg, C, P, (unsigned)tiles, (cudaStream_t)s));
+    const uint64_t grid = enc_grid(tiles, unit_rows(C), w);
+    if (grid == 0) return ZC_ERR_WORKSPACE;
+    return cuda_status(launch_reduce_any(lg, C, P, (unsigned)grid, (cudaStream_t)s));
 }
 
 size_t zc_plan_table_bytes(int n_items)
@@ -487,7 +552,9 @@ int zc_reduce_step_batch(const zc_plan* plan, void* d_ws, size_t ws_bytes, zc_st
             return ZC_ERR_CUDA;
         P.tile_map = w.tile_map;
     }
-    return cuda_status(launch_reduce_any(lg, C, P, (unsigned)plan->total_tiles, (cudaStream_t)s));
+    const uint64_t grid = enc_grid(plan->total_tiles, unit_rows(C), w);
+    if (grid == 0) return ZC_ERR_WORKSPACE;
+    return cuda_status(launch_reduce_any(lg, C, P, (unsigned)grid, (cudaStream_t)s));
 }
 
 int zc_scatter_pack(const void* d_in, int dtype, int P, const uint64_t* h_counts,
@@ -555,7 +622,9 @@ int zc_scatter_pack(const void* d_in, int dtype, int P, const uint64_t* h_counts
     L.n_items = (unsigned)P;
     L.total_tiles = (unsigned)tile;
     L.urows = unit_rows(C);
-    return cuda_status(launch_scatter_any(lg, C, dtype, L, SP, (unsigned)tile, (cudaStream_t)s));
+    const uint64_t grid = enc_grid(tile, unit_rows(C), w);
+    if (grid == 0) return ZC_ERR_WORKSPACE;
+    return cuda_status(launch_scatter_any(lg, C, dtype, L, SP, (unsigned)grid, (cudaStream_t)s));
 }
 
 size_t zc_batch_table_bytes(int n_msgs)
@@ -654,6 +723,8 @@ int zc_compress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_stre
     P.total_tiles = (unsigned)plan->total_tiles;
     uint64_t grid = plan->grid > 0 ? (uint64_t)plan->grid : plan->total_tiles;
     if (grid > plan->total_tiles) grid = plan->total_tiles;
+    grid = enc_grid(grid, unit_rows(C), w);
+    if (grid == 0) return ZC_ERR_WORKSPACE;
     if (plan->n_msgs > 1) {
         if (launch_tile_map(P.items, P.n_items, P.total_tiles, w.tile_map, (cudaStream_t)s) !=
             cudaSuccess)

@@ -28,6 +28,8 @@
 // 256-tile chunks); decoding then needs no look-back and no barrier.
 #pragma once
 
+#include <type_traits>
+
 #include "zc_device.cuh"
 
 namespace zc {
@@ -77,6 +79,9 @@ struct Launch {
     // item of every tile (written by k_tile_map before the launch), or null:
     // then the item is found by a binary search over tile_begin
     const unsigned* tile_map;
+    // encoder launches: the CTAs' tile rings (ring_cta_bytes each, in CTA order)
+    uint8_t* ring;
+    unsigned long long ring_bytes;
 };
 
 struct Smem {
@@ -87,12 +92,22 @@ struct Smem {
     float eb, two_eb, inv;
 };
 
-// Dynamic shared memory of an encoder CTA with U-row warp units: every warp's
-// payload segment and width bytes.
-__host__ __device__ constexpr int enc_smem_bytes(int U)
+// Encoder CTAs: NWARPS encoder warps plus one resolver warp, ENC_SLOTS tiles
+// in flight.  Every tile slot has, per encoder warp, a payload segment of
+// seg_bytes(U) in the CTA's ring (global memory) and U * 2 width bytes in
+// shared memory.
+constexpr int ENC_SLOTS = 3;
+constexpr int ENC_THREADS = NTHREADS + 32;
+constexpr int ENC_CTAS_PER_SM = 4;            // resident encoder CTAs per SM (registers)
+constexpr unsigned BAR_ENCW = 1;              // named barrier: the encoder warps
+constexpr unsigned BAR_ENC = 2;               // + slot: tile encoded (resolver waits)
+constexpr unsigned BAR_RES = BAR_ENC + ENC_SLOTS;  // + slot: tile resolved (encoders wait)
+static_assert(BAR_RES + ENC_SLOTS <= 16, "named barriers per CTA");
+__host__ __device__ constexpr unsigned long long ring_cta_bytes(int U)
 {
-    return NWARPS * (seg_bytes(U) + U * 2);
+    return (unsigned long long)ENC_SLOTS * NWARPS * seg_bytes(U);
 }
+__host__ __device__ constexpr int enc_smem_bytes(int U) { return ENC_SLOTS * NWARPS * U * 2; }
 
 template <typename T>
 __device__ __forceinline__ float load_x(const T* p, int i);
@@ -619,95 +634,139 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
     return lo;
 }
 
-// Copies `len` bytes (a multiple of UNIT, both ends UNIT-aligned) from shared
-// to global memory with one warp.
+// ---- encoder tiles -------------------------------------------------------------
+// An encoder CTA runs two kinds of warps.  Its NWARPS encoder warps take tiles
+// in ticket order and encode each of the tile's warp units into the CTA's ring
+// (global memory, ENC_SLOTS tiles deep) and its width bytes into shared
+// memory.  Its resolver warp takes every encoded tile, sums the units' sizes,
+// runs the tile's look-back (and, for packed streams, the stream-start wait)
+// and hands the tile's place in the output back.  ENC_SLOTS - 1 tiles later
+// the encoder warps copy the tile from the ring to the stream.  So the encoder
+// warps never stop for a look-back: the wait for the tiles before this one
+// overlaps the encoding of the tiles after it.
+
+// Copies `len` bytes (a multiple of UNIT) from the ring (16-byte aligned) to
+// `dst` (UNIT-aligned) with one warp; four loads per lane are in flight.
 template <int UNIT>
-__device__ __forceinline__ void warp_copy(uint8_t* dst, const uint8_t* src, int len)
+__device__ __forceinline__ void ring_copy(uint8_t* dst, const uint8_t* src, int len)
 {
     const int lane = threadIdx.x & 31;
-    if (UNIT == 16) {
-        for (int i = lane; i < len / 16; i += 32) ((uint4*)dst)[i] = ((const uint4*)src)[i];
-    } else if (UNIT == 8) {
-        for (int i = lane; i < len / 8; i += 32) ((uint2*)dst)[i] = ((const uint2*)src)[i];
-    } else if (UNIT == 4) {
-        for (int i = lane; i < len / 4; i += 32) ((uint32_t*)dst)[i] = ((const uint32_t*)src)[i];
-    } else {
-        for (int i = lane; i < len / 2; i += 32) ((uint16_t*)dst)[i] = ((const uint16_t*)src)[i];
+    using T = typename std::conditional<
+        UNIT == 16, uint4,
+        typename std::conditional<UNIT == 8, uint2,
+                                  typename std::conditional<UNIT == 4, unsigned,
+                                                            unsigned short>::type>::type>::type;
+    const int cnt = len / UNIT;
+    for (int b = 0; b < cnt; b += 32 * 4) {
+        T v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = b + k * 32 + lane;
+            if (i < cnt) v[k] = __ldcg((const T*)src + i);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = b + k * 32 + lane;
+            if (i < cnt) ((T*)dst)[i] = v[k];
+        }
     }
 }
 
 // Packed mode (one chain through many streams): the first tile of a stream
 // publishes where the stream starts (its exclusive value ex), the stream's
 // other tiles wait for that.  Outside packed mode a stream starts at 0.
-// Returns false (status set) when the wait runs out.  Run by the whole CTA.
-__device__ __forceinline__ bool packed_start(const Launch& P, bool first, unsigned item_idx,
-                                             unsigned long long ex, unsigned g, Smem& sm,
-                                             unsigned long long& start)
+// Returns false (status set) when the wait runs out.  Run by one warp.
+__device__ __forceinline__ bool packed_start_warp(const Launch& P, bool first, unsigned item_idx,
+                                                  unsigned long long ex, unsigned g, unsigned E,
+                                                  unsigned long long& start)
 {
+    const int lane = threadIdx.x & 31;
     start = 0ull;
     if (!P.packed) return true;
     if (first) {
         start = ex;
-        if (threadIdx.x == 0) {
+        if (lane == 0) {
             st_relaxed(P.seg_off + item_idx, ex);
-            st_release(P.seg_flag + item_idx, ((unsigned long long)sm.E << 32) | 1ull);
+            st_release(P.seg_flag + item_idx, ((unsigned long long)E << 32) | 1ull);
         }
         return true;
     }
-    if (threadIdx.x == 0) {
-        sm.abort = !wait_flag(P.seg_flag + item_idx, sm.E, P.wc.limit_ns);
-        if (sm.abort) fail(P.ctl, ZC_ERR_TIMEOUT, g);
-        else sm.start = ld_relaxed(P.seg_off + item_idx);
+    int ok = 1;
+    unsigned long long v = 0ull;
+    if (lane == 0) {
+        ok = wait_flag(P.seg_flag + item_idx, E, P.wc.limit_ns);
+        if (!ok) fail(P.ctl, ZC_ERR_TIMEOUT, g);
+        else v = ld_relaxed(P.seg_off + item_idx);
     }
-    __syncthreads();
-    if (sm.abort) return false;
-    start = sm.start;
-    return true;
+    ok = __shfl_sync(FULL, ok, 0);
+    start = __shfl_sync(FULL, v, 0);
+    return ok != 0;
 }
 
-// One encoder tile: NWARPS warp units of U rows, each warp encoding its unit
-// into its own shared-memory segment.  HAS_CIN: decode `it.cin` first (same
-// block size, unit offsets from k_wscan) and add the local chunk.  The FP32
-// sum goes to `it.raw_out` when that is set.  Null pointers switch a step off.
+// One tile in flight.  The encoder warps fill it (thread 0 the scalars, lane
+// 0 of every warp its unit's size), the resolver warp adds ex, start and ok.
+struct TileSlot {
+    unsigned g, item, tile;       // ticket, item, tile within the item
+    int valid;                    // g is a tile of this launch
+    int pub;                      // the tile takes part in the chain
+    int first, last;              // first / last tile of its stream
+    unsigned long long head;      // bytes of the tile besides its units' payload
+    int segsz[NWARPS];            // payload bytes of every warp unit
+    unsigned long long ex, start; // place in the chain, start of its stream
+    int ok;                       // ex and start are usable: store the tile
+};
+
+struct EncShared {
+    unsigned E;    // launch generation
+    int abort;     // 1: unusable workspace (the CTA does nothing), 2: no usable bound
+    int hdr_bad;   // fused ring step: the tile's input stream failed its check
+    float eb_in;   // its bound
+};
+
+// Encoder warp `warp`'s unit of one tile: quantize, delta-code and bit-plane
+// pack its U rows into its ring segment `seg` and width bytes `wb`; returns
+// the segment's size.  HAS_CIN: decode `it.cin` first (same block size, unit
+// offsets from k_wscan) and add the local chunk; the FP32 sum then goes to
+// `it.raw_out` when that is set.  Null pointers switch a step off.  HEADS
+// (block heads stored apart, single unpacked streams) writes the heads
+// straight to their fixed place in the output.  Thread 0 fills the slot's
+// scalars.
 template <int LOG2L, int U, bool HAS_CIN, typename TX, bool HEADS = false>
-__device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, unsigned item_idx,
-                                            unsigned tile_in_item, unsigned g, Smem& sm,
-                                            uint8_t* dsm)
+__device__ __forceinline__ int enc_tile(const Launch& P, const Item& it, unsigned item_idx,
+                                        unsigned tile_in_item, uint8_t* seg, uint8_t* wb,
+                                        TileSlot& S, EncShared& es)
 {
-    // HEADS (block heads stored apart) is for single, unpacked streams: the
-    // heads are written straight to their fixed place in the output.
     static_assert(!HEADS || !HAS_CIN, "heads apart: compression only");
     constexpr int L = 1 << LOG2L;
-    constexpr int PB = L / 8;
     constexpr int BU = U * 32 / L;  // blocks per warp unit
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     Ctl* ctl = P.ctl;
-    const unsigned E = sm.E;
     const unsigned long long n = it.n;
-    const unsigned long long te0 = (unsigned long long)tile_in_item * (NWARPS * U * 32);
-    const unsigned long long ue0 = te0 + (unsigned long long)warp * U * 32;
+    const unsigned long long ue0 = (unsigned long long)tile_in_item * (NWARPS * U * 32) +
+                                   (unsigned long long)warp * U * 32;
     const unsigned long long nb = (n + L - 1) >> LOG2L;
     const unsigned long long wbytes = ceil16(nb);
-    const unsigned long long hbytes = HEADS ? ceil16(3ull * nb) : 0ull;
     const bool first = tile_in_item == 0;
-    const bool last = tile_in_item + 1 == it.ntiles;
     const bool do_cin = HAS_CIN && it.cin != nullptr;
     const bool do_enc = it.out != nullptr;
-    uint8_t* const seg = dsm + warp * seg_bytes(U);                   // this warp's payload
-    uint8_t* const wb = dsm + NWARPS * seg_bytes(U) + warp * (U * 2);  // its width bytes
-    __shared__ int segsz[NWARPS];
-
+    if (tid == 0) {
+        S.first = first;
+        S.last = tile_in_item + 1 == it.ntiles;
+        S.head = first ? 32ull + wbytes + (HEADS ? ceil16(3ull * nb) : 0ull) : 0ull;
+        S.pub = do_enc;
+    }
     float two_eb_in = 0.0f;
     if (do_cin) {
         if (tid == 0) {
             float eb_in;
-            const int lg = check_header(it, ctl, item_idx, LOG2L, eb_in, tile_in_item == 0);
-            sm.abort = lg != LOG2L;
-            sm.eb = eb_in;
+            const int lg = check_header(it, ctl, item_idx, LOG2L, eb_in, first);
+            es.hdr_bad = lg != LOG2L;
+            es.eb_in = eb_in;
+            if (es.hdr_bad) S.pub = 0;
         }
-        __syncthreads();
-        if (sm.abort) return;
-        two_eb_in = __fadd_rn(sm.eb, sm.eb);
+        bar_sync_n(BAR_ENCW, NTHREADS);
+        if (es.hdr_bad) return 0;
+        two_eb_in = __fadd_rn(es.eb_in, es.eb_in);
     }
     float eb = it.eb, two_eb = it.two_eb, inv = it.inv;
     if (P.eb_from_ctl) {
@@ -716,7 +775,6 @@ __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, uns
         inv = ctl->inv;
     }
 
-    // ---- 1. this warp's unit: decode / add / raw store / encode ----------------
     const TpC tc = tp_consts(lane);
     int err = 0;
     int lo = 0;
@@ -727,7 +785,8 @@ __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, uns
         if constexpr (HAS_CIN) {
             __shared__ __align__(16) int2 meta_all[NWARPS][BU];
             meta = meta_all[warp];
-            if (do_cin) src = it.cin + unit_meta<LOG2L, U>(P, it, g * NWARPS + warp, ue0, meta, narrow);
+            if (do_cin)
+                src = it.cin + unit_meta<LOG2L, U>(P, it, S.g * NWARPS + warp, ue0, meta, narrow);
         }
         // the next group's input is loaded while the current one is encoded
         float xn[GR];
@@ -747,11 +806,17 @@ __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, uns
 #pragma unroll
             for (int r = 0; r < GR; ++r) acc[r] = xn[r];
             if (gi + 1 < U / GR && e0 + GR * 32 < n) {
-                const int nrem1 = (int)min(n - e0 - GR * 32, (unsigned long long)(GR * 32));
                 const TX* xp = xbase + (gi + 1) * GR * 32;
+                if (xbase != nullptr && e0 + 2 * GR * 32 <= n) {
 #pragma unroll
-                for (int r = 0; r < GR; ++r)
-                    xn[r] = (xbase != nullptr && r * 32 + lane < nrem1) ? load_x<TX>(xp, r * 32) : 0.0f;
+                    for (int r = 0; r < GR; ++r) xn[r] = load_x<TX>(xp, r * 32);
+                } else {
+                    const int nrem1 = (int)min(n - e0 - GR * 32, (unsigned long long)(GR * 32));
+#pragma unroll
+                    for (int r = 0; r < GR; ++r)
+                        xn[r] = (xbase != nullptr && r * 32 + lane < nrem1) ? load_x<TX>(xp, r * 32)
+                                                                             : 0.0f;
+                }
             }
             if constexpr (HAS_CIN) {
                 if (do_cin) {
@@ -762,7 +827,7 @@ __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, uns
                     for (int r = 0; r < GR; ++r) acc[r] = __fadd_rn(dv[r], acc[r]);
                 }
             }
-            if (it.raw_out != nullptr) {
+            if (HAS_CIN && it.raw_out != nullptr) {
                 float* op = (float*)it.raw_out + e0 + lane;
                 const bool check = do_cin && !do_enc;
 #pragma unroll
@@ -790,34 +855,44 @@ __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, uns
         const unsigned bad = __ballot_sync(FULL, err != 0);
         if (bad && lane == __ffs(bad) - 1) fail(ctl, (unsigned)err, ue0);
     }
-    if (!do_enc) return;
-    if (lane == 0) segsz[warp] = lo;
-    __syncthreads();
+    return do_enc ? lo : 0;
+}
 
-    // ---- 2. segment offsets, tile position (look-back), stream start ---------
+// Stores of one encoded tile once its place is known: every encoder warp
+// copies its unit's segment from the ring and its width bytes; the last tile
+// of a stream zero-pads the width array (and the heads) and the payload and
+// writes the header.
+template <int LOG2L, int U, bool HAS_CIN, bool HEADS = false>
+__device__ __forceinline__ void fin_tile(const Launch& P, const Item& it, unsigned item_idx,
+                                         unsigned tile_in_item, unsigned g, const TileSlot& S,
+                                         const uint8_t* seg, const uint8_t* wb)
+{
+    constexpr int L = 1 << LOG2L;
+    constexpr int PB = L / 8;
+    constexpr int BU = U * 32 / L;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned long long n = it.n;
+    const unsigned long long ue0 = (unsigned long long)tile_in_item * (NWARPS * U * 32) +
+                                   (unsigned long long)warp * U * 32;
+    const unsigned long long nb = (n + L - 1) >> LOG2L;
+    const unsigned long long wbytes = ceil16(nb);
+    const unsigned long long hbytes = HEADS ? ceil16(3ull * nb) : 0ull;
     int segoff = 0, payload_i = 0;
 #pragma unroll
     for (int w = 0; w < NWARPS; ++w) {
-        if (w < warp) segoff += segsz[w];
-        payload_i += segsz[w];
+        if (w < warp) segoff += S.segsz[w];
+        payload_i += S.segsz[w];
     }
     const unsigned long long payload = (unsigned long long)payload_i;
-    const unsigned long long agg = payload + (first ? 32ull + wbytes + hbytes : 0ull);
-    const unsigned g0 = P.packed ? 0u : g - tile_in_item;
-    bool to = false;
-    const unsigned long long ex = lookback_cta(P.chB, g, g0, agg, last, E, P.wc, ctl, to, sm.lb);
-    unsigned long long start = 0ull;
-    if (to || !packed_start(P, first, item_idx, ex, g, sm, start)) return;
-    const unsigned long long base = ex + (first ? 32ull + wbytes + hbytes : 0ull);
+    const unsigned long long ex = S.ex, start = S.start;
+    const unsigned long long base = ex + S.head;
     const unsigned long long cap = it.out_cap;
     uint8_t* const out = it.out;
-    const unsigned long long end = ex + agg;  // unpadded end of this tile's payload
-
-    // ---- 3. stores: each warp copies its segment and its width bytes -------------
+    const unsigned long long end = base + payload;  // unpadded end of this tile's payload
     if (base + payload <= cap) {
-        warp_copy<PB>(out + base + segoff, seg, lo);
+        ring_copy<PB>(out + base + segoff, seg, S.segsz[warp]);
     } else if (tid == 0) {
-        fail(ctl, ZC_ERR_CAPACITY, g);
+        fail(P.ctl, ZC_ERR_CAPACITY, g);
     }
     {
         const unsigned long long b0 = ue0 >> LOG2L;
@@ -827,7 +902,7 @@ __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, uns
             if (b < nb && pos < cap) out[pos] = wb[i];
         }
     }
-    if (last) {
+    if (S.last) {
         const unsigned long long total = ceil16(end);
         const unsigned long long pl = end - start - 32 - wbytes - hbytes;
         for (unsigned long long p = start + 32 + nb + tid; p < start + 32 + wbytes; p += NTHREADS)
@@ -846,8 +921,87 @@ __device__ __forceinline__ void tile_encode(const Launch& P, const Item& it, uns
             case 1: v = (uint32_t)xdt | ((uint32_t)LOG2L << 8) | (HEADS ? (2u << 16) : 0u); break;
             case 2: v = (uint32_t)n; break;
             case 3: v = (uint32_t)(n >> 32); break;
-            case 4: v = __float_as_uint(eb); break;
+            case 4: v = __float_as_uint(P.eb_from_ctl ? P.ctl->eb : it.eb); break;
             case 5: v = (uint32_t)nb; break;
+            case 6: v = (uint32_t)pl; break;
+            default: v = (uint32_t)(pl >> 32); break;
+            }
+            ((uint32_t*)(out + start))[tid] = v;
+        }
+        if (tid == 0) {
+            if (it.out_bytes) *it.out_bytes = total - start;
+            if (P.packed) P.seg_off[item_idx + 1] = total;
+        }
+    }
+}
+
+// One tile of a raw (verbatim) stream: the item's elements of this tile go
+// unchanged after the 32-byte header (flag bit 0 set, no width bytes).  Same
+// tile geometry, look-back and stream-start protocol as an encoded tile, so
+// raw and encoded streams mix in one packed launch.  Nothing is staged: the
+// tile's size is known from its element count.
+template <int U>
+__device__ __forceinline__ int enc_raw(const Item& it, unsigned tile_in_item, TileSlot& S)
+{
+    if (threadIdx.x == 0) {
+        constexpr unsigned long long TE = (unsigned long long)NWARPS * U * 32;
+        const unsigned long long es = it.x_dtype == ZC_F32 ? 4ull : 2ull;
+        const unsigned long long te0 = (unsigned long long)tile_in_item * TE;
+        const unsigned long long cnt = te0 < it.n ? min(it.n - te0, TE) : 0ull;
+        S.first = tile_in_item == 0;
+        S.last = tile_in_item + 1 == it.ntiles;
+        S.head = cnt * es + (tile_in_item == 0 ? 32ull : 0ull);
+        S.pub = it.out != nullptr;
+    }
+    return 0;
+}
+
+template <int U>
+__device__ __forceinline__ void fin_raw(const Launch& P, const Item& it, unsigned item_idx,
+                                        unsigned tile_in_item, unsigned g, const TileSlot& S)
+{
+    constexpr unsigned long long TE = (unsigned long long)NWARPS * U * 32;
+    const int tid = threadIdx.x;
+    const unsigned long long n = it.n;
+    const unsigned long long es = it.x_dtype == ZC_F32 ? 4ull : 2ull;
+    const unsigned long long te0 = (unsigned long long)tile_in_item * TE;
+    const unsigned long long cnt = te0 < n ? min(n - te0, TE) : 0ull;
+    const unsigned long long bytes = cnt * es;
+    const unsigned long long ex = S.ex, start = S.start;
+    const unsigned long long base = ex + (S.first ? 32ull : 0ull);  // 16-byte aligned
+    const unsigned long long cap = it.out_cap;
+    uint8_t* const out = it.out;
+    if (base + bytes <= cap) {
+        const uint8_t* src = (const uint8_t*)it.x + te0 * es;
+        if (((uintptr_t)src & 15u) == 0) {
+            const unsigned long long nv = bytes / 16;
+            for (unsigned long long i = tid; i < nv; i += NTHREADS)
+                ((uint4*)(out + base))[i] = __ldg((const uint4*)src + i);
+            for (unsigned long long i = nv * 16 + tid * 2; i < bytes; i += 2 * NTHREADS)
+                *(uint16_t*)(out + base + i) = __ldg((const unsigned short*)(src + i));
+        } else {
+            // the input is only element-aligned: 2-byte copies
+            for (unsigned long long i = (unsigned long long)tid * 2; i < bytes; i += 2 * NTHREADS)
+                *(uint16_t*)(out + base + i) = __ldg((const unsigned short*)(src + i));
+        }
+    } else if (tid == 0) {
+        fail(P.ctl, ZC_ERR_CAPACITY, g);
+    }
+    if (S.last) {
+        const unsigned long long end = ex + S.head;
+        const unsigned long long total = ceil16(end);
+        const unsigned long long pl = n * es;
+        for (unsigned long long p = end + tid; p < total; p += NTHREADS)
+            if (p < cap) out[p] = 0;
+        if (tid < 8 && start + 32 <= cap) {
+            uint32_t v = 0;
+            switch (tid) {
+            case 0: v = 0x3176435au; break;  // "ZCv1"
+            case 1: v = (uint32_t)it.x_dtype | (5u << 8) | (1u << 16); break;  // raw flag
+            case 2: v = (uint32_t)n; break;
+            case 3: v = (uint32_t)(n >> 32); break;
+            case 4: v = 0u; break;  // eb: none
+            case 5: v = 0u; break;  // no blocks
             case 6: v = (uint32_t)pl; break;
             default: v = (uint32_t)(pl >> 32); break;
             }
@@ -913,178 +1067,203 @@ struct ScatterSrc {
     }
 };
 
-// Tile loop of the encoders: CTAs take tiles in ticket order, so a tile only
-// ever waits for tiles taken earlier by CTAs that are running or done; the
-// last CTA to finish advances the launch generation.
-template <typename Src, typename Body>
-__device__ __forceinline__ void tile_loop(const Launch& P, const Src& src, Smem& sm, Body body)
+// Resolver warp: the tile's place in the chain (look-back over the tiles
+// before it) and, in packed mode, its stream's start.
+__device__ __forceinline__ void resolve_slot(const Launch& P, TileSlot& S, unsigned E)
 {
-    if (threadIdx.x == 0) {
-        sm.E = ld_volatile_u32(&P.ctl->epoch) + 1u;
-        sm.abort = ld_volatile_u32(&P.ctl->magic) != WS_MAGIC;
-        if (sm.abort) fail(P.ctl, ZC_ERR_WORKSPACE, 0);
-        else if (P.eb_from_ctl && ld_volatile_u32(&P.ctl->eb_ok) != 1u) sm.abort = 2;
+    int ok = 0;
+    unsigned long long ex = 0ull, start = 0ull;
+    if (S.pub) {
+        unsigned long long agg = S.head;
+#pragma unroll
+        for (int w = 0; w < NWARPS; ++w) agg += (unsigned long long)S.segsz[w];
+        const unsigned g0 = P.packed ? 0u : S.g - S.tile;
+        bool expired = false;
+        ex = lookback_warp(P.chB, S.g, g0, agg, S.last != 0, E, P.wc, P.ctl, expired);
+        ok = !expired && packed_start_warp(P, S.first != 0, S.item, ex, S.g, E, start);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        S.ex = ex;
+        S.start = start;
+        S.ok = ok;
+    }
+}
+
+// The encoder CTA.  Tickets are taken in order, so a tile only ever waits for
+// tiles taken earlier by CTAs that are running or done; every resolver
+// publishes its tiles in ticket order, so the chain always advances.  The
+// last CTA to finish advances the launch generation.
+//   enc(item, index, tile in item, segment, width bytes, slot, shared) -> unit size
+//   fin(item, index, tile in item, ticket, slot, segment, width bytes)
+// Barrier protocol per tile in slot s: the encoder warps arrive on BAR_ENC + s
+// after encoding it, the resolver waits there, resolves it and arrives on
+// BAR_RES + s, where the encoder warps wait ENC_SLOTS - 1 tiles later before
+// storing it.  A slot's barriers are used again only after both sides have
+// passed them, and every path through the loops meets every barrier.
+template <int U, typename Src, typename Enc, typename Fin>
+__device__ __forceinline__ void enc_pipeline(const Launch& P, const Src& src, Enc enc, Fin fin)
+{
+    constexpr int D = ENC_SLOTS - 1;  // tiles between a tile's encoding and its stores
+    __shared__ TileSlot slots[ENC_SLOTS];
+    __shared__ EncShared es;
+    extern __shared__ __align__(16) uint8_t dsm[];  // width bytes [slot][warp][2U]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        es.E = ld_volatile_u32(&P.ctl->epoch) + 1u;
+        int a = ld_volatile_u32(&P.ctl->magic) != WS_MAGIC;
+        if (a) {
+            fail(P.ctl, ZC_ERR_WORKSPACE, 0);
+        } else if ((unsigned long long)gridDim.x * ring_cta_bytes(U) > P.ring_bytes) {
+            a = 1;  // more CTAs than rings: the whole launch does nothing
+            if (blockIdx.x == 0) fail(P.ctl, ZC_ERR_WORKSPACE, 1);
+        } else if (P.eb_from_ctl && ld_volatile_u32(&P.ctl->eb_ok) != 1u) {
+            a = 2;
+        }
+        es.abort = a;
     }
     __syncthreads();
-    if (sm.abort == 1) return;  // uninitialised workspace: touch nothing
-    const bool no_eb = sm.abort == 2;
+    if (es.abort == 1) return;
+    const bool no_eb = es.abort == 2;
+    const unsigned E = es.E;
     const unsigned modulus = P.total_tiles + gridDim.x - 1u;
-    while (true) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            sm.ticket = atomicInc(&P.ctl->ticket, modulus);
-            sm.item = sm.ticket < P.total_tiles ? src.find(sm.ticket) : 0u;
-            sm.abort = 0;
+    uint8_t* const ring = P.ring + (unsigned long long)blockIdx.x * ring_cta_bytes(U);
+    if (warp < NWARPS) {
+        auto seg_of = [&](int s) { return ring + (unsigned long long)(s * NWARPS + warp) * seg_bytes(U); };
+        auto wb_of = [&](int s) { return dsm + (s * NWARPS + warp) * (U * 2); };
+        auto store = [&](int q) {
+            bar_sync_n(BAR_RES + q, ENC_THREADS);
+            const TileSlot& Q = slots[q];
+            if (Q.ok) {
+                const Item it = src.get(Q.item);
+                fin(it, Q.item, Q.tile, Q.g, Q, seg_of(q), wb_of(q));
+            }
+        };
+        int s = 0;
+        for (int i = 0;; ++i) {
+            bar_sync_n(BAR_ENCW, NTHREADS);  // slot s's previous tile is stored
+            if (tid == 0) {
+                TileSlot& S = slots[s];
+                const unsigned g = atomicInc(&P.ctl->ticket, modulus);
+                S.g = g;
+                S.valid = g < P.total_tiles;
+                S.item = g < P.total_tiles ? src.find(g) : 0u;
+                S.pub = 0;
+            }
+            bar_sync_n(BAR_ENCW, NTHREADS);
+            TileSlot& S = slots[s];
+            const bool valid = S.valid != 0;
+            int lo = 0;
+            if (valid && !no_eb) {
+                const Item it = src.get(S.item);
+                const unsigned t = S.g - it.tile_begin;
+                if (tid == 0) S.tile = t;
+                lo = enc(it, S.item, t, seg_of(s), wb_of(s), S, es);
+            }
+            if (lane == 0) S.segsz[warp] = lo;
+            bar_arrive_n(BAR_ENC + s, ENC_THREADS);
+            if (!valid) {
+                // the tiles still waiting for their stores, oldest first
+                for (int k = (i < D ? i : D) - 1; k >= 0; --k) store((s + ENC_SLOTS - 1 - k) % ENC_SLOTS);
+                break;
+            }
+            if (i >= D) store((s + 1) % ENC_SLOTS);
+            s = s + 1 == ENC_SLOTS ? 0 : s + 1;
         }
-        __syncthreads();
-        const unsigned g = sm.ticket;
-        if (g >= P.total_tiles) break;
-        if (!no_eb) {
-            const Item item = src.get(sm.item);
-            body(item, sm.item, g - item.tile_begin, g);
+    } else {
+        int s = 0;
+        while (true) {
+            bar_sync_n(BAR_ENC + s, ENC_THREADS);
+            TileSlot& S = slots[s];
+            if (!S.valid) break;
+            resolve_slot(P, S, E);
+            __syncwarp();
+            bar_arrive_n(BAR_RES + s, ENC_THREADS);
+            s = s + 1 == ENC_SLOTS ? 0 : s + 1;
         }
     }
-    if (threadIdx.x == 0) {
+    __syncthreads();
+    if (tid == 0) {
         __threadfence();
         if (atomicInc(&P.ctl->done, gridDim.x - 1u) == gridDim.x - 1u) {
-            P.ctl->epoch = sm.E;
+            P.ctl->epoch = E;
             __threadfence();
         }
     }
 }
 
 template <int LOG2L, int U, typename TX, bool HEADS = false>
-__global__ void __launch_bounds__(NTHREADS, 4) k_compress(const Launch P)
+__global__ void __launch_bounds__(ENC_THREADS, ENC_CTAS_PER_SM) k_compress(const Launch P)
 {
-    __shared__ Smem sm;
-    extern __shared__ __align__(16) uint8_t dsm[];
-    tile_loop(P, ItemsSrc{P}, sm, [&](const Item& it, unsigned idx, unsigned t, unsigned g) {
-        tile_encode<LOG2L, U, false, TX, HEADS>(P, it, idx, t, g, sm, dsm);
-    });
+    enc_pipeline<U>(
+        P, ItemsSrc{P},
+        [&](const Item& it, unsigned idx, unsigned t, uint8_t* seg, uint8_t* wb, TileSlot& S,
+            EncShared& es) { return enc_tile<LOG2L, U, false, TX, HEADS>(P, it, idx, t, seg, wb, S, es); },
+        [&](const Item& it, unsigned idx, unsigned t, unsigned g, const TileSlot& S,
+            const uint8_t* seg, const uint8_t* wb) { fin_tile<LOG2L, U, false, HEADS>(P, it, idx, t, g, S, seg, wb); });
 }
 
 template <int LOG2L, int U, typename TX>
-__global__ void __launch_bounds__(NTHREADS, 4) k_scatter(const Launch P, const ScatterParams SP)
+__global__ void __launch_bounds__(ENC_THREADS, ENC_CTAS_PER_SM) k_scatter(const Launch P,
+                                                                          const ScatterParams SP)
 {
-    __shared__ Smem sm;
-    extern __shared__ __align__(16) uint8_t dsm[];
-    tile_loop(P, ScatterSrc{P, SP}, sm, [&](const Item& it, unsigned idx, unsigned t, unsigned g) {
-        tile_encode<LOG2L, U, false, TX>(P, it, idx, t, g, sm, dsm);
-    });
+    enc_pipeline<U>(
+        P, ScatterSrc{P, SP},
+        [&](const Item& it, unsigned idx, unsigned t, uint8_t* seg, uint8_t* wb, TileSlot& S,
+            EncShared& es) { return enc_tile<LOG2L, U, false, TX>(P, it, idx, t, seg, wb, S, es); },
+        [&](const Item& it, unsigned idx, unsigned t, unsigned g, const TileSlot& S,
+            const uint8_t* seg, const uint8_t* wb) { fin_tile<LOG2L, U, false>(P, it, idx, t, g, S, seg, wb); });
 }
 
 template <int LOG2L, int U>
-__global__ void __launch_bounds__(NTHREADS, 4) k_reduce(const Launch P)
+__global__ void __launch_bounds__(ENC_THREADS, ENC_CTAS_PER_SM) k_reduce(const Launch P)
 {
-    __shared__ Smem sm;
-    extern __shared__ __align__(16) uint8_t dsm[];
-    tile_loop(P, ItemsSrc{P}, sm, [&](const Item& it, unsigned idx, unsigned t, unsigned g) {
-        tile_encode<LOG2L, U, true, float>(P, it, idx, t, g, sm, dsm);
-    });
+    enc_pipeline<U>(
+        P, ItemsSrc{P},
+        [&](const Item& it, unsigned idx, unsigned t, uint8_t* seg, uint8_t* wb, TileSlot& S,
+            EncShared& es) { return enc_tile<LOG2L, U, true, float>(P, it, idx, t, seg, wb, S, es); },
+        [&](const Item& it, unsigned idx, unsigned t, unsigned g, const TileSlot& S,
+            const uint8_t* seg, const uint8_t* wb) { fin_tile<LOG2L, U, true>(P, it, idx, t, g, S, seg, wb); });
 }
 
 // ---- batched compression -----------------------------------------------------
-
-// One tile of a raw (verbatim) stream: the item's elements of this tile go
-// unchanged after the 32-byte header (flag bit 0 set, no width bytes).  Same
-// tile geometry, look-back and stream-start protocol as tile_encode, so raw
-// and encoded streams mix in one packed launch.
+// Every item is a stream of its own block size and input type (or raw), all
+// packed back to back by one chain; the CTAs take tiles of all items from one
+// ticket counter, so one launch of a few CTAs per SM covers any mix of
+// message sizes.
 template <int U>
-__device__ __forceinline__ void tile_raw(const Launch& P, const Item& it, unsigned item_idx,
-                                         unsigned tile_in_item, unsigned g, Smem& sm)
+__global__ void __launch_bounds__(ENC_THREADS, ENC_CTAS_PER_SM) k_batch(const Launch P)
 {
-    constexpr unsigned long long TE = (unsigned long long)NWARPS * U * 32;
-    const int tid = threadIdx.x;
-    const unsigned long long n = it.n;
-    const unsigned long long es = it.x_dtype == ZC_F32 ? 4ull : 2ull;
-    const unsigned long long te0 = (unsigned long long)tile_in_item * TE;
-    const unsigned long long cnt = te0 < n ? min(n - te0, TE) : 0ull;
-    const unsigned long long bytes = cnt * es;
-    const bool first = tile_in_item == 0;
-    const bool last = tile_in_item + 1 == it.ntiles;
-    const unsigned long long agg = bytes + (first ? 32ull : 0ull);
-    const unsigned g0 = P.packed ? 0u : g - tile_in_item;
-    bool to = false;
-    const unsigned long long ex = lookback_cta(P.chB, g, g0, agg, last, sm.E, P.wc, P.ctl, to, sm.lb);
-    unsigned long long start = 0ull;
-    if (to || !packed_start(P, first, item_idx, ex, g, sm, start)) return;
-    const unsigned long long base = ex + (first ? 32ull : 0ull);  // 16-byte aligned
-    const unsigned long long cap = it.out_cap;
-    uint8_t* const out = it.out;
-    if (base + bytes <= cap) {
-        const uint8_t* src = (const uint8_t*)it.x + te0 * es;
-        if (((uintptr_t)src & 15u) == 0) {
-            const unsigned long long nv = bytes / 16;
-            for (unsigned long long i = tid; i < nv; i += NTHREADS)
-                ((uint4*)(out + base))[i] = __ldg((const uint4*)src + i);
-            for (unsigned long long i = nv * 16 + tid * 2; i < bytes; i += 2 * NTHREADS)
-                *(uint16_t*)(out + base + i) = __ldg((const unsigned short*)(src + i));
-        } else {
-            // the input is only element-aligned: 2-byte copies
-            for (unsigned long long i = (unsigned long long)tid * 2; i < bytes; i += 2 * NTHREADS)
-                *(uint16_t*)(out + base + i) = __ldg((const unsigned short*)(src + i));
-        }
-    } else if (tid == 0) {
-        fail(P.ctl, ZC_ERR_CAPACITY, g);
-    }
-    if (last) {
-        const unsigned long long end = ex + agg;
-        const unsigned long long total = ceil16(end);
-        const unsigned long long pl = n * es;
-        for (unsigned long long p = end + tid; p < total; p += NTHREADS)
-            if (p < cap) out[p] = 0;
-        if (tid < 8 && start + 32 <= cap) {
-            uint32_t v = 0;
-            switch (tid) {
-            case 0: v = 0x3176435au; break;  // "ZCv1"
-            case 1: v = (uint32_t)it.x_dtype | (5u << 8) | (1u << 16); break;  // raw flag
-            case 2: v = (uint32_t)n; break;
-            case 3: v = (uint32_t)(n >> 32); break;
-            case 4: v = 0u; break;  // eb: none
-            case 5: v = 0u; break;  // no blocks
-            case 6: v = (uint32_t)pl; break;
-            default: v = (uint32_t)(pl >> 32); break;
+    enc_pipeline<U>(
+        P, ItemsSrc{P},
+        [&](const Item& it, unsigned idx, unsigned t, uint8_t* seg, uint8_t* wb, TileSlot& S,
+            EncShared& es) -> int {
+            const bool f32 = it.x_dtype == ZC_F32;
+            switch (it.log2L) {
+            case 4:
+                return f32 ? enc_tile<4, U, false, float>(P, it, idx, t, seg, wb, S, es)
+                           : enc_tile<4, U, false, uint16_t>(P, it, idx, t, seg, wb, S, es);
+            case 5:
+                return f32 ? enc_tile<5, U, false, float>(P, it, idx, t, seg, wb, S, es)
+                           : enc_tile<5, U, false, uint16_t>(P, it, idx, t, seg, wb, S, es);
+            case 6:
+                return f32 ? enc_tile<6, U, false, float>(P, it, idx, t, seg, wb, S, es)
+                           : enc_tile<6, U, false, uint16_t>(P, it, idx, t, seg, wb, S, es);
+            case 7:
+                return f32 ? enc_tile<7, U, false, float>(P, it, idx, t, seg, wb, S, es)
+                           : enc_tile<7, U, false, uint16_t>(P, it, idx, t, seg, wb, S, es);
+            default: return enc_raw<U>(it, t, S);
             }
-            ((uint32_t*)(out + start))[tid] = v;
-        }
-        if (tid == 0) {
-            if (it.out_bytes) *it.out_bytes = total - start;
-            if (P.packed) P.seg_off[item_idx + 1] = total;
-        }
-    }
-}
-
-// Batched compression: every item is a stream of its own block size and
-// input type (or raw), all packed back to back by one chain; the CTAs take
-// tiles of all items from one ticket counter, so one launch of a few CTAs per
-// SM covers any mix of message sizes.
-template <int U>
-__global__ void __launch_bounds__(NTHREADS, 4) k_batch(const Launch P)
-{
-    __shared__ Smem sm;
-    extern __shared__ __align__(16) uint8_t dsm[];
-    tile_loop(P, ItemsSrc{P}, sm, [&](const Item& it, unsigned idx, unsigned t, unsigned g) {
-        const bool f32 = it.x_dtype == ZC_F32;
-        switch (it.log2L) {
-        case 4:
-            if (f32) tile_encode<4, U, false, float>(P, it, idx, t, g, sm, dsm);
-            else tile_encode<4, U, false, uint16_t>(P, it, idx, t, g, sm, dsm);
-            break;
-        case 5:
-            if (f32) tile_encode<5, U, false, float>(P, it, idx, t, g, sm, dsm);
-            else tile_encode<5, U, false, uint16_t>(P, it, idx, t, g, sm, dsm);
-            break;
-        case 6:
-            if (f32) tile_encode<6, U, false, float>(P, it, idx, t, g, sm, dsm);
-            else tile_encode<6, U, false, uint16_t>(P, it, idx, t, g, sm, dsm);
-            break;
-        case 7:
-            if (f32) tile_encode<7, U, false, float>(P, it, idx, t, g, sm, dsm);
-            else tile_encode<7, U, false, uint16_t>(P, it, idx, t, g, sm, dsm);
-            break;
-        default: tile_raw<U>(P, it, idx, t, g, sm); break;
-        }
-    });
+        },
+        [&](const Item& it, unsigned idx, unsigned t, unsigned g, const TileSlot& S,
+            const uint8_t* seg, const uint8_t* wb) {
+            switch (it.log2L) {
+            case 4: fin_tile<4, U, false>(P, it, idx, t, g, S, seg, wb); break;
+            case 5: fin_tile<5, U, false>(P, it, idx, t, g, S, seg, wb); break;
+            case 6: fin_tile<6, U, false>(P, it, idx, t, g, S, seg, wb); break;
+            case 7: fin_tile<7, U, false>(P, it, idx, t, g, S, seg, wb); break;
+            default: fin_raw<U>(P, it, idx, t, g, S); break;
+            }
+        });
 }
 
 // Batched decompression: item idx's stream, from a packed buffer written by an

@@ -284,127 +284,133 @@ __device__ __forceinline__ bool flag_valid(unsigned long long f, unsigned E)
     return (unsigned)(f >> 32) == E && ((f >> 30) & 3u) != 0u;
 }
 
-// Run by the whole CTA; only warp 0 polls (the other warps wait at a
-// barrier and issue nothing).  g: this tile's slot; g0: first slot of its
-// chain (whose exclusive value is 0).  Publishes g's aggregate, then inspects
-// the LB_WINDOW preceding slots (LB_PER_LANE consecutive slots per lane),
-// waits until all of them have published, composes the aggregates after the
-// nearest inclusive prefix, and repeats further back if there is none.
-// Publishes g's inclusive prefix and returns g's exclusive value (the same in
-// every thread).  If the wait runs out, records ZC_ERR_TIMEOUT, sets
-// timed_out and returns 0.
-__device__ __forceinline__ unsigned long long lookback_cta(const Chain& ch, unsigned g,
-                                                           unsigned g0, unsigned long long agg,
-                                                           bool h, unsigned E, const WaitCfg& wc,
-                                                           Ctl* ctl, bool& timed_out, LbSmem& ls)
+// Run by one whole warp.  g: this tile's slot; g0: first slot of its chain
+// (whose exclusive value is 0).  Publishes g's aggregate, then inspects the
+// LB_WINDOW preceding slots (LB_PER_LANE consecutive slots per lane), waits
+// until all of them have published, composes the aggregates after the nearest
+// inclusive prefix, and repeats further back if there is none.  Publishes g's
+// inclusive prefix and returns g's exclusive value (the same in every lane).
+// If the wait runs out, records ZC_ERR_TIMEOUT, sets `expired` and returns 0
+// (the prefix is still published, so the chain moves on; the status word
+// already marks the result unusable).
+__device__ __forceinline__ unsigned long long lookback_warp(const Chain& ch, unsigned g,
+                                                            unsigned g0, unsigned long long agg,
+                                                            bool h, unsigned E, const WaitCfg& wc,
+                                                            Ctl* ctl, bool& expired)
 {
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int lane = threadIdx.x & 31;
     const bool publish = (long long)g != wc.withhold;
     const Xf self{agg, 0ull, h};
-    timed_out = false;
+    expired = false;
     if (g == g0) {
-        if (tid == 0 && publish) {
+        if (lane == 0 && publish) {
             st_relaxed(ch.pref + g, xf_apply(self, 0ull));
             if (agg > AGG_INLINE_MAX) st_relaxed(ch.aggw + g, agg);
             st_release(ch.flag + g, make_flag(E, ST_PREFIX, h, agg));
         }
         return 0ull;
     }
-    if (tid < 32) {
-        if (tid == 0 && publish) {
-            if (agg > AGG_INLINE_MAX) st_relaxed(ch.aggw + g, agg);
-            st_release(ch.flag + g, make_flag(E, ST_AGG, h, agg));
+    if (lane == 0 && publish) {
+        if (agg > AGG_INLINE_MAX) st_relaxed(ch.aggw + g, agg);
+        st_release(ch.flag + g, make_flag(E, ST_AGG, h, agg));
+    }
+    Xf acc = xf_id();
+    long long hi = (long long)g - 1;
+    unsigned long long excl = 0ull;
+    const unsigned long long t0 = globaltimer();
+    while (true) {
+        // slots j0 .. j0 + LB_PER_LANE - 1 of this lane, oldest first
+        const long long j0 = hi - (LB_WINDOW - 1) + (long long)lane * LB_PER_LANE;
+        unsigned long long f[LB_PER_LANE];
+        unsigned valid = 0;
+#pragma unroll
+        for (int i = 0; i < LB_PER_LANE; ++i) {
+            const long long j = j0 + i;
+            if (j < (long long)g0) {
+                f[i] = 0ull;
+                valid |= 1u << i;
+            } else {
+                f[i] = ld_acquire(ch.flag + j);
+                if (flag_valid(f[i], E)) valid |= 1u << i;
+            }
         }
-        Xf acc = xf_id();
-        long long hi = (long long)g - 1;
-        unsigned long long excl = 0ull;
-        bool expired = false;
-        const unsigned long long t0 = globaltimer();
-        while (true) {
-            // slots j0 .. j0 + LB_PER_LANE - 1 of this lane, oldest first
-            const long long j0 = hi - (LB_WINDOW - 1) + (long long)lane * LB_PER_LANE;
-            unsigned long long f[LB_PER_LANE];
-            unsigned valid = 0;
+        unsigned ns = 32;
+        while (!__all_sync(FULL, valid == (1u << LB_PER_LANE) - 1u)) {
+            expired = __any_sync(FULL, globaltimer() - t0 > wc.limit_ns);
+            if (expired) break;
+            __nanosleep(ns);
+            ns = ns < 256 ? ns * 2 : ns;
 #pragma unroll
             for (int i = 0; i < LB_PER_LANE; ++i) {
-                const long long j = j0 + i;
-                if (j < (long long)g0) {
-                    f[i] = 0ull;
-                    valid |= 1u << i;
-                } else {
-                    f[i] = ld_acquire(ch.flag + j);
+                if (!((valid >> i) & 1u)) {
+                    f[i] = ld_acquire(ch.flag + (j0 + i));
                     if (flag_valid(f[i], E)) valid |= 1u << i;
                 }
             }
-            unsigned ns = 32;
-            while (!__all_sync(FULL, valid == (1u << LB_PER_LANE) - 1u)) {
-                expired = __any_sync(FULL, globaltimer() - t0 > wc.limit_ns);
-                if (expired) break;
-                __nanosleep(ns);
-                ns = ns < 256 ? ns * 2 : ns;
+        }
+        if (expired) {
+            if (lane == 0) fail(ctl, ZC_ERR_TIMEOUT, g);
+            excl = 0ull;
+            break;
+        }
+        // this lane's newest prefix slot (virtual slots before g0 count as prefix 0)
+        int pi = -1;
 #pragma unroll
-                for (int i = 0; i < LB_PER_LANE; ++i) {
-                    if (!((valid >> i) & 1u)) {
-                        f[i] = ld_acquire(ch.flag + (j0 + i));
-                        if (flag_valid(f[i], E)) valid |= 1u << i;
-                    }
-                }
-            }
-            if (expired) {
-                if (lane == 0) fail(ctl, ZC_ERR_TIMEOUT, g);
-                excl = 0ull;
-                break;
-            }
-            // this lane's newest prefix slot (virtual slots before g0 count as prefix 0)
-            int pi = -1;
+        for (int i = 0; i < LB_PER_LANE; ++i) {
+            const bool is_pref = (j0 + i < (long long)g0) || ((f[i] >> 30) & 3u) == ST_PREFIX;
+            if (is_pref) pi = i;
+        }
+        const unsigned pm = __ballot_sync(FULL, pi >= 0);
+        const int pl = pm ? 31 - __clz(pm) : -1;  // lane holding the newest prefix
+        // this lane's composed transform of its slots after the newest prefix
+        Xf t = xf_id();
+        if (lane >= pl) {
 #pragma unroll
             for (int i = 0; i < LB_PER_LANE; ++i) {
-                const bool is_pref = (j0 + i < (long long)g0) || ((f[i] >> 30) & 3u) == ST_PREFIX;
-                if (is_pref) pi = i;
-            }
-            const unsigned pm = __ballot_sync(FULL, pi >= 0);
-            const int pl = pm ? 31 - __clz(pm) : -1;  // lane holding the newest prefix
-            // this lane's composed transform of its slots after the newest prefix
-            Xf t = xf_id();
-            if (lane >= pl) {
-#pragma unroll
-                for (int i = 0; i < LB_PER_LANE; ++i) {
-                    const long long j = j0 + i;
-                    if (j >= (long long)g0 && (lane > pl || i > pi)) {
-                        Xf x;
-                        x.h = (f[i] >> 29) & 1u;
-                        x.a = ((f[i] >> 28) & 1u) ? ld_relaxed(ch.aggw + j) : (f[i] & AGG_INLINE_MAX);
-                        x.b = 0ull;
-                        t = xf_compose(t, x);
-                    }
+                const long long j = j0 + i;
+                if (j >= (long long)g0 && (lane > pl || i > pi)) {
+                    Xf x;
+                    x.h = (f[i] >> 29) & 1u;
+                    x.a = ((f[i] >> 28) & 1u) ? ld_relaxed(ch.aggw + j) : (f[i] & AGG_INLINE_MAX);
+                    x.b = 0ull;
+                    t = xf_compose(t, x);
                 }
             }
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const Xf o = xf_shfl_up(t, off);
-                if (lane >= off) t = xf_compose(o, t);
-            }
-            acc = xf_compose(xf_shfl(t, 31), acc);
-            if (pl >= 0) {
-                unsigned long long pv = 0ull;
-                if (lane == pl && j0 + pi >= (long long)g0) pv = ld_relaxed(ch.pref + (j0 + pi));
-                pv = __shfl_sync(FULL, pv, pl);
-                excl = xf_apply(acc, pv);
-                break;
-            }
-            hi -= LB_WINDOW;
         }
-        if (lane == 0) {
-            if (publish && !expired) {
-                st_relaxed(ch.pref + g, xf_apply(self, excl));
-                st_release(ch.flag + g, make_flag(E, ST_PREFIX, h, agg));
-            } else if (publish) {
-                // keep the chain moving: successors read a (wrong) prefix, the
-                // status word already says the result is unusable
-                st_relaxed(ch.pref + g, xf_apply(self, 0ull));
-                st_release(ch.flag + g, make_flag(E, ST_PREFIX, h, agg));
-            }
-            ls.excl = excl;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const Xf o = xf_shfl_up(t, off);
+            if (lane >= off) t = xf_compose(o, t);
+        }
+        acc = xf_compose(xf_shfl(t, 31), acc);
+        if (pl >= 0) {
+            unsigned long long pv = 0ull;
+            if (lane == pl && j0 + pi >= (long long)g0) pv = ld_relaxed(ch.pref + (j0 + pi));
+            pv = __shfl_sync(FULL, pv, pl);
+            excl = xf_apply(acc, pv);
+            break;
+        }
+        hi -= LB_WINDOW;
+    }
+    if (lane == 0 && publish) {
+        st_relaxed(ch.pref + g, xf_apply(self, expired ? 0ull : excl));
+        st_release(ch.flag + g, make_flag(E, ST_PREFIX, h, agg));
+    }
+    return excl;
+}
+
+// The same for a whole CTA: warp 0 runs the look-back while the other warps
+// wait at a barrier; every thread gets the exclusive value.
+__device__ __forceinline__ unsigned long long lookback_cta(const Chain& ch, unsigned g,
+                                                           unsigned g0, unsigned long long agg,
+                                                           bool h, unsigned E, const WaitCfg& wc,
+                                                           Ctl* ctl, bool& timed_out, LbSmem& ls)
+{
+    if (threadIdx.x < 32) {
+        bool expired = false;
+        const unsigned long long ex = lookback_warp(ch, g, g0, agg, h, E, wc, ctl, expired);
+        if (threadIdx.x == 0) {
+            ls.excl = ex;
             ls.timed_out = expired;
         }
     }
@@ -413,6 +419,18 @@ __device__ __forceinline__ unsigned long long lookback_cta(const Chain& ch, unsi
     const unsigned long long ex = ls.excl;
     __syncthreads();  // ls may be reused right after
     return ex;
+}
+
+// Named barriers (ids 1..15) shared by a subset of a CTA's warps: `n`
+// threads (whole warps) take part.  bar.arrive does not wait; both order the
+// caller's earlier memory accesses before the barrier completes.
+__device__ __forceinline__ void bar_sync_n(unsigned id, unsigned n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive_n(unsigned id, unsigned n)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
 // Bounded wait for a value published with st_release on `flag` (epoch E in

@@ -16,8 +16,8 @@ static cudaError_t compress_u(int x_dtype, const Launch& P, unsigned grid, cudaS
     static const cudaError_t e32 = prepare(k_compress<4, U, float>, U);
     static const cudaError_t e16 = prepare(k_compress<4, U, uint16_t>, U);
     if (e32 != cudaSuccess || e16 != cudaSuccess) return e32 != cudaSuccess ? e32 : e16;
-    if (x_dtype == ZC_F32) k_compress<4, U, float><<<grid, NTHREADS, enc_smem_bytes(U), s>>>(P);
-    else k_compress<4, U, uint16_t><<<grid, NTHREADS, enc_smem_bytes(U), s>>>(P);
+    if (x_dtype == ZC_F32) k_compress<4, U, float><<<grid, ENC_THREADS, enc_smem_bytes(U), s>>>(P);
+    else k_compress<4, U, uint16_t><<<grid, ENC_THREADS, enc_smem_bytes(U), s>>>(P);
     return cudaGetLastError();
 }
 
@@ -28,9 +28,9 @@ cudaError_t launch_compress_heads_l16(int x_dtype, const Launch& P, unsigned gri
     static const cudaError_t e16 = prepare(k_compress<4, 64, uint16_t, true>, 64);
     if (e32 != cudaSuccess || e16 != cudaSuccess) return e32 != cudaSuccess ? e32 : e16;
     if (x_dtype == ZC_F32)
-        k_compress<4, 64, float, true><<<grid, NTHREADS, enc_smem_bytes(64), s>>>(P);
+        k_compress<4, 64, float, true><<<grid, ENC_THREADS, enc_smem_bytes(64), s>>>(P);
     else
-        k_compress<4, 64, uint16_t, true><<<grid, NTHREADS, enc_smem_bytes(64), s>>>(P);
+        k_compress<4, 64, uint16_t, true><<<grid, ENC_THREADS, enc_smem_bytes(64), s>>>(P);
     return cudaGetLastError();
 }
 
@@ -51,8 +51,8 @@ static cudaError_t scatter_u(int x_dtype, const Launch& P, const ScatterParams& 
     static const cudaError_t e32 = prepare(k_scatter<4, U, float>, U);
     static const cudaError_t e16 = prepare(k_scatter<4, U, uint16_t>, U);
     if (e32 != cudaSuccess || e16 != cudaSuccess) return e32 != cudaSuccess ? e32 : e16;
-    if (x_dtype == ZC_F32) k_scatter<4, U, float><<<grid, NTHREADS, enc_smem_bytes(U), s>>>(P, SP);
-    else k_scatter<4, U, uint16_t><<<grid, NTHREADS, enc_smem_bytes(U), s>>>(P, SP);
+    if (x_dtype == ZC_F32) k_scatter<4, U, float><<<grid, ENC_THREADS, enc_smem_bytes(U), s>>>(P, SP);
+    else k_scatter<4, U, uint16_t><<<grid, ENC_THREADS, enc_smem_bytes(U), s>>>(P, SP);
     return cudaGetLastError();
 }
 
@@ -72,7 +72,7 @@ static cudaError_t reduce_u(const Launch& P, unsigned grid, cudaStream_t s)
 {
     static const cudaError_t e = prepare(k_reduce<4, U>, U);
     if (e != cudaSuccess) return e;
-    k_reduce<4, U><<<grid, NTHREADS, enc_smem_bytes(U), s>>>(P);
+    k_reduce<4, U><<<grid, ENC_THREADS, enc_smem_bytes(U), s>>>(P);
     return cudaGetLastError();
 }
 

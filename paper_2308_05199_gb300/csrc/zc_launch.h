@@ -35,7 +35,7 @@ cudaError_t launch_batch_u(const Launch& P, unsigned grid, cudaStream_t s)
     static const cudaError_t e = cudaFuncSetAttribute(
         k_batch<U>, cudaFuncAttributeMaxDynamicSharedMemorySize, enc_smem_bytes(U));
     if (e != cudaSuccess) return e;
-    k_batch<U><<<grid, NTHREADS, enc_smem_bytes(U), s>>>(P);
+    k_batch<U><<<grid, ENC_THREADS, enc_smem_bytes(U), s>>>(P);
     return cudaGetLastError();
 }
 
