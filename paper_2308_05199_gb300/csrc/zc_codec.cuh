@@ -464,12 +464,54 @@ __device__ __forceinline__ void decode_group(const uint8_t* src, const int2* met
 }
 
 // ---- encoding ------------------------------------------------------------------
-// Quantizes, delta-codes and bit-plane packs GR rows (the first `nrem`
-// elements are valid, all of them when ALL; the rest are padding with zero
-// deltas), appends the
-// planes of their blocks to `seg` at byte `lo` in stream order, writes their
-// width bytes to `wb`, ORs any quantizer error into `err`, and returns the new
-// `lo`.  Two rows whose values fit 16 bits share one transpose.
+// Predicated stores without a branch: the store happens when a < b.  `p` is
+// a global address (the tile ring).
+__device__ __forceinline__ void stg_u32_if(uint8_t* p, uint32_t v, int a, int b)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.s32 q, %2, %3;\n\t@q st.global.u32 [%0], %1;\n\t}"
+                 ::"l"(__cvta_generic_to_global(p)), "r"(v), "r"(a), "r"(b) : "memory");
+}
+__device__ __forceinline__ void stg_u16_if(uint8_t* p, uint32_t v, int a, int b)
+{
+    asm volatile("{\n\t.reg .pred q;\n\t.reg .b16 h;\n\tcvt.u16.u32 h, %1;\n\t"
+                 "setp.lt.s32 q, %2, %3;\n\t@q st.global.u16 [%0], h;\n\t}"
+                 ::"l"(__cvta_generic_to_global(p)), "r"(v), "r"(a), "r"(b) : "memory");
+}
+__device__ __forceinline__ void stg_u64_if(uint8_t* p, uint32_t v0, uint32_t v1, int a, int b)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.s32 q, %3, %4;\n\t@q st.global.v2.u32 [%0], {%1, %2};\n\t}"
+                 ::"l"(__cvta_generic_to_global(p)), "r"(v0), "r"(v1), "r"(a), "r"(b) : "memory");
+}
+__device__ __forceinline__ void stg_u128_if(uint8_t* p, uint32_t v0, uint32_t v1, uint32_t v2,
+                                            uint32_t v3, int a, int b)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.s32 q, %5, %6;\n\t"
+                 "@q st.global.v4.u32 [%0], {%1, %2, %3, %4};\n\t}"
+                 ::"l"(__cvta_generic_to_global(p)), "r"(v0), "r"(v1), "r"(v2), "r"(v3), "r"(a),
+                 "r"(b) : "memory");
+}
+// Predicated shared-memory stores of width bytes (`p` in shared memory).
+__device__ __forceinline__ void sts_if(uint8_t* p, uint4 v, bool c)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %5, 0;\n\t@q st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n\t}"
+                 ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"((int)c) : "memory");
+}
+__device__ __forceinline__ void sts_if(uint8_t* p, uint2 v, bool c)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %3, 0;\n\t@q st.shared.v2.u32 [%0], {%1, %2};\n\t}"
+                 ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v.x), "r"(v.y), "r"((int)c) : "memory");
+}
+__device__ __forceinline__ void sts_if(uint8_t* p, uint32_t v, bool c)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %2, 0;\n\t@q st.shared.u32 [%0], %1;\n\t}"
+                 ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v), "r"((int)c) : "memory");
+}
+__device__ __forceinline__ void sts_if(uint8_t* p, unsigned short v, bool c)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %2, 0;\n\t@q st.shared.u16 [%0], %1;\n\t}"
+                 ::"r"((unsigned)__cvta_generic_to_shared(p)), "h"(v), "r"((int)c) : "memory");
+}
+
 // The previous lane's q within segments of W lanes; the first lane of a
 // segment gets `fill` (uses the in-range predicate of shfl.up).
 template <int W>
@@ -484,6 +526,13 @@ __device__ __forceinline__ int prev_lane(int q, int fill)
     return p;
 }
 
+// Quantizes, delta-codes and bit-plane packs GR rows (the first `nrem`
+// elements are valid, all of them when ALL; the rest are padding with zero
+// deltas), appends the planes of their blocks to the ring segment `seg` at
+// byte `lo` in stream order, writes their width bytes to `wb` (shared
+// memory, one store per group), ORs any quantizer error into `err`, and
+// returns the new `lo`.  Two rows whose values fit 16 bits share one
+// transpose.
 template <int LOG2L, bool ALL, bool HEADS = false>
 __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float eb, float two_eb,
                                             float inv, uint8_t* seg, int lo, uint8_t* wb, int& err,
@@ -542,6 +591,8 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
     // one vote: does any value of the group need more than 16 planes?
     const bool any_wide = __any_sync(FULL, (wide >> 16) != 0u);
     const uint32_t hmask = hi ? 0xffffffffu : 0u;
+    // the group's width bytes, gathered in registers and stored once (GR * 32 / L bytes)
+    uint32_t wacc[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int r = 0; r < GR; r += (L == 128 ? 4 : 2)) {
         if (L == 32) {
@@ -552,15 +603,15 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                 fa = 31 - __clz(m & 0xffffu);
                 fb = 31 - __clz(m >> 16);
                 const int npm = hi ? fb + 1 : fa + 1;
-                if (k < npm) *(uint32_t*)(seg + lo + (hmask & (4 * fa + 4)) + 4 * k) = t;
+                stg_u32_if(seg + lo + (hmask & (4 * fa + 4)) + 4 * k, t, k, npm);
             } else {
                 const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
                 fa = 31 - __clz(__ballot_sync(FULL, ta != 0u));
                 fb = 31 - __clz(__ballot_sync(FULL, tb != 0u));
-                if (lane <= fa) ((uint32_t*)(seg + lo))[lane] = ta;
-                if (lane <= fb) ((uint32_t*)(seg + lo + 4 * fa + 4))[lane] = tb;
+                stg_u32_if(seg + lo + 4 * lane, ta, lane, fa + 1);
+                stg_u32_if(seg + lo + 4 * fa + 4 + 4 * lane, tb, lane, fb + 1);
             }
-            if (lane == 0) *(uint16_t*)(wb + r) = (uint16_t)(max(fa, 0) | (max(fb, 0) << 8));
+            wacc[r / 4] |= ((uint32_t)max(fa, 0) | ((uint32_t)max(fb, 0) << 8)) << (8 * (r % 4));
             lo += 4 * (fa + fb + 2);
         } else if (L == 16) {
             int npA, npB, npC, npD;
@@ -575,8 +626,8 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                 const int oA = lo, oB = oA + 2 * npA, oC = oB + 2 * npB, oD = oC + 2 * npC;
                 const int npL = hi ? npC : npA, npH = hi ? npD : npB;
                 const int offL = hi ? oC : oA, offH = hi ? oD : oB;
-                if (k < npL) *(uint16_t*)(seg + offL + 2 * k) = (uint16_t)(t & 0xffffu);
-                if (k < npH) *(uint16_t*)(seg + offH + 2 * k) = (uint16_t)(t >> 16);
+                stg_u16_if(seg + offL + 2 * k, t & 0xffffu, k, npL);
+                stg_u16_if(seg + offH + 2 * k, t >> 16, k, npH);
             } else {
                 const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
                 npA = 32 - __clz(__ballot_sync(FULL, (ta & 0xffffu) != 0u));
@@ -584,15 +635,13 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                 npC = 32 - __clz(__ballot_sync(FULL, (tb & 0xffffu) != 0u));
                 npD = 32 - __clz(__ballot_sync(FULL, (tb >> 16) != 0u));
                 const int oA = lo, oB = oA + 2 * npA, oC = oB + 2 * npB, oD = oC + 2 * npC;
-                if (lane < npA) ((uint16_t*)(seg + oA))[lane] = (uint16_t)(ta & 0xffffu);
-                if (lane < npB) ((uint16_t*)(seg + oB))[lane] = (uint16_t)(ta >> 16);
-                if (lane < npC) ((uint16_t*)(seg + oC))[lane] = (uint16_t)(tb & 0xffffu);
-                if (lane < npD) ((uint16_t*)(seg + oD))[lane] = (uint16_t)(tb >> 16);
+                stg_u16_if(seg + oA + 2 * lane, ta & 0xffffu, lane, npA);
+                stg_u16_if(seg + oB + 2 * lane, ta >> 16, lane, npB);
+                stg_u16_if(seg + oC + 2 * lane, tb & 0xffffu, lane, npC);
+                stg_u16_if(seg + oD + 2 * lane, tb >> 16, lane, npD);
             }
-            if (lane == 0)
-                *(uint32_t*)(wb + 2 * r) = (uint32_t)width_byte(npA) | ((uint32_t)width_byte(npB) << 8) |
-                                           ((uint32_t)width_byte(npC) << 16) |
-                                           ((uint32_t)width_byte(npD) << 24);
+            wacc[r / 2] = (uint32_t)width_byte(npA) | ((uint32_t)width_byte(npB) << 8) |
+                          ((uint32_t)width_byte(npC) << 16) | ((uint32_t)width_byte(npD) << 24);
             lo += 2 * (npA + npB + npC + npD);
         } else if (L == 64) {
             int np;
@@ -600,13 +649,13 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                 const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
                 const unsigned m = __ballot_sync(FULL, t != 0u);
                 np = 32 - __clz((m & 0xffffu) | (m >> 16));
-                if (k < np) *(uint32_t*)(seg + lo + 8 * k + (hmask & 4)) = t;
+                stg_u32_if(seg + lo + 8 * k + (hmask & 4), t, k, np);
             } else {
                 const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
                 np = 32 - __clz(__ballot_sync(FULL, (ta | tb) != 0u));
-                if (lane < np) ((uint2*)(seg + lo))[lane] = make_uint2(ta, tb);
+                stg_u64_if(seg + lo + 8 * lane, ta, tb, lane, np);
             }
-            if (lane == 0) wb[r / 2] = width_byte(np);
+            wacc[0] |= (uint32_t)width_byte(np) << (8 * (r / 2));
             lo += 8 * np;
         } else {
             int np;
@@ -616,21 +665,25 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                 const uint32_t t1 = tpose(__byte_perm(u[r + 2], u[r + 3], 0x5410), tc);
                 const unsigned m = __ballot_sync(FULL, (t0 | t1) != 0u);
                 np = 32 - __clz((m & 0xffffu) | (m >> 16));
-                if (k < np) {
-                    uint8_t* pp = seg + lo + 16 * k + (hmask & 4);
-                    *(uint32_t*)pp = t0;
-                    *(uint32_t*)(pp + 8) = t1;
-                }
+                uint8_t* pp = seg + lo + 16 * k + (hmask & 4);
+                stg_u32_if(pp, t0, k, np);
+                stg_u32_if(pp + 8, t1, k, np);
             } else {
                 const uint32_t t0 = tpose(u[r], tc), t1 = tpose(u[r + 1], tc);
                 const uint32_t t2 = tpose(u[r + 2], tc), t3 = tpose(u[r + 3], tc);
                 np = 32 - __clz(__ballot_sync(FULL, (t0 | t1 | t2 | t3) != 0u));
-                if (lane < np) ((uint4*)(seg + lo))[lane] = make_uint4(t0, t1, t2, t3);
+                stg_u128_if(seg + lo + 16 * lane, t0, t1, t2, t3, lane, np);
             }
-            if (lane == 0) wb[r / 4] = width_byte(np);
+            wacc[0] |= (uint32_t)width_byte(np) << (8 * (r / 4));
             lo += 16 * np;
         }
     }
+    // one store of the group's width bytes (wb is 16-byte aligned per group
+    // at L = 16, 8 at L = 32, 4 at L = 64, 2 at L = 128)
+    if (L == 16) sts_if(wb, make_uint4(wacc[0], wacc[1], wacc[2], wacc[3]), lane == 0);
+    else if (L == 32) sts_if(wb, make_uint2(wacc[0], wacc[1]), lane == 0);
+    else if (L == 64) sts_if(wb, wacc[0], lane == 0);
+    else sts_if(wb, (unsigned short)wacc[0], lane == 0);
     return lo;
 }
 
