@@ -150,16 +150,19 @@ __device__ __forceinline__ int scan_incl(int v)
 // ---- prequantization ------------------------------------------------------
 // q = the integer nearest to x / two_eb, ties to even, exactly.
 // Fast path: v = x * inv rounds (at most two roundings) to within |v| 2^-22.9
-// of the exact quotient; if v is farther than |v| 2^-20 from a half-integer,
-// rint(v) is the exact answer.  rint uses the 1.5 * 2^23 magic add (exact for
-// |v| < 2^22; the fast test already fails for |v| >= 2^19).
+// of the exact quotient; if v is farther than |v| 2^-22 from a half-integer,
+// rint(v) is the exact answer.  The test f + |v| 2^-22 < 0.5 (f = |v - rint v|,
+// exact) is rounded once; its rounding error (at most 2^-26 near 0.5) stays
+// inside the factor-two margin for |v| > 1/8, and for |v| <= 1/8 both v and
+// the quotient round to 0.  rint uses the 1.5 * 2^23 magic add (exact for
+// |v| < 2^22; the fast test already fails for |v| >= 2^21).
 // Slow path (near a tie, large |v|, non-finite): q0 = rint(v), then the
 // residual r = x - q0 * two_eb, rounded once by an FMA, decides exactly
 // whether q0 or its neighbour is nearest (the residual is a multiple of
 // ulp(eb) near |r| = eb, so rounding cannot move it across eb).
 // Returns 0 or a zc_status code.
 // Branch-free fast path of quantize(): q = rint(x * inv); returns false when
-// that may differ from the exact rounding (near a tie, |v| >= 2^19, NaN/Inf).
+// that may differ from the exact rounding (near a tie, |v| >= 2^21, NaN/Inf).
 __device__ __forceinline__ bool quantize_fast(float x, float inv, int& q)
 {
     const float v = __fmul_rn(x, inv);
@@ -167,7 +170,7 @@ __device__ __forceinline__ bool quantize_fast(float x, float inv, int& q)
     const float r = __fsub_rn(t, 12582912.0f);
     const float f = fabsf(__fsub_rn(v, r));
     q = __float_as_int(t) - 0x4b400000;
-    return __fmaf_rn(fabsf(v), 9.5367431640625e-07f, f) < 0.5f;  // |v| * 2^-20
+    return __fmaf_rn(fabsf(v), 2.384185791015625e-07f, f) < 0.5f;  // |v| * 2^-22
 }
 
 __device__ __forceinline__ int quantize(float x, float eb, float two_eb, float inv, int& q)
@@ -176,7 +179,7 @@ __device__ __forceinline__ int quantize(float x, float eb, float two_eb, float i
     const float t = __fadd_rn(v, 12582912.0f);
     const float r = __fsub_rn(t, 12582912.0f);
     const float f = fabsf(__fsub_rn(v, r));
-    if (__fmaf_rn(fabsf(v), 9.5367431640625e-07f, f) < 0.5f) {  // |v| * 2^-20
+    if (__fmaf_rn(fabsf(v), 2.384185791015625e-07f, f) < 0.5f) {  // |v| * 2^-22
         q = __float_as_int(t) - 0x4b400000;
         return 0;
     }

@@ -151,6 +151,33 @@ def test_quantizer_ties_and_near_ties(zc):
         assert s == oracle.compress(x, eb, int(math.log2(block)))
 
 
+def test_quantizer_fast_path_edge(zc):
+    """The fast rounding is trusted only where v = x * inv lies farther than
+    |v| 2^-22 from a half-integer: that is about 2 ulp of v.  Values 1 to 8
+    ulp on both sides of ties, at magnitudes from 1/8 to 2^21 (where the fast
+    test switches off), under three bounds: the GPU must round every one of
+    them exactly like the oracle."""
+    g = np.random.default_rng(7)
+    for eb in (1e-3, 3.7e-5, 0.25):
+        eb_f, two = oracle.qparams(eb)
+        k = np.concatenate([g.integers(-8, 8, 200), g.integers(-4096, 4096, 1500),
+                            g.integers(-(1 << 21), 1 << 21, 1500),
+                            np.array([(1 << 21) - 1, (1 << 21), -(1 << 21), (1 << 20) + 7])])
+        ties = ((k + 0.5) * np.float64(two)).astype(np.float32)
+        parts = [ties]
+        for direction in (np.float32(np.inf), np.float32(-np.inf)):
+            y = ties.copy()
+            for _ in range(8):
+                y = np.nextafter(y, direction)
+                parts.append(y.copy())
+        x = np.concatenate(parts)
+        x = x[np.abs(x.astype(np.float64) / np.float64(two)) < (1 << 22) - 1]
+        for block in (16, 32):
+            s, st = gpu_compress(zc, torch.from_numpy(x), eb, block)
+            assert st[0] == 0
+            assert s == oracle.compress(x, eb, int(math.log2(block))), (eb, block)
+
+
 def test_relative_bound(zc):
     from paper_2308_05199_gb300 import workloads
     x = workloads.grf_3d(side=48, seed=2000, device="cuda")
