@@ -96,8 +96,8 @@ size_t zc_raw_stream_bytes(uint64_t n, int dtype);
  * `n_items` items (1 for single calls, P for batched ring steps and scatter
  * packs, M for batched compression).  Host-side arithmetic only.  Besides the
  * look-back records it holds the encoder CTAs' tile rings (staged payload of
- * the tiles in flight, about 300 KB per CTA, up to 608 CTAs: at most 187 MB);
- * a smaller workspace still works, with fewer encoder CTAs. */
+ * the tiles in flight, at most 200 KB per CTA, up to 608 CTAs: at most
+ * 124.5 MB); a smaller workspace still works, with fewer encoder CTAs. */
 size_t zc_workspace_bytes(uint64_t n_total, int n_items);
 
 /* Zero the workspace (cudaMemsetAsync) and stamp it as initialised.  Call
@@ -436,7 +436,7 @@ void zc_graph_destroy(zc_graph g);
  * all device memory through its own allocator has no way to obtain a
  * workspace.  This variant of zc_compress takes no workspace: its scratch
  * (look-back records, range partials, status word, the encoder's tile rings)
- * is one fixed 24 MiB device array inside this library, present on every GPU
+ * is one fixed 32 MiB device array inside this library, present on every GPU
  * that loads the library until the process exits; its rings allow about one
  * encoder CTA per SM.  It allocates nothing and calls no allocating
  * routine.

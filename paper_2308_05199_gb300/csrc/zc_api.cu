@@ -68,13 +68,15 @@ int qparams(double eb_abs, float* eb, float* two, float* inv)
 // encoder CTAs' tile rings: ring_ctas(cap) rings of the largest tile size.
 constexpr uint64_t WS_ARRAYS = 9;
 constexpr uint64_t RING_CTAS_MAX = 152 * ENC_CTAS_PER_SM;  // every resident encoder CTA
-constexpr uint64_t RING_UNIT = ring_cta_bytes(unit_rows(16));
+constexpr uint64_t RING_UNIT = ring_cta_bytes(unit_rows(16));  // the largest ring of any tile size
+static_assert(RING_UNIT >= ring_cta_bytes(unit_rows(8)) && RING_UNIT >= ring_cta_bytes(unit_rows(4)), "ring unit");
 
-// Rings for a workspace of `cap` array entries: one per 32 entries (a tile
-// of 16 chunks needs 32 entries of decode slots), at least one.
+// Rings (of the largest tile size) for a workspace of `cap` array entries:
+// one per 16 entries (a tile of 8 chunks needs 16 entries of decode slots),
+// at least one.
 inline uint64_t ring_ctas(uint64_t cap)
 {
-    const uint64_t r = (cap + 31) / 32;
+    const uint64_t r = (cap + 15) / 16;
     return r < 1 ? 1 : (r > RING_CTAS_MAX ? RING_CTAS_MAX : r);
 }
 inline uint64_t ring_offset(uint64_t cap)

@@ -92,34 +92,36 @@ struct Smem {
     float eb, two_eb, inv;
 };
 
-// Encoder CTAs: NWARPS encoder warps plus one resolver warp, ENC_SLOTS tiles
-// in flight.  Every tile slot has, per encoder warp, a payload segment of
-// seg_bytes(U) in the CTA's ring (global memory) and U * 2 width bytes in
-// shared memory.
-constexpr int ENC_SLOTS = 3;
+// Encoder CTAs: NWARPS encoder warps plus one resolver warp, enc_slots(U)
+// tiles in flight.  Every tile slot has, per encoder warp, a payload segment
+// of seg_bytes(U) in the CTA's ring (global memory) and U * 2 width bytes in
+// shared memory.  Three slots give the resolver two tiles' time; the largest
+// tiles take two, which keeps the rings of all CTAs inside L2.
+__host__ __device__ constexpr int enc_slots(int U) { return U >= 128 ? 2 : 3; }
+constexpr int ENC_SLOTS_MAX = 3;
 constexpr int ENC_THREADS = NTHREADS + 32;
 constexpr int ENC_CTAS_PER_SM = 4;            // resident encoder CTAs per SM (registers)
 constexpr unsigned BAR_ENCW = 1;              // named barrier: the encoder warps
 constexpr unsigned BAR_ENC = 2;               // + slot: tile encoded (resolver waits)
-constexpr unsigned BAR_RES = BAR_ENC + ENC_SLOTS;  // + slot: tile resolved (encoders wait)
-static_assert(BAR_RES + ENC_SLOTS <= 16, "named barriers per CTA");
+constexpr unsigned BAR_RES = BAR_ENC + ENC_SLOTS_MAX;  // + slot: tile resolved (encoders wait)
+static_assert(BAR_RES + ENC_SLOTS_MAX <= 16, "named barriers per CTA");
 __host__ __device__ constexpr unsigned long long ring_cta_bytes(int U)
 {
-    return (unsigned long long)ENC_SLOTS * NWARPS * seg_bytes(U);
+    return (unsigned long long)enc_slots(U) * NWARPS * seg_bytes(U);
 }
-__host__ __device__ constexpr int enc_smem_bytes(int U) { return ENC_SLOTS * NWARPS * U * 2; }
+__host__ __device__ constexpr int enc_smem_bytes(int U) { return enc_slots(U) * NWARPS * U * 2; }
 
 template <typename T>
 __device__ __forceinline__ float load_x(const T* p, int i);
 template <>
 __device__ __forceinline__ float load_x<float>(const float* p, int i)
 {
-    return __ldg(p + i);
+    return __ldcs(p + i);  // read once: evict first, the tile rings stay in L2
 }
 template <>
 __device__ __forceinline__ float load_x<uint16_t>(const uint16_t* p, int i)
 {
-    return bf16_to_f32(__ldg((const unsigned short*)p + i));
+    return bf16_to_f32(__ldcs((const unsigned short*)p + i));
 }
 
 __device__ __forceinline__ void store_raw(void* p, int dtype, unsigned long long i, float v)
@@ -690,16 +692,19 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
 // ---- encoder tiles -------------------------------------------------------------
 // An encoder CTA runs two kinds of warps.  Its NWARPS encoder warps take tiles
 // in ticket order and encode each of the tile's warp units into the CTA's ring
-// (global memory, ENC_SLOTS tiles deep) and its width bytes into shared
+// (global memory, enc_slots(U) tiles deep) and its width bytes into shared
 // memory.  Its resolver warp takes every encoded tile, sums the units' sizes,
 // runs the tile's look-back (and, for packed streams, the stream-start wait)
-// and hands the tile's place in the output back.  ENC_SLOTS - 1 tiles later
+// and hands the tile's place in the output back.  enc_slots(U) - 1 tiles later
 // the encoder warps copy the tile from the ring to the stream.  So the encoder
 // warps never stop for a look-back: the wait for the tiles before this one
 // overlaps the encoding of the tiles after it.
 
 // Copies `len` bytes (a multiple of UNIT) from the ring (16-byte aligned) to
-// `dst` (UNIT-aligned) with one warp; four loads per lane are in flight.
+// `dst` (UNIT-aligned) with one warp; four loads per lane are in flight.  The
+// staged bytes are dead afterwards: their L2 lines (the segment owns whole
+// 128-byte lines) are dropped without a write-back, so the ring costs no DRAM
+// traffic as long as a tile's lines stay in L2 until it is stored.
 template <int UNIT>
 __device__ __forceinline__ void ring_copy(uint8_t* dst, const uint8_t* src, int len)
 {
@@ -715,14 +720,18 @@ __device__ __forceinline__ void ring_copy(uint8_t* dst, const uint8_t* src, int 
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int i = b + k * 32 + lane;
-            if (i < cnt) v[k] = __ldcg((const T*)src + i);
+            if (i < cnt) v[k] = __ldcs((const T*)src + i);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int i = b + k * 32 + lane;
-            if (i < cnt) ((T*)dst)[i] = v[k];
+            if (i < cnt) __stcs((T*)dst + i, v[k]);
         }
     }
+    __syncwarp();
+    for (int l = lane; l < (len + 127) >> 7; l += 32)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(__cvta_generic_to_global(src + 128 * l))
+                     : "memory");
 }
 
 // Packed mode (one chain through many streams): the first tile of a stream
@@ -1150,14 +1159,15 @@ __device__ __forceinline__ void resolve_slot(const Launch& P, TileSlot& S, unsig
 //   fin(item, index, tile in item, ticket, slot, segment, width bytes)
 // Barrier protocol per tile in slot s: the encoder warps arrive on BAR_ENC + s
 // after encoding it, the resolver waits there, resolves it and arrives on
-// BAR_RES + s, where the encoder warps wait ENC_SLOTS - 1 tiles later before
+// BAR_RES + s, where the encoder warps wait NS - 1 tiles later before
 // storing it.  A slot's barriers are used again only after both sides have
 // passed them, and every path through the loops meets every barrier.
 template <int U, typename Src, typename Enc, typename Fin>
 __device__ __forceinline__ void enc_pipeline(const Launch& P, const Src& src, Enc enc, Fin fin)
 {
-    constexpr int D = ENC_SLOTS - 1;  // tiles between a tile's encoding and its stores
-    __shared__ TileSlot slots[ENC_SLOTS];
+    constexpr int NS = enc_slots(U);  // tiles in flight
+    constexpr int D = NS - 1;         // tiles between a tile's encoding and its stores
+    __shared__ TileSlot slots[NS];
     __shared__ EncShared es;
     extern __shared__ __align__(16) uint8_t dsm[];  // width bytes [slot][warp][2U]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1216,11 +1226,11 @@ __device__ __forceinline__ void enc_pipeline(const Launch& P, const Src& src, En
             bar_arrive_n(BAR_ENC + s, ENC_THREADS);
             if (!valid) {
                 // the tiles still waiting for their stores, oldest first
-                for (int k = (i < D ? i : D) - 1; k >= 0; --k) store((s + ENC_SLOTS - 1 - k) % ENC_SLOTS);
+                for (int k = (i < D ? i : D) - 1; k >= 0; --k) store((s + NS - 1 - k) % NS);
                 break;
             }
-            if (i >= D) store((s + 1) % ENC_SLOTS);
-            s = s + 1 == ENC_SLOTS ? 0 : s + 1;
+            if (i >= D) store((s + 1) % NS);
+            s = s + 1 == NS ? 0 : s + 1;
         }
     } else {
         int s = 0;
@@ -1231,7 +1241,7 @@ __device__ __forceinline__ void enc_pipeline(const Launch& P, const Src& src, En
             resolve_slot(P, S, E);
             __syncwarp();
             bar_arrive_n(BAR_RES + s, ENC_THREADS);
-            s = s + 1 == ENC_SLOTS ? 0 : s + 1;
+            s = s + 1 == NS ? 0 : s + 1;
         }
     }
     __syncthreads();

@@ -16,7 +16,7 @@
 namespace {
 
 constexpr uint64_t NOALLOC_MAX_N = ZC_NOALLOC_MAX_N;
-constexpr size_t NOALLOC_BYTES = 24u << 20;  // 24 MiB on every GPU that loads the library
+constexpr size_t NOALLOC_BYTES = 32u << 20;  // 32 MiB on every GPU that loads the library
 constexpr int MAX_DEVICES = 64;
 
 std::mutex g_mutex;

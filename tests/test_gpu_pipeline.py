@@ -1,7 +1,7 @@
 """The encoder's tile pipeline at its limits (needs a GB300).
 
 Every encoder CTA stages its tiles in a ring of its own inside the workspace
-and stores each tile ENC_SLOTS - 1 tiles after encoding it, once its resolver
+and stores each tile one or two tiles after encoding it, once its resolver
 warp has placed it in the chain.  The grid is bounded by the rings the
 workspace holds, so a small workspace runs few CTAs, each through many tiles:
 every stream must still be byte-identical to the oracle's.  The same holds for
@@ -45,7 +45,7 @@ def small_workspace(zc, n_small):
 @pytest.mark.parametrize("chunks,n_small,n", [(8, 40000, 600001), (16, 1, 300001),
                                               (4, 1, 140001)])
 def test_ring_limited_grid_streams_match_oracle(zc, chunks, n_small, n):
-    """Workspaces whose rings allow 1 to 4 CTAs: 10 to 37 tiles per launch go
+    """Workspaces whose rings allow 2 to 5 CTAs: 10 to 37 tiles per launch go
     through the same few CTAs."""
     zc.zc_set_tile_chunks(chunks)
     try:
@@ -93,7 +93,7 @@ def test_batch_with_one_cta(zc, chunks):
 
 def test_ring_step_with_few_ctas(zc):
     """The fused decode + add + encode step with 16-chunk tiles on a workspace
-    that holds the input's decode slots but rings for only 8 CTAs (31 tiles):
+    that holds the input's decode slots but rings for only 16 CTAs (31 tiles):
     stream and FP32 sum equal the oracle's step."""
     n = 1000001
     a = W.student_t3(n, 0.02, 7).cuda()
@@ -103,7 +103,7 @@ def test_ring_step_with_few_ctas(zc):
     s_in = zc.stream_bytes(cin, cb)
     zc.zc_set_tile_chunks(16)
     try:
-        ws = zc.Workspace(235520, 1)  # 248 decode slots, 8 rings
+        ws = zc.Workspace(235520, 1)  # 248 decode slots, 16 rings
         out, ob, total = zc.reduce_step(cin, b, eb, 32, want_sum=True, ws=ws)
         assert ws.status()[0] == 0, ws.status()
     finally:

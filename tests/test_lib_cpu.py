@@ -63,9 +63,9 @@ def test_sizing_matches_format(lib):
     assert 0 < a < b < c and a % 256 == 0
     # one record set (8 u64) per 2048-element decode tile
     assert b >= 8 * 8 * ((1 << 27) // 2048)
-    # the encoder CTAs' tile rings: about 300 KB per 32 entries of a small
-    # workspace, at most 608 CTAs' worth (187 MB) in a large one
-    ring = 3 * 8 * 100 * 128
+    # the encoder CTAs' tile rings: 200 KB per 16 entries of a small
+    # workspace, at most 608 CTAs' worth (124.5 MB) in a large one
+    ring = 2 * 8 * 100 * 128
     assert a >= 8 * 8 * ((1 << 20) // 2048) + ring
     assert lib.zc_workspace_bytes(1 << 34, 1) - lib.zc_workspace_bytes(1 << 33, 1) < 9 * 8 * (1 << 24)
     assert b >= 608 * ring
