@@ -840,7 +840,22 @@ __device__ __forceinline__ int enc_tile(const Launch& P, const Item& it, unsigne
     const TpC tc = tp_consts(lane);
     int err = 0;
     int lo = 0;
-    if (ue0 < n) {
+    if (!HAS_CIN && do_enc && it.x != nullptr && ue0 + U * 32 <= n) {
+        // a whole unit (every unit but the last of a stream): no tails, and
+        // few live values, so the group loop stays in registers
+        const TX* const xb = (const TX*)it.x + ue0 + lane;
+#pragma unroll 1
+        for (int gi = 0; gi < U / GR; ++gi) {
+            float acc[GR];
+#pragma unroll
+            for (int r = 0; r < GR; ++r) acc[r] = load_x<TX>(xb, gi * GR * 32 + r * 32);
+            const int b0 = L >= 32 ? gi * GR / (L / 32) : gi * GR * 2;
+            uint8_t* hout = nullptr;
+            if (HEADS) hout = it.out + 32 + wbytes + 3ull * ((ue0 >> LOG2L) + b0);
+            lo = encode_group<LOG2L, true, HEADS>(acc, GR * 32, eb, two_eb, inv, seg, lo, wb + b0,
+                                                  err, tc, hout);
+        }
+    } else if (ue0 < n) {
         const uint8_t* src = nullptr;
         int2* meta = nullptr;
         bool narrow = false;
