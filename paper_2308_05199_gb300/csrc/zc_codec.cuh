@@ -840,15 +840,38 @@ __device__ __forceinline__ int enc_tile(const Launch& P, const Item& it, unsigne
     const TpC tc = tp_consts(lane);
     int err = 0;
     int lo = 0;
-    if (!HAS_CIN && do_enc && it.x != nullptr && ue0 + U * 32 <= n) {
+    if (do_enc && it.x != nullptr && ue0 + U * 32 <= n) {
         // a whole unit (every unit but the last of a stream): no tails, and
         // few live values, so the group loop stays in registers
         const TX* const xb = (const TX*)it.x + ue0 + lane;
+        const uint8_t* src = nullptr;
+        int2* meta = nullptr;
+        bool narrow = false;
+        if constexpr (HAS_CIN) {
+            __shared__ __align__(16) int2 meta_full[NWARPS][BU];
+            meta = meta_full[warp];
+            if (do_cin)
+                src = it.cin + unit_meta<LOG2L, U>(P, it, S.g * NWARPS + warp, ue0, meta, narrow);
+        }
 #pragma unroll 1
         for (int gi = 0; gi < U / GR; ++gi) {
             float acc[GR];
 #pragma unroll
             for (int r = 0; r < GR; ++r) acc[r] = load_x<TX>(xb, gi * GR * 32 + r * 32);
+            if constexpr (HAS_CIN) {
+                if (do_cin) {
+                    float dv[GR];
+                    if (narrow) decode_group<LOG2L, true>(src, meta, gi, two_eb_in, dv, tc);
+                    else decode_group<LOG2L, false>(src, meta, gi, two_eb_in, dv, tc);
+#pragma unroll
+                    for (int r = 0; r < GR; ++r) acc[r] = __fadd_rn(dv[r], acc[r]);
+                }
+                if (it.raw_out != nullptr) {
+                    float* op = (float*)it.raw_out + ue0 + gi * GR * 32 + lane;
+#pragma unroll
+                    for (int r = 0; r < GR; ++r) op[r * 32] = acc[r];
+                }
+            }
             const int b0 = L >= 32 ? gi * GR / (L / 32) : gi * GR * 2;
             uint8_t* hout = nullptr;
             if (HEADS) hout = it.out + 32 + wbytes + 3ull * ((ue0 >> LOG2L) + b0);
@@ -973,10 +996,15 @@ __device__ __forceinline__ void fin_tile(const Launch& P, const Item& it, unsign
     }
     {
         const unsigned long long b0 = ue0 >> LOG2L;
-        for (int i = lane; i < BU; i += 32) {
-            const unsigned long long b = b0 + i;
-            const unsigned long long pos = start + 32 + b;
-            if (b < nb && pos < cap) out[pos] = wb[i];
+        const unsigned long long pos0 = start + 32 + b0;  // 16-byte aligned when BU is
+        if (BU % 16 == 0 && b0 + BU <= nb && pos0 + BU <= cap) {
+            if (lane < BU / 16) ((uint4*)(out + pos0))[lane] = ((const uint4*)wb)[lane];
+        } else {
+            for (int i = lane; i < BU; i += 32) {
+                const unsigned long long b = b0 + i;
+                const unsigned long long pos = pos0 + i;
+                if (b < nb && pos < cap) out[pos] = wb[i];
+            }
         }
     }
     if (S.last) {
