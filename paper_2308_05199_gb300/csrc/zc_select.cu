@@ -59,16 +59,25 @@ __device__ __forceinline__ unsigned stat_span(const float xs[4], int cnt, const 
     const int lane = threadIdx.x & 31;
     int q[4], d[4], pd[4];
     bool v[4];
+    // the exact quantizer: the fast rounding for all four rows, the exact slow
+    // path only when some lane's fast result may be off (one vote)
+    bool slow = false;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int i = 32 * r + lane;
         v[r] = i < cnt;
-        int qq = 0;
-        if (v[r] && quantize(xs[r], it.eb, it.two_eb, it.inv, qq) != 0) {
-            A.bad = 1;
-            qq = 0;
+        slow |= !quantize_fast(v[r] ? xs[r] : 0.0f, it.inv, q[r]);
+    }
+    if (__any_sync(FULL, slow)) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int qq = 0;
+            if (v[r] && quantize(xs[r], it.eb, it.two_eb, it.inv, qq) != 0) {
+                A.bad = 1;
+                qq = 0;
+            }
+            q[r] = qq;
         }
-        q[r] = qq;
     }
     // d_i = q_i - q_{i-1}, and d_{i-1} (for the second differences)
 #pragma unroll
@@ -131,7 +140,7 @@ __device__ __forceinline__ unsigned stat_span(const float xs[4], int cnt, const 
     return sb32;
 }
 
-__global__ void __launch_bounds__(256) k_chunk_stats(const Item* items, unsigned n_items,
+__global__ void __launch_bounds__(256, 4) k_chunk_stats(const Item* items, unsigned n_items,
                                                      float* feat)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
