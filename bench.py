@@ -218,48 +218,46 @@ class Workload:
         # map, batched compress); the ring adds its own
         self.launches_per_step = 12
 
-    def step(self, ev=None, waits=None):
-        """One pass of every row on the step's stream.  ev: 7 events recorded
-        between the rows; waits: events the stream waits for before the rows
-        that read the field (0), the ring's ranks (2), the messages (4) and the
-        held-out chunks (5) -- the end-to-end run's input copies."""
+    # the rows of one step, in step order: (name, input buffer index or None)
+    ROWS = ("compress", "decompress", "ring_allreduce", "scatter_pack", "batched_compress",
+            "selector_compress")
+
+    def run_row(self, k):
         zc, s, ws = self.zc, self.s, self.ws
+        if k == 0:
+            assert zc.zc_compress(self.field.data_ptr(), self.n, 0, zc.EB_REL, REL, BLOCK,
+                                  self.cmp.data_ptr(), self.cap, self.cmp_n.data_ptr(), ws.ptr,
+                                  ws.nbytes, s) == 0
+        elif k == 1:
+            assert zc.zc_decompress(self.cmp.data_ptr(), self.cap, self.dec.data_ptr(), self.n, 0,
+                                    ws.ptr, ws.nbytes, s) == 0
+        elif k == 2:
+            self.ring_row.ring.run()
+        elif k == 3:
+            assert zc.zc_scatter_pack(self.field.data_ptr(), 0, P_RING, self.hc, self.hd,
+                                      zc.EB_ABS, self.eb_abs, BLOCK, self.packed.data_ptr(),
+                                      self.pcap, self.seg.data_ptr(), ws.ptr, ws.nbytes, s) == 0
+        elif k == 4:
+            self.batch_row.graph.launch()
+        else:
+            self.sel_row.graph.launch()
+
+    def step(self, ev=None, waits=None, order=None):
+        """One pass of every row on the step's stream.  ev: 7 events, ev[0]
+        before the first row and ev[k + 1] after row k; waits: events the
+        stream waits for before row k (the end-to-end run's input copies);
+        order: the rows' order (step order by default; every row runs once,
+        decompression after compression)."""
         st = self.stream
         waits = waits or {}
-
-        def wait(row):
-            if row in waits:
-                st.wait_event(waits[row])
-
         if ev:
             ev[0].record(st)
-        wait(0)
-        assert zc.zc_compress(self.field.data_ptr(), self.n, 0, zc.EB_REL, REL, BLOCK,
-                              self.cmp.data_ptr(), self.cap, self.cmp_n.data_ptr(), ws.ptr,
-                              ws.nbytes, s) == 0
-        if ev:
-            ev[1].record(st)
-        assert zc.zc_decompress(self.cmp.data_ptr(), self.cap, self.dec.data_ptr(), self.n, 0,
-                                ws.ptr, ws.nbytes, s) == 0
-        if ev:
-            ev[2].record(st)
-        wait(2)
-        self.ring_row.ring.run()
-        if ev:
-            ev[3].record(st)
-        assert zc.zc_scatter_pack(self.field.data_ptr(), 0, P_RING, self.hc, self.hd, zc.EB_ABS,
-                                  self.eb_abs, BLOCK, self.packed.data_ptr(), self.pcap,
-                                  self.seg.data_ptr(), ws.ptr, ws.nbytes, s) == 0
-        if ev:
-            ev[4].record(st)
-        wait(4)
-        self.batch_row.graph.launch()
-        if ev:
-            ev[5].record(st)
-        wait(5)
-        self.sel_row.graph.launch()
-        if ev:
-            ev[6].record(st)
+        for k in (order or range(len(self.ROWS))):
+            if k in waits:
+                st.wait_event(waits[k])
+            self.run_row(k)
+            if ev:
+                ev[k + 1].record(st)
 
     def sizes(self):
         C = int(self.cmp_n.item())
@@ -868,9 +866,14 @@ def e2e_ours(torch, W, args, step_bytes, world):
     cs_in = torch.cuda.Stream(device=st.device)
     cs_out = torch.cuda.Stream(device=st.device)
     # every workload lives in one buffer per row: four copies in, three out
-    dev_in = [W.field, W.ring_row.buf, W.batch_row.buf, W.sel_row.buf]
-    rows_in = [0, 2, 4, 5]  # the row that first reads each input
+    # inputs in copy order; the rows run in the order their inputs arrive,
+    # the ring (no output to copy back) last, so the tail after the last
+    # input copy is one row's compute
+    dev_in = [W.field, W.batch_row.buf, W.sel_row.buf, W.ring_row.buf]
+    rows_in = [0, 4, 5, 2]  # the row that first reads each input
+    order = [0, 1, 3, 4, 5, 2]
     host_in = [t.cpu().pin_memory() for t in dev_in]
+    # outputs with the event recorded after the row that writes them
     outs = [(W.cmp, W.cmp_n[0:1], 1), (W.batch_row.b.packed, W.batch_row.b.msg_off[-1:], 5),
             (W.sel_row.cb.batch.packed, W.sel_row.cb.batch.msg_off[-1:], 6)]
     host_out = [torch.empty(o.numel(), dtype=torch.uint8).pin_memory() for o, _, _ in outs]
@@ -887,7 +890,7 @@ def e2e_ours(torch, W, args, step_bytes, world):
                 e.record(cs_in)
                 waits[row] = e
         ev = [torch.cuda.Event() for _ in range(7)]
-        W.step(ev, waits)
+        W.step(ev, waits, order)
         d2h = 0
         for i, (o, ln, row) in enumerate(outs):
             with torch.cuda.stream(cs_out):
