@@ -844,6 +844,15 @@ __device__ __forceinline__ int enc_tile(const Launch& P, const Item& it, unsigne
         // a whole unit (every unit but the last of a stream): no tails, and
         // few live values, so the group loop stays in registers
         const TX* const xb = (const TX*)it.x + ue0 + lane;
+        if (lane == 0) {
+            // the whole unit's input into L2 at once (16-byte aligned inner range)
+            const uintptr_t a0 = (uintptr_t)((const TX*)it.x + ue0), a1 = a0 + U * 32 * sizeof(TX);
+            const uintptr_t s0 = (a0 + 15) & ~(uintptr_t)15, s1 = a1 & ~(uintptr_t)15;
+            if (s1 > s0)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s0),
+                             "r"((unsigned)(s1 - s0))
+                             : "memory");
+        }
         const uint8_t* src = nullptr;
         int2* meta = nullptr;
         bool narrow = false;
