@@ -997,6 +997,63 @@ def cpu_fields(side):
     return x, ring, msgs, chunks
 
 
+def _oracle_piece(args):
+    """One core's share of the block-parallel oracle run: range, compress and
+    decompress of one field segment (its own stream, at the common bound; the
+    segment is read from shared memory, not copied), then the compression of
+    its messages.  Returns algorithmic bytes."""
+    shm_name, lo, hi, eb, msgs = args
+    import numpy as np
+    from multiprocessing import shared_memory
+    import oracle
+    shm = shared_memory.SharedMemory(name=shm_name)
+    try:
+        seg = np.ndarray((hi - lo,), dtype=np.float32, buffer=shm.buf, offset=4 * lo)
+        oracle.minmax(seg)
+        s = oracle.compress(seg, eb, 5)
+        oracle.decompress(s, seg.size)
+        n4 = 4 * seg.size
+        nbytes = (n4 + n4 + len(s)) + (len(s) + n4)
+        del seg
+    finally:
+        shm.close()
+    for a, e in msgs:
+        nbytes += a.nbytes + len(oracle.compress(a, e, 5))
+    return nbytes
+
+
+def cpu_parallel(x, msgs, sample_n):
+    """The oracle block-parallel over all host cores: the field sample split
+    into one segment per core (independent blocks, as in a scatter pack),
+    the messages dealt round-robin; one spawned process per core, the field
+    shared with them through shared memory."""
+    import multiprocessing as mp
+    import numpy as np
+    from multiprocessing import shared_memory
+    cores = os.cpu_count() or 1
+    xs = np.ascontiguousarray(x[:sample_n], dtype=np.float32)
+    eb = REL * float(xs.max() - xs.min())
+    m = (sample_n // cores) // 32 * 32
+    shm = shared_memory.SharedMemory(create=True, size=max(xs.nbytes, 4))
+    try:
+        np.ndarray(xs.shape, dtype=np.float32, buffer=shm.buf)[:] = xs
+        bounds = [(i * m, (i + 1) * m if i < cores - 1 else sample_n) for i in range(cores)]
+        parts = [(shm.name, lo, hi, eb, msgs[i::cores]) for i, (lo, hi) in enumerate(bounds)]
+        with mp.get_context("spawn").Pool(cores) as pool:
+            pool.map(_oracle_piece, [(shm.name, 0, min(1024, sample_n), eb, [])] * cores)  # start-up
+            t = time.perf_counter()
+            nbytes = sum(pool.map(_oracle_piece, parts))
+            secs = time.perf_counter() - t
+    finally:
+        shm.close()
+        shm.unlink()
+    return {"value": round(nbytes / secs / 1e9, 4), "unit": "GB/s", "cores": cores,
+            "sample": "first %d elements of the field (range, compress, decompress) in %d "
+                      "segments and the first %d messages, one spawned process per core"
+                      % (sample_n, cores, len(msgs)),
+            "seconds": round(secs, 2)}
+
+
 def cpu_baseline(side, sample_n=1 << 25):
     x, ring, msgs, chunks = cpu_fields(side)
     sample_n = min(sample_n, x.size)
@@ -1007,7 +1064,8 @@ def cpu_baseline(side, sample_n=1 << 25):
                       "512^2, the first %d of the "
                       "1000 messages, %d chunks of 64 KiB through the selector; single-threaded "
                       "plain C and numpy" % (sample_n, len(msgs), len(chunks)),
-            "seconds": round(secs, 2)}
+            "seconds": round(secs, 2),
+            "parallel": cpu_parallel(x, msgs, x.size)}
 
 
 def run_reference(args):
