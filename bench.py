@@ -145,6 +145,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
+
+
 # The sources the encoder kernels (k_compress, k_batch, k_reduce, k_scatter) are
 # built from: a DRAM-traffic figure taken with ncu stays valid while these are
 # unchanged.
@@ -816,6 +819,7 @@ def run_ours(args, rank, world):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(kern_gbs[dom], 1),
                 "peak": hbm, "unit": "GB/s", "frac": round(kern_gbs[dom] / hbm, 4),
                 "peak_kind": peak_kind,
+                "frac_of_nominal": round(kern_gbs[dom] / HBM_NOMINAL_GBS, 4),
                 "traffic": traffic["bytes_per_launch"] if traffic else None,
                 "algorithmic_bytes": parts[dom]}
     out = {
