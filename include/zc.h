@@ -474,8 +474,10 @@ void zc_debug_withhold_tile(int64_t tile);
 
 /* Tile size of the next encoder launches and plans: chunks of 2048 elements
  * per CTA tile (4, 8 or 16; default 8).  Larger tiles shorten the chain of
- * offsets between tiles and use more shared memory per CTA (6.6 KB per
- * chunk).  Returns ZC_ERR_ARG for other values.  Changes no stream byte. */
+ * offsets between tiles and stage more bytes per CTA in the workspace's tile
+ * rings (so the same workspace runs fewer CTAs of them); small inputs keep
+ * more CTAs busy with small tiles.  Returns ZC_ERR_ARG for other values.
+ * Changes no stream byte. */
 int zc_set_tile_chunks(int chunks);
 
 /* Library version string. */
