@@ -38,7 +38,7 @@
  *   [.., +pad16(P))               block payloads back to back, zero padded
  * where pad16(v) rounds v up to a multiple of 16.
  *
- * Heads apart (flag bit 1; SURVEY's "format v2"): the block head is stored in
+ * Heads apart (flag bit 1; the second format variant): the block head is stored in
  * its fixed 3-byte field and its own delta is taken as 0, so the width covers
  * only d_1 .. d_{L-1}.  Data on a large offset then costs 24 bits per block
  * instead of the offset's bit length on every element.
