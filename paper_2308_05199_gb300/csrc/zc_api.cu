@@ -575,7 +575,7 @@ int zc_scatter_pack(const void* d_in, int dtype, int P, const uint64_t* h_counts
     int st = ws_view(d_ws, ws_bytes, w);
     if (st) return st;
     const int C = g_chunks;
-    static ScatterParams SP;  // host staging of the by-value parameter block
+    thread_local static ScatterParams SP;  // host staging of the by-value parameter block
     uint64_t tile = 0, total_n = 0, min_cap = 0;
     std::vector<const void*> ptrs((size_t)P);
     std::vector<unsigned long long> cnts((size_t)P);
