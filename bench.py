@@ -615,6 +615,47 @@ def heads_report(torch, zc, W, reps=5):
     return out
 
 
+def bound_sweep(torch, zc, W, rels=(1e-2, 1e-3, 1e-4), reps=5):
+    """The 512^3 field at three relative bounds (range + compress, and
+    decompress, L = 32): ratio, GB/s (algorithmic bytes as the step's rows)
+    and the largest error over eb, checked on the device."""
+    st = W.stream
+    s = st.cuda_stream
+    n = W.n
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(f):
+        f()
+        e0, e1 = ev(), ev()
+        e0.record(st)
+        for _ in range(reps):
+            f()
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = []
+    lo, hi = float(W.field.min()), float(W.field.max())
+    for rel in rels:
+        c = lambda: zc._check(zc.zc_compress(W.field.data_ptr(), n, zc.F32, zc.EB_REL, rel, BLOCK,
+                                             W.cmp.data_ptr(), W.cap, W.cmp_n.data_ptr(), W.ws.ptr,
+                                             W.ws.nbytes, s), "compress")
+        tc = timed(c)
+        C = int(W.cmp_n.item())
+        d = lambda: zc._check(zc.zc_decompress(W.cmp.data_ptr(), W.cap, W.dec.data_ptr(), n, zc.F32,
+                                               W.ws.ptr, W.ws.nbytes, s), "decompress")
+        td = timed(d)
+        eb = float(torch.tensor(rel * (hi - lo), dtype=torch.float32))
+        with torch.cuda.stream(st):
+            err = float((W.dec - W.field).abs().max())
+        out.append({"rel": rel, "eb_abs": eb, "ratio": round(4 * n / C, 3),
+                    "compress_gbs": round((8 * n + C) / tc / 1e6, 1),
+                    "decompress_gbs": round((4 * n + C) / td / 1e6, 1),
+                    "max_err_over_eb": round(err / eb, 4)})
+    st.synchronize()
+    return {"status": W.ws.status()[0], "points": out}
+
+
 def size_sweep(torch, zc, workloads, stream, device, max_bytes=646 << 20, reps=5):
     """Compression / decompression time over message sizes (the paper's
     characterization of its GPU compressor, Sec. 3.2.2, on uniform synthetic
@@ -775,6 +816,7 @@ def run_ours(args, rank, world):
     selector = W.sel_row.report()
     sweep = size_sweep(torch, zc, workloads, W.stream, dev) if args.sweep else None
     heads = heads_report(torch, zc, W)
+    bounds = bound_sweep(torch, zc, W)
     coll = collectives_report(torch, workloads, W.stream, dev,
                               [int(v) for v in args.collective_ranks.split(",") if v],
                               args.ring_side) if args.collective_ranks else None
@@ -851,6 +893,7 @@ def run_ours(args, rank, world):
         "collectives": coll,
         "size_sweep": sweep,
         "heads_apart": heads,
+        "bound_sweep": bounds,
     }
     if not args.no_e2e:
         out["e2e"] = e2e_ours(torch, W, args, step_bytes, world)
