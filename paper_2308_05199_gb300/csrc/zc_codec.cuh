@@ -595,89 +595,135 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
     const uint32_t hmask = hi ? 0xffffffffu : 0u;
     // the group's width bytes, gathered in registers and stored once (GR * 32 / L bytes)
     uint32_t wacc[4] = {0u, 0u, 0u, 0u};
+    if (!any_wide) {
+        // every value of the group fits 16 bits (the common case): paired (or
+        // quadrupled) rows share a transpose, with no per-pair votes
 #pragma unroll
-    for (int r = 0; r < GR; r += (L == 128 ? 4 : 2)) {
-        if (L == 32) {
-            int fa, fb;  // highest nonzero plane of blocks r, r + 1 (-1: none)
-            if (!any_wide || !__any_sync(FULL, ((u[r] | u[r + 1]) >> 16) != 0u)) {
+        for (int r = 0; r < GR; r += (L == 128 ? 4 : 2)) {
+            if (L == 32) {
                 const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
                 const unsigned m = __ballot_sync(FULL, t != 0u);
-                fa = 31 - __clz(m & 0xffffu);
-                fb = 31 - __clz(m >> 16);
-                const int npm = hi ? fb + 1 : fa + 1;
-                stg_u32_if(seg + lo + (hmask & (4 * fa + 4)) + 4 * k, t, k, npm);
-            } else {
-                const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
-                fa = 31 - __clz(__ballot_sync(FULL, ta != 0u));
-                fb = 31 - __clz(__ballot_sync(FULL, tb != 0u));
-                stg_u32_if(seg + lo + 4 * lane, ta, lane, fa + 1);
-                stg_u32_if(seg + lo + 4 * fa + 4 + 4 * lane, tb, lane, fb + 1);
-            }
-            wacc[r / 4] |= ((uint32_t)max(fa, 0) | ((uint32_t)max(fb, 0) << 8)) << (8 * (r % 4));
-            lo += 4 * (fa + fb + 2);
-        } else if (L == 16) {
-            int npA, npB, npC, npD;
-            if (!any_wide || !__any_sync(FULL, ((u[r] | u[r + 1]) >> 16) != 0u)) {
+                const int na = 32 - __clz(m & 0xffffu), nb = 32 - __clz(m >> 16);
+                stg_u32_if(seg + 4 * k + lo + (hmask & (4 * na)), t, k, hi ? nb : na);
+                wacc[r / 4] |= ((uint32_t)max(na - 1, 0) | ((uint32_t)max(nb - 1, 0) << 8))
+                               << (8 * (r % 4));
+                lo += 4 * (na + nb);
+            } else if (L == 16) {
                 const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
                 const unsigned m0 = __ballot_sync(FULL, (t & 0xffffu) != 0u);
                 const unsigned m1 = __ballot_sync(FULL, (t >> 16) != 0u);
-                npA = 32 - __clz(m0 & 0xffffu);
-                npB = 32 - __clz(m1 & 0xffffu);
-                npC = 32 - __clz(m0 >> 16);
-                npD = 32 - __clz(m1 >> 16);
+                const int npA = 32 - __clz(m0 & 0xffffu), npB = 32 - __clz(m1 & 0xffffu);
+                const int npC = 32 - __clz(m0 >> 16), npD = 32 - __clz(m1 >> 16);
                 const int oA = lo, oB = oA + 2 * npA, oC = oB + 2 * npB, oD = oC + 2 * npC;
-                const int npL = hi ? npC : npA, npH = hi ? npD : npB;
-                const int offL = hi ? oC : oA, offH = hi ? oD : oB;
-                stg_u16_if(seg + offL + 2 * k, t & 0xffffu, k, npL);
-                stg_u16_if(seg + offH + 2 * k, t >> 16, k, npH);
-            } else {
-                const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
-                npA = 32 - __clz(__ballot_sync(FULL, (ta & 0xffffu) != 0u));
-                npB = 32 - __clz(__ballot_sync(FULL, (ta >> 16) != 0u));
-                npC = 32 - __clz(__ballot_sync(FULL, (tb & 0xffffu) != 0u));
-                npD = 32 - __clz(__ballot_sync(FULL, (tb >> 16) != 0u));
-                const int oA = lo, oB = oA + 2 * npA, oC = oB + 2 * npB, oD = oC + 2 * npC;
-                stg_u16_if(seg + oA + 2 * lane, ta & 0xffffu, lane, npA);
-                stg_u16_if(seg + oB + 2 * lane, ta >> 16, lane, npB);
-                stg_u16_if(seg + oC + 2 * lane, tb & 0xffffu, lane, npC);
-                stg_u16_if(seg + oD + 2 * lane, tb >> 16, lane, npD);
-            }
-            wacc[r / 2] = (uint32_t)width_byte(npA) | ((uint32_t)width_byte(npB) << 8) |
-                          ((uint32_t)width_byte(npC) << 16) | ((uint32_t)width_byte(npD) << 24);
-            lo += 2 * (npA + npB + npC + npD);
-        } else if (L == 64) {
-            int np;
-            if (!any_wide || !__any_sync(FULL, ((u[r] | u[r + 1]) >> 16) != 0u)) {
+                stg_u16_if(seg + (hi ? oC : oA) + 2 * k, t & 0xffffu, k, hi ? npC : npA);
+                stg_u16_if(seg + (hi ? oD : oB) + 2 * k, t >> 16, k, hi ? npD : npB);
+                wacc[r / 2] = (uint32_t)width_byte(npA) | ((uint32_t)width_byte(npB) << 8) |
+                              ((uint32_t)width_byte(npC) << 16) | ((uint32_t)width_byte(npD) << 24);
+                lo += 2 * (npA + npB + npC + npD);
+            } else if (L == 64) {
                 const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
                 const unsigned m = __ballot_sync(FULL, t != 0u);
-                np = 32 - __clz((m & 0xffffu) | (m >> 16));
+                const int np = 32 - __clz((m & 0xffffu) | (m >> 16));
                 stg_u32_if(seg + lo + 8 * k + (hmask & 4), t, k, np);
+                wacc[0] |= (uint32_t)width_byte(np) << (8 * (r / 2));
+                lo += 8 * np;
             } else {
-                const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
-                np = 32 - __clz(__ballot_sync(FULL, (ta | tb) != 0u));
-                stg_u64_if(seg + lo + 8 * lane, ta, tb, lane, np);
-            }
-            wacc[0] |= (uint32_t)width_byte(np) << (8 * (r / 2));
-            lo += 8 * np;
-        } else {
-            int np;
-            if (!any_wide ||
-                !__any_sync(FULL, ((u[r] | u[r + 1] | u[r + 2] | u[r + 3]) >> 16) != 0u)) {
                 const uint32_t t0 = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
                 const uint32_t t1 = tpose(__byte_perm(u[r + 2], u[r + 3], 0x5410), tc);
                 const unsigned m = __ballot_sync(FULL, (t0 | t1) != 0u);
-                np = 32 - __clz((m & 0xffffu) | (m >> 16));
+                const int np = 32 - __clz((m & 0xffffu) | (m >> 16));
                 uint8_t* pp = seg + lo + 16 * k + (hmask & 4);
                 stg_u32_if(pp, t0, k, np);
                 stg_u32_if(pp + 8, t1, k, np);
-            } else {
-                const uint32_t t0 = tpose(u[r], tc), t1 = tpose(u[r + 1], tc);
-                const uint32_t t2 = tpose(u[r + 2], tc), t3 = tpose(u[r + 3], tc);
-                np = 32 - __clz(__ballot_sync(FULL, (t0 | t1 | t2 | t3) != 0u));
-                stg_u128_if(seg + lo + 16 * lane, t0, t1, t2, t3, lane, np);
+                wacc[0] |= (uint32_t)width_byte(np) << (8 * (r / 4));
+                lo += 16 * np;
             }
-            wacc[0] |= (uint32_t)width_byte(np) << (8 * (r / 4));
-            lo += 16 * np;
+        }
+    } else {
+    #pragma unroll
+        for (int r = 0; r < GR; r += (L == 128 ? 4 : 2)) {
+            if (L == 32) {
+                int fa, fb;  // highest nonzero plane of blocks r, r + 1 (-1: none)
+                if (!any_wide || !__any_sync(FULL, ((u[r] | u[r + 1]) >> 16) != 0u)) {
+                    const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
+                    const unsigned m = __ballot_sync(FULL, t != 0u);
+                    fa = 31 - __clz(m & 0xffffu);
+                    fb = 31 - __clz(m >> 16);
+                    const int npm = hi ? fb + 1 : fa + 1;
+                    stg_u32_if(seg + lo + (hmask & (4 * fa + 4)) + 4 * k, t, k, npm);
+                } else {
+                    const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
+                    fa = 31 - __clz(__ballot_sync(FULL, ta != 0u));
+                    fb = 31 - __clz(__ballot_sync(FULL, tb != 0u));
+                    stg_u32_if(seg + lo + 4 * lane, ta, lane, fa + 1);
+                    stg_u32_if(seg + lo + 4 * fa + 4 + 4 * lane, tb, lane, fb + 1);
+                }
+                wacc[r / 4] |= ((uint32_t)max(fa, 0) | ((uint32_t)max(fb, 0) << 8)) << (8 * (r % 4));
+                lo += 4 * (fa + fb + 2);
+            } else if (L == 16) {
+                int npA, npB, npC, npD;
+                if (!any_wide || !__any_sync(FULL, ((u[r] | u[r + 1]) >> 16) != 0u)) {
+                    const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
+                    const unsigned m0 = __ballot_sync(FULL, (t & 0xffffu) != 0u);
+                    const unsigned m1 = __ballot_sync(FULL, (t >> 16) != 0u);
+                    npA = 32 - __clz(m0 & 0xffffu);
+                    npB = 32 - __clz(m1 & 0xffffu);
+                    npC = 32 - __clz(m0 >> 16);
+                    npD = 32 - __clz(m1 >> 16);
+                    const int oA = lo, oB = oA + 2 * npA, oC = oB + 2 * npB, oD = oC + 2 * npC;
+                    const int npL = hi ? npC : npA, npH = hi ? npD : npB;
+                    const int offL = hi ? oC : oA, offH = hi ? oD : oB;
+                    stg_u16_if(seg + offL + 2 * k, t & 0xffffu, k, npL);
+                    stg_u16_if(seg + offH + 2 * k, t >> 16, k, npH);
+                } else {
+                    const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
+                    npA = 32 - __clz(__ballot_sync(FULL, (ta & 0xffffu) != 0u));
+                    npB = 32 - __clz(__ballot_sync(FULL, (ta >> 16) != 0u));
+                    npC = 32 - __clz(__ballot_sync(FULL, (tb & 0xffffu) != 0u));
+                    npD = 32 - __clz(__ballot_sync(FULL, (tb >> 16) != 0u));
+                    const int oA = lo, oB = oA + 2 * npA, oC = oB + 2 * npB, oD = oC + 2 * npC;
+                    stg_u16_if(seg + oA + 2 * lane, ta & 0xffffu, lane, npA);
+                    stg_u16_if(seg + oB + 2 * lane, ta >> 16, lane, npB);
+                    stg_u16_if(seg + oC + 2 * lane, tb & 0xffffu, lane, npC);
+                    stg_u16_if(seg + oD + 2 * lane, tb >> 16, lane, npD);
+                }
+                wacc[r / 2] = (uint32_t)width_byte(npA) | ((uint32_t)width_byte(npB) << 8) |
+                              ((uint32_t)width_byte(npC) << 16) | ((uint32_t)width_byte(npD) << 24);
+                lo += 2 * (npA + npB + npC + npD);
+            } else if (L == 64) {
+                int np;
+                if (!any_wide || !__any_sync(FULL, ((u[r] | u[r + 1]) >> 16) != 0u)) {
+                    const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
+                    const unsigned m = __ballot_sync(FULL, t != 0u);
+                    np = 32 - __clz((m & 0xffffu) | (m >> 16));
+                    stg_u32_if(seg + lo + 8 * k + (hmask & 4), t, k, np);
+                } else {
+                    const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
+                    np = 32 - __clz(__ballot_sync(FULL, (ta | tb) != 0u));
+                    stg_u64_if(seg + lo + 8 * lane, ta, tb, lane, np);
+                }
+                wacc[0] |= (uint32_t)width_byte(np) << (8 * (r / 2));
+                lo += 8 * np;
+            } else {
+                int np;
+                if (!any_wide ||
+                    !__any_sync(FULL, ((u[r] | u[r + 1] | u[r + 2] | u[r + 3]) >> 16) != 0u)) {
+                    const uint32_t t0 = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
+                    const uint32_t t1 = tpose(__byte_perm(u[r + 2], u[r + 3], 0x5410), tc);
+                    const unsigned m = __ballot_sync(FULL, (t0 | t1) != 0u);
+                    np = 32 - __clz((m & 0xffffu) | (m >> 16));
+                    uint8_t* pp = seg + lo + 16 * k + (hmask & 4);
+                    stg_u32_if(pp, t0, k, np);
+                    stg_u32_if(pp + 8, t1, k, np);
+                } else {
+                    const uint32_t t0 = tpose(u[r], tc), t1 = tpose(u[r + 1], tc);
+                    const uint32_t t2 = tpose(u[r + 2], tc), t3 = tpose(u[r + 3], tc);
+                    np = 32 - __clz(__ballot_sync(FULL, (t0 | t1 | t2 | t3) != 0u));
+                    stg_u128_if(seg + lo + 16 * lane, t0, t1, t2, t3, lane, np);
+                }
+                wacc[0] |= (uint32_t)width_byte(np) << (8 * (r / 4));
+                lo += 16 * np;
+            }
         }
     }
     // one store of the group's width bytes (wb is 16-byte aligned per group
