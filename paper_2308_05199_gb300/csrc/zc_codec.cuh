@@ -545,17 +545,19 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
     const int lane = threadIdx.x & 31;
     const int k = lane & 15;
     const bool hi = lane >= 16;
-    // quantize: the exactness of the fast rounding is voted once per group
+    // quantize: the exactness of the fast rounding is voted once per group.
+    // q holds q + QBIAS (the rounded float's bits): the deltas are the same
     int q[GR];
     {
         bool slow = false;
 #pragma unroll
-        for (int r = 0; r < GR; ++r) slow |= !quantize_fast(acc[r], inv, q[r]);
+        for (int r = 0; r < GR; ++r) slow |= !quantize_fast_bits(acc[r], inv, q[r]);
         if (__any_sync(FULL, slow)) {
 #pragma unroll
             for (int r = 0; r < GR; ++r) {
-                q[r] = 0;
-                if (ALL || r * 32 + lane < nrem) err |= quantize(acc[r], eb, two_eb, inv, q[r]);
+                int qq = 0;
+                if (ALL || r * 32 + lane < nrem) err |= quantize(acc[r], eb, two_eb, inv, qq);
+                q[r] = qq + QBIAS;
             }
         }
     }
@@ -564,7 +566,7 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
     int carry = 0;
 #pragma unroll
     for (int r = 0; r < GR; ++r) {
-        const int fill = (L >= 64 && (r % RPB) != 0) ? carry : 0;
+        const int fill = (L >= 64 && (r % RPB) != 0) ? carry : QBIAS;  // a block starts from q = 0
         const int prev = prev_lane<L == 16 ? 16 : 32>(q[r], fill);
         if (L >= 64 && (r % RPB) != RPB - 1) carry = __shfl_sync(FULL, q[r], 31);
         int d = q[r] - prev;
@@ -578,10 +580,11 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
             else if (L >= 64 && lane == 0 && (r % RPB) == 0) b = r / RPB;
             if (b >= 0) {
                 if (ALL || r * 32 + lane < nrem) {
+                    const int head = q[r] - QBIAS;
                     uint8_t* p = hout + 3 * b;
-                    p[0] = (uint8_t)q[r];
-                    p[1] = (uint8_t)(q[r] >> 8);
-                    p[2] = (uint8_t)(q[r] >> 16);
+                    p[0] = (uint8_t)head;
+                    p[1] = (uint8_t)(head >> 8);
+                    p[2] = (uint8_t)(head >> 16);
                 }
                 d = 0;
             }

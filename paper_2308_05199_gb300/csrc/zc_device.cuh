@@ -173,6 +173,20 @@ __device__ __forceinline__ bool quantize_fast(float x, float inv, int& q)
     return __fmaf_rn(fabsf(v), 2.384185791015625e-07f, f) < 0.5f;  // |v| * 2^-22
 }
 
+// The same, returning the bit pattern of the rounded float (q + QBIAS):
+// differences of two such values are differences of q, so an encoder that
+// only needs deltas skips the offset.
+constexpr int QBIAS = 0x4b400000;  // the bits of 1.5 * 2^23, the rounding constant
+__device__ __forceinline__ bool quantize_fast_bits(float x, float inv, int& qb)
+{
+    const float v = __fmul_rn(x, inv);
+    const float t = __fadd_rn(v, 12582912.0f);
+    const float r = __fsub_rn(t, 12582912.0f);
+    const float f = fabsf(__fsub_rn(v, r));
+    qb = __float_as_int(t);
+    return __fmaf_rn(fabsf(v), 2.384185791015625e-07f, f) < 0.5f;  // |v| * 2^-22
+}
+
 __device__ __forceinline__ int quantize(float x, float eb, float two_eb, float inv, int& q)
 {
     const float v = __fmul_rn(x, inv);
