@@ -109,7 +109,24 @@ __host__ __device__ constexpr unsigned long long ring_cta_bytes(int U)
 {
     return (unsigned long long)enc_slots(U) * NWARPS * seg_bytes(U);
 }
-__host__ __device__ constexpr int enc_smem_bytes(int U) { return enc_slots(U) * NWARPS * U * 2; }
+// Rows of a warp unit staged in shared memory before a copy to the ring: the
+// whole unit up to 64 rows for the single-stream kernels (compress, scatter
+// pack), 32 rows at a time otherwise (16-chunk tiles, the batch kernel with
+// its many code paths, the fused ring step whose decoder metadata also takes
+// shared memory), so that 4 CTAs fit an SM; the stage holds their worst case
+// plus the carried partial 16 bytes.
+__host__ __device__ constexpr int stage_rows(int U, bool single) { return (single && U <= 64) ? U : 32; }
+__host__ __device__ constexpr int stage_bytes(int rows) { return seg_bytes(rows) + 16; }
+// Dynamic shared memory of an encoder CTA: width bytes of every slot and
+// warp, then every encoder warp's stage.
+__host__ __device__ constexpr int enc_wb_bytes(int U) { return enc_slots(U) * NWARPS * U * 2; }
+// (The single-stream kernels take their stages in dynamic shared memory;
+// the others in a static array of 32-row stages, which leaves the driver
+// free to give the rest of the SM's memory to L1.)
+__host__ __device__ constexpr int enc_smem_bytes(int U, bool single = false)
+{
+    return enc_wb_bytes(U) + (single ? NWARPS * stage_bytes(stage_rows(U, true)) : 0);
+}
 
 template <typename T>
 __device__ __forceinline__ float load_x(const T* p, int i);
@@ -467,30 +484,29 @@ __device__ __forceinline__ void decode_group(const uint8_t* src, const int2* met
 
 // ---- encoding ------------------------------------------------------------------
 // Predicated stores without a branch: the store happens when a < b.  `p` is
-// a global address (the tile ring).
-__device__ __forceinline__ void stg_u32_if(uint8_t* p, uint32_t v, int a, int b)
+// a shared-memory address (the warp's staging buffer).
+__device__ __forceinline__ void sts_u32_if(unsigned p, uint32_t v, int a, int b)
 {
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.s32 q, %2, %3;\n\t@q st.global.u32 [%0], %1;\n\t}"
-                 ::"l"(__cvta_generic_to_global(p)), "r"(v), "r"(a), "r"(b) : "memory");
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.s32 q, %2, %3;\n\t@q st.shared.u32 [%0], %1;\n\t}"
+                 ::"r"(p), "r"(v), "r"(a), "r"(b) : "memory");
 }
-__device__ __forceinline__ void stg_u16_if(uint8_t* p, uint32_t v, int a, int b)
+__device__ __forceinline__ void sts_u16_if(unsigned p, uint32_t v, int a, int b)
 {
     asm volatile("{\n\t.reg .pred q;\n\t.reg .b16 h;\n\tcvt.u16.u32 h, %1;\n\t"
-                 "setp.lt.s32 q, %2, %3;\n\t@q st.global.u16 [%0], h;\n\t}"
-                 ::"l"(__cvta_generic_to_global(p)), "r"(v), "r"(a), "r"(b) : "memory");
+                 "setp.lt.s32 q, %2, %3;\n\t@q st.shared.u16 [%0], h;\n\t}"
+                 ::"r"(p), "r"(v), "r"(a), "r"(b) : "memory");
 }
-__device__ __forceinline__ void stg_u64_if(uint8_t* p, uint32_t v0, uint32_t v1, int a, int b)
+__device__ __forceinline__ void sts_u64_if(unsigned p, uint32_t v0, uint32_t v1, int a, int b)
 {
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.s32 q, %3, %4;\n\t@q st.global.v2.u32 [%0], {%1, %2};\n\t}"
-                 ::"l"(__cvta_generic_to_global(p)), "r"(v0), "r"(v1), "r"(a), "r"(b) : "memory");
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.s32 q, %3, %4;\n\t@q st.shared.v2.u32 [%0], {%1, %2};\n\t}"
+                 ::"r"(p), "r"(v0), "r"(v1), "r"(a), "r"(b) : "memory");
 }
-__device__ __forceinline__ void stg_u128_if(uint8_t* p, uint32_t v0, uint32_t v1, uint32_t v2,
+__device__ __forceinline__ void sts_u128_if(unsigned p, uint32_t v0, uint32_t v1, uint32_t v2,
                                             uint32_t v3, int a, int b)
 {
     asm volatile("{\n\t.reg .pred q;\n\tsetp.lt.s32 q, %5, %6;\n\t"
-                 "@q st.global.v4.u32 [%0], {%1, %2, %3, %4};\n\t}"
-                 ::"l"(__cvta_generic_to_global(p)), "r"(v0), "r"(v1), "r"(v2), "r"(v3), "r"(a),
-                 "r"(b) : "memory");
+                 "@q st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n\t}"
+                 ::"r"(p), "r"(v0), "r"(v1), "r"(v2), "r"(v3), "r"(a), "r"(b) : "memory");
 }
 // Predicated shared-memory stores of width bytes (`p` in shared memory).
 __device__ __forceinline__ void sts_if(uint8_t* p, uint4 v, bool c)
@@ -530,14 +546,14 @@ __device__ __forceinline__ int prev_lane(int q, int fill)
 
 // Quantizes, delta-codes and bit-plane packs GR rows (the first `nrem`
 // elements are valid, all of them when ALL; the rest are padding with zero
-// deltas), appends the planes of their blocks to the ring segment `seg` at
-// byte `lo` in stream order, writes their width bytes to `wb` (shared
-// memory, one store per group), ORs any quantizer error into `err`, and
-// returns the new `lo`.  Two rows whose values fit 16 bits share one
-// transpose.
+// deltas), appends the planes of their blocks at byte `lo` of the unit's
+// payload (shared-memory address seg + lo: the warp's staging buffer), writes
+// their width bytes to `wb` (shared memory, one store per group), ORs any
+// quantizer error into `err`, and returns the new `lo`.  Two rows whose
+// values fit 16 bits share one transpose.
 template <int LOG2L, bool ALL, bool HEADS = false>
 __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float eb, float two_eb,
-                                            float inv, uint8_t* seg, int lo, uint8_t* wb, int& err,
+                                            float inv, unsigned seg, int lo, uint8_t* wb, int& err,
                                             const TpC& tc, uint8_t* hout = nullptr)
 {
     constexpr int L = 1 << LOG2L;
@@ -607,7 +623,7 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                 const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
                 const unsigned m = __ballot_sync(FULL, t != 0u);
                 const int na = 32 - __clz(m & 0xffffu), nb = 32 - __clz(m >> 16);
-                stg_u32_if(seg + 4 * k + lo + (hmask & (4 * na)), t, k, hi ? nb : na);
+                sts_u32_if(seg + 4 * k + lo + (hmask & (4 * na)), t, k, hi ? nb : na);
                 wacc[r / 4] |= ((uint32_t)max(na - 1, 0) | ((uint32_t)max(nb - 1, 0) << 8))
                                << (8 * (r % 4));
                 lo += 4 * (na + nb);
@@ -618,8 +634,8 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                 const int npA = 32 - __clz(m0 & 0xffffu), npB = 32 - __clz(m1 & 0xffffu);
                 const int npC = 32 - __clz(m0 >> 16), npD = 32 - __clz(m1 >> 16);
                 const int oA = lo, oB = oA + 2 * npA, oC = oB + 2 * npB, oD = oC + 2 * npC;
-                stg_u16_if(seg + (hi ? oC : oA) + 2 * k, t & 0xffffu, k, hi ? npC : npA);
-                stg_u16_if(seg + (hi ? oD : oB) + 2 * k, t >> 16, k, hi ? npD : npB);
+                sts_u16_if(seg + (hi ? oC : oA) + 2 * k, t & 0xffffu, k, hi ? npC : npA);
+                sts_u16_if(seg + (hi ? oD : oB) + 2 * k, t >> 16, k, hi ? npD : npB);
                 wacc[r / 2] = (uint32_t)width_byte(npA) | ((uint32_t)width_byte(npB) << 8) |
                               ((uint32_t)width_byte(npC) << 16) | ((uint32_t)width_byte(npD) << 24);
                 lo += 2 * (npA + npB + npC + npD);
@@ -627,7 +643,7 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                 const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
                 const unsigned m = __ballot_sync(FULL, t != 0u);
                 const int np = 32 - __clz((m & 0xffffu) | (m >> 16));
-                stg_u32_if(seg + lo + 8 * k + (hmask & 4), t, k, np);
+                sts_u32_if(seg + lo + 8 * k + (hmask & 4), t, k, np);
                 wacc[0] |= (uint32_t)width_byte(np) << (8 * (r / 2));
                 lo += 8 * np;
             } else {
@@ -635,9 +651,9 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                 const uint32_t t1 = tpose(__byte_perm(u[r + 2], u[r + 3], 0x5410), tc);
                 const unsigned m = __ballot_sync(FULL, (t0 | t1) != 0u);
                 const int np = 32 - __clz((m & 0xffffu) | (m >> 16));
-                uint8_t* pp = seg + lo + 16 * k + (hmask & 4);
-                stg_u32_if(pp, t0, k, np);
-                stg_u32_if(pp + 8, t1, k, np);
+                const unsigned pp = seg + lo + 16 * k + (hmask & 4);
+                sts_u32_if(pp, t0, k, np);
+                sts_u32_if(pp + 8, t1, k, np);
                 wacc[0] |= (uint32_t)width_byte(np) << (8 * (r / 4));
                 lo += 16 * np;
             }
@@ -653,13 +669,13 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                     fa = 31 - __clz(m & 0xffffu);
                     fb = 31 - __clz(m >> 16);
                     const int npm = hi ? fb + 1 : fa + 1;
-                    stg_u32_if(seg + lo + (hmask & (4 * fa + 4)) + 4 * k, t, k, npm);
+                    sts_u32_if(seg + lo + (hmask & (4 * fa + 4)) + 4 * k, t, k, npm);
                 } else {
                     const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
                     fa = 31 - __clz(__ballot_sync(FULL, ta != 0u));
                     fb = 31 - __clz(__ballot_sync(FULL, tb != 0u));
-                    stg_u32_if(seg + lo + 4 * lane, ta, lane, fa + 1);
-                    stg_u32_if(seg + lo + 4 * fa + 4 + 4 * lane, tb, lane, fb + 1);
+                    sts_u32_if(seg + lo + 4 * lane, ta, lane, fa + 1);
+                    sts_u32_if(seg + lo + 4 * fa + 4 + 4 * lane, tb, lane, fb + 1);
                 }
                 wacc[r / 4] |= ((uint32_t)max(fa, 0) | ((uint32_t)max(fb, 0) << 8)) << (8 * (r % 4));
                 lo += 4 * (fa + fb + 2);
@@ -676,8 +692,8 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                     const int oA = lo, oB = oA + 2 * npA, oC = oB + 2 * npB, oD = oC + 2 * npC;
                     const int npL = hi ? npC : npA, npH = hi ? npD : npB;
                     const int offL = hi ? oC : oA, offH = hi ? oD : oB;
-                    stg_u16_if(seg + offL + 2 * k, t & 0xffffu, k, npL);
-                    stg_u16_if(seg + offH + 2 * k, t >> 16, k, npH);
+                    sts_u16_if(seg + offL + 2 * k, t & 0xffffu, k, npL);
+                    sts_u16_if(seg + offH + 2 * k, t >> 16, k, npH);
                 } else {
                     const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
                     npA = 32 - __clz(__ballot_sync(FULL, (ta & 0xffffu) != 0u));
@@ -685,10 +701,10 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                     npC = 32 - __clz(__ballot_sync(FULL, (tb & 0xffffu) != 0u));
                     npD = 32 - __clz(__ballot_sync(FULL, (tb >> 16) != 0u));
                     const int oA = lo, oB = oA + 2 * npA, oC = oB + 2 * npB, oD = oC + 2 * npC;
-                    stg_u16_if(seg + oA + 2 * lane, ta & 0xffffu, lane, npA);
-                    stg_u16_if(seg + oB + 2 * lane, ta >> 16, lane, npB);
-                    stg_u16_if(seg + oC + 2 * lane, tb & 0xffffu, lane, npC);
-                    stg_u16_if(seg + oD + 2 * lane, tb >> 16, lane, npD);
+                    sts_u16_if(seg + oA + 2 * lane, ta & 0xffffu, lane, npA);
+                    sts_u16_if(seg + oB + 2 * lane, ta >> 16, lane, npB);
+                    sts_u16_if(seg + oC + 2 * lane, tb & 0xffffu, lane, npC);
+                    sts_u16_if(seg + oD + 2 * lane, tb >> 16, lane, npD);
                 }
                 wacc[r / 2] = (uint32_t)width_byte(npA) | ((uint32_t)width_byte(npB) << 8) |
                               ((uint32_t)width_byte(npC) << 16) | ((uint32_t)width_byte(npD) << 24);
@@ -699,11 +715,11 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                     const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
                     const unsigned m = __ballot_sync(FULL, t != 0u);
                     np = 32 - __clz((m & 0xffffu) | (m >> 16));
-                    stg_u32_if(seg + lo + 8 * k + (hmask & 4), t, k, np);
+                    sts_u32_if(seg + lo + 8 * k + (hmask & 4), t, k, np);
                 } else {
                     const uint32_t ta = tpose(u[r], tc), tb = tpose(u[r + 1], tc);
                     np = 32 - __clz(__ballot_sync(FULL, (ta | tb) != 0u));
-                    stg_u64_if(seg + lo + 8 * lane, ta, tb, lane, np);
+                    sts_u64_if(seg + lo + 8 * lane, ta, tb, lane, np);
                 }
                 wacc[0] |= (uint32_t)width_byte(np) << (8 * (r / 2));
                 lo += 8 * np;
@@ -715,14 +731,14 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                     const uint32_t t1 = tpose(__byte_perm(u[r + 2], u[r + 3], 0x5410), tc);
                     const unsigned m = __ballot_sync(FULL, (t0 | t1) != 0u);
                     np = 32 - __clz((m & 0xffffu) | (m >> 16));
-                    uint8_t* pp = seg + lo + 16 * k + (hmask & 4);
-                    stg_u32_if(pp, t0, k, np);
-                    stg_u32_if(pp + 8, t1, k, np);
+                    const unsigned pp = seg + lo + 16 * k + (hmask & 4);
+                    sts_u32_if(pp, t0, k, np);
+                    sts_u32_if(pp + 8, t1, k, np);
                 } else {
                     const uint32_t t0 = tpose(u[r], tc), t1 = tpose(u[r + 1], tc);
                     const uint32_t t2 = tpose(u[r + 2], tc), t3 = tpose(u[r + 3], tc);
                     np = 32 - __clz(__ballot_sync(FULL, (t0 | t1 | t2 | t3) != 0u));
-                    stg_u128_if(seg + lo + 16 * lane, t0, t1, t2, t3, lane, np);
+                    sts_u128_if(seg + lo + 16 * lane, t0, t1, t2, t3, lane, np);
                 }
                 wacc[0] |= (uint32_t)width_byte(np) << (8 * (r / 4));
                 lo += 16 * np;
@@ -842,10 +858,10 @@ struct EncShared {
 // (block heads stored apart, single unpacked streams) writes the heads
 // straight to their fixed place in the output.  Thread 0 fills the slot's
 // scalars.
-template <int LOG2L, int U, bool HAS_CIN, typename TX, bool HEADS = false>
+template <int LOG2L, int U, bool HAS_CIN, typename TX, bool HEADS = false, int SR = 32>
 __device__ __forceinline__ int enc_tile(const Launch& P, const Item& it, unsigned item_idx,
                                         unsigned tile_in_item, uint8_t* seg, uint8_t* wb,
-                                        TileSlot& S, EncShared& es)
+                                        uint8_t* stage, TileSlot& S, EncShared& es)
 {
     static_assert(!HEADS || !HAS_CIN, "heads apart: compression only");
     constexpr int L = 1 << LOG2L;
@@ -889,6 +905,26 @@ __device__ __forceinline__ int enc_tile(const Launch& P, const Item& it, unsigne
     const TpC tc = tp_consts(lane);
     int err = 0;
     int lo = 0;
+    // The unit's payload is staged in shared memory (`stage`, this warp's
+    // stage_bytes(SR)), SR rows at a time, and flushed to its ring segment
+    // `seg` with 16-byte copies.  The
+    // stage holds ring bytes [sbase, lo) (sbase 16-byte aligned); a flush
+    // copies them and keeps the partial last 16 bytes at the stage start.
+    static_assert(SR % GR == 0 && U % SR == 0, "stage geometry");
+    __shared__ __align__(16) int2 meta_all[HAS_CIN ? NWARPS : 1][HAS_CIN ? BU : 1];
+    const unsigned stage_s = (unsigned)__cvta_generic_to_shared(stage);
+    int sbase = 0;
+    auto flush = [&](int lo_end) {
+        const int n16 = (lo_end - sbase + 15) >> 4;
+        for (int i = lane; i < n16; i += 32)
+            ((uint4*)(seg + sbase))[i] = ((const uint4*)stage)[i];
+        const int nbase = lo_end & ~15;
+        __syncwarp();
+        if (lane == 0 && nbase != sbase && (lo_end & 15) != 0)
+            ((uint4*)stage)[0] = ((const uint4*)stage)[(nbase - sbase) >> 4];
+        __syncwarp();
+        sbase = nbase;
+    };
     if (do_enc && it.x != nullptr && ue0 + U * 32 <= n) {
         // a whole unit (every unit but the last of a stream): no tails, and
         // few live values, so the group loop stays in registers
@@ -906,8 +942,7 @@ __device__ __forceinline__ int enc_tile(const Launch& P, const Item& it, unsigne
         int2* meta = nullptr;
         bool narrow = false;
         if constexpr (HAS_CIN) {
-            __shared__ __align__(16) int2 meta_full[NWARPS][BU];
-            meta = meta_full[warp];
+            meta = meta_all[warp];
             if (do_cin)
                 src = it.cin + unit_meta<LOG2L, U>(P, it, S.g * NWARPS + warp, ue0, meta, narrow);
         }
@@ -933,15 +968,15 @@ __device__ __forceinline__ int enc_tile(const Launch& P, const Item& it, unsigne
             const int b0 = L >= 32 ? gi * GR / (L / 32) : gi * GR * 2;
             uint8_t* hout = nullptr;
             if (HEADS) hout = it.out + 32 + wbytes + 3ull * ((ue0 >> LOG2L) + b0);
-            lo = encode_group<LOG2L, true, HEADS>(acc, GR * 32, eb, two_eb, inv, seg, lo, wb + b0,
-                                                  err, tc, hout);
+            lo = encode_group<LOG2L, true, HEADS>(acc, GR * 32, eb, two_eb, inv, stage_s - sbase, lo,
+                                                  wb + b0, err, tc, hout);
+            if ((gi + 1) % (SR / GR) == 0) flush(lo);
         }
     } else if (ue0 < n) {
         const uint8_t* src = nullptr;
         int2* meta = nullptr;
         bool narrow = false;
         if constexpr (HAS_CIN) {
-            __shared__ __align__(16) int2 meta_all[NWARPS][BU];
             meta = meta_all[warp];
             if (do_cin)
                 src = it.cin + unit_meta<LOG2L, U>(P, it, S.g * NWARPS + warp, ue0, meta, narrow);
@@ -1001,13 +1036,17 @@ __device__ __forceinline__ int enc_tile(const Launch& P, const Item& it, unsigne
                 uint8_t* hout = nullptr;
                 if (HEADS) hout = it.out + 32 + wbytes + 3ull * ((ue0 >> LOG2L) + b0);
                 if (nrem == GR * 32)
-                    lo = encode_group<LOG2L, true, HEADS>(acc, nrem, eb, two_eb, inv, seg, lo,
-                                                          wb + b0, err, tc, hout);
+                    lo = encode_group<LOG2L, true, HEADS>(acc, nrem, eb, two_eb, inv,
+                                                          stage_s - sbase, lo, wb + b0, err, tc,
+                                                          hout);
                 else
-                    lo = encode_group<LOG2L, false, HEADS>(acc, nrem, eb, two_eb, inv, seg, lo,
-                                                           wb + b0, err, tc, hout);
+                    lo = encode_group<LOG2L, false, HEADS>(acc, nrem, eb, two_eb, inv,
+                                                           stage_s - sbase, lo, wb + b0, err, tc,
+                                                           hout);
+                if ((gi + 1) % (SR / GR) == 0) flush(lo);
             }
         }
+        if (do_enc) flush(lo);
     }
     {
         const unsigned bad = __ballot_sync(FULL, err != 0);
@@ -1256,21 +1295,22 @@ __device__ __forceinline__ void resolve_slot(const Launch& P, TileSlot& S, unsig
 // tiles taken earlier by CTAs that are running or done; every resolver
 // publishes its tiles in ticket order, so the chain always advances.  The
 // last CTA to finish advances the launch generation.
-//   enc(item, index, tile in item, segment, width bytes, slot, shared) -> unit size
+//   enc(item, index, tile in item, segment, width bytes, stage, slot, shared) -> unit size
 //   fin(item, index, tile in item, ticket, slot, segment, width bytes)
 // Barrier protocol per tile in slot s: the encoder warps arrive on BAR_ENC + s
 // after encoding it, the resolver waits there, resolves it and arrives on
 // BAR_RES + s, where the encoder warps wait NS - 1 tiles later before
 // storing it.  A slot's barriers are used again only after both sides have
 // passed them, and every path through the loops meets every barrier.
-template <int U, typename Src, typename Enc, typename Fin>
+template <int U, bool SINGLE, typename Src, typename Enc, typename Fin>
 __device__ __forceinline__ void enc_pipeline(const Launch& P, const Src& src, Enc enc, Fin fin)
 {
     constexpr int NS = enc_slots(U);  // tiles in flight
     constexpr int D = NS - 1;         // tiles between a tile's encoding and its stores
     __shared__ TileSlot slots[NS];
     __shared__ EncShared es;
-    extern __shared__ __align__(16) uint8_t dsm[];  // width bytes [slot][warp][2U]
+    extern __shared__ __align__(16) uint8_t dsm[];  // width bytes [slot][warp][2U] (, stages)
+    __shared__ __align__(16) uint8_t stage_static[SINGLE ? 1 : NWARPS][SINGLE ? 16 : stage_bytes(32)];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         es.E = ld_volatile_u32(&P.ctl->epoch) + 1u;
@@ -1294,6 +1334,10 @@ __device__ __forceinline__ void enc_pipeline(const Launch& P, const Src& src, En
     if (warp < NWARPS) {
         auto seg_of = [&](int s) { return ring + (unsigned long long)(s * NWARPS + warp) * seg_bytes(U); };
         auto wb_of = [&](int s) { return dsm + (s * NWARPS + warp) * (U * 2); };
+        auto stage_of = [&]() -> uint8_t* {
+            if constexpr (SINGLE) return dsm + enc_wb_bytes(U) + warp * stage_bytes(stage_rows(U, true));
+            else return stage_static[warp];
+        };
         auto store = [&](int q) {
             bar_sync_n(BAR_RES + q, ENC_THREADS);
             const TileSlot& Q = slots[q];
@@ -1321,7 +1365,7 @@ __device__ __forceinline__ void enc_pipeline(const Launch& P, const Src& src, En
                 const Item it = src.get(S.item);
                 const unsigned t = S.g - it.tile_begin;
                 if (tid == 0) S.tile = t;
-                lo = enc(it, S.item, t, seg_of(s), wb_of(s), S, es);
+                lo = enc(it, S.item, t, seg_of(s), wb_of(s), stage_of(), S, es);
             }
             if (lane == 0) S.segsz[warp] = lo;
             bar_arrive_n(BAR_ENC + s, ENC_THREADS);
@@ -1358,10 +1402,13 @@ __device__ __forceinline__ void enc_pipeline(const Launch& P, const Src& src, En
 template <int LOG2L, int U, typename TX, bool HEADS = false>
 __global__ void __launch_bounds__(ENC_THREADS, ENC_CTAS_PER_SM) k_compress(const Launch P)
 {
-    enc_pipeline<U>(
+    enc_pipeline<U, true>(
         P, ItemsSrc{P},
-        [&](const Item& it, unsigned idx, unsigned t, uint8_t* seg, uint8_t* wb, TileSlot& S,
-            EncShared& es) { return enc_tile<LOG2L, U, false, TX, HEADS>(P, it, idx, t, seg, wb, S, es); },
+        [&](const Item& it, unsigned idx, unsigned t, uint8_t* seg, uint8_t* wb, uint8_t* stage,
+            TileSlot& S, EncShared& es) {
+            return enc_tile<LOG2L, U, false, TX, HEADS, stage_rows(U, true)>(P, it, idx, t, seg, wb,
+                                                                          stage, S, es);
+        },
         [&](const Item& it, unsigned idx, unsigned t, unsigned g, const TileSlot& S,
             const uint8_t* seg, const uint8_t* wb) { fin_tile<LOG2L, U, false, HEADS>(P, it, idx, t, g, S, seg, wb); });
 }
@@ -1370,10 +1417,13 @@ template <int LOG2L, int U, typename TX>
 __global__ void __launch_bounds__(ENC_THREADS, ENC_CTAS_PER_SM) k_scatter(const Launch P,
                                                                           const ScatterParams SP)
 {
-    enc_pipeline<U>(
+    enc_pipeline<U, true>(
         P, ScatterSrc{P, SP},
-        [&](const Item& it, unsigned idx, unsigned t, uint8_t* seg, uint8_t* wb, TileSlot& S,
-            EncShared& es) { return enc_tile<LOG2L, U, false, TX>(P, it, idx, t, seg, wb, S, es); },
+        [&](const Item& it, unsigned idx, unsigned t, uint8_t* seg, uint8_t* wb, uint8_t* stage,
+            TileSlot& S, EncShared& es) {
+            return enc_tile<LOG2L, U, false, TX, false, stage_rows(U, true)>(P, it, idx, t, seg, wb,
+                                                                          stage, S, es);
+        },
         [&](const Item& it, unsigned idx, unsigned t, unsigned g, const TileSlot& S,
             const uint8_t* seg, const uint8_t* wb) { fin_tile<LOG2L, U, false>(P, it, idx, t, g, S, seg, wb); });
 }
@@ -1381,10 +1431,12 @@ __global__ void __launch_bounds__(ENC_THREADS, ENC_CTAS_PER_SM) k_scatter(const 
 template <int LOG2L, int U>
 __global__ void __launch_bounds__(ENC_THREADS, ENC_CTAS_PER_SM) k_reduce(const Launch P)
 {
-    enc_pipeline<U>(
+    enc_pipeline<U, false>(
         P, ItemsSrc{P},
-        [&](const Item& it, unsigned idx, unsigned t, uint8_t* seg, uint8_t* wb, TileSlot& S,
-            EncShared& es) { return enc_tile<LOG2L, U, true, float>(P, it, idx, t, seg, wb, S, es); },
+        [&](const Item& it, unsigned idx, unsigned t, uint8_t* seg, uint8_t* wb, uint8_t* stage,
+            TileSlot& S, EncShared& es) {
+            return enc_tile<LOG2L, U, true, float>(P, it, idx, t, seg, wb, stage, S, es);
+        },
         [&](const Item& it, unsigned idx, unsigned t, unsigned g, const TileSlot& S,
             const uint8_t* seg, const uint8_t* wb) { fin_tile<LOG2L, U, true>(P, it, idx, t, g, S, seg, wb); });
 }
@@ -1397,24 +1449,24 @@ __global__ void __launch_bounds__(ENC_THREADS, ENC_CTAS_PER_SM) k_reduce(const L
 template <int U>
 __global__ void __launch_bounds__(ENC_THREADS, ENC_CTAS_PER_SM) k_batch(const Launch P)
 {
-    enc_pipeline<U>(
+    enc_pipeline<U, false>(
         P, ItemsSrc{P},
-        [&](const Item& it, unsigned idx, unsigned t, uint8_t* seg, uint8_t* wb, TileSlot& S,
-            EncShared& es) -> int {
+        [&](const Item& it, unsigned idx, unsigned t, uint8_t* seg, uint8_t* wb, uint8_t* stage,
+            TileSlot& S, EncShared& es) -> int {
             const bool f32 = it.x_dtype == ZC_F32;
             switch (it.log2L) {
             case 4:
-                return f32 ? enc_tile<4, U, false, float>(P, it, idx, t, seg, wb, S, es)
-                           : enc_tile<4, U, false, uint16_t>(P, it, idx, t, seg, wb, S, es);
+                return f32 ? enc_tile<4, U, false, float>(P, it, idx, t, seg, wb, stage, S, es)
+                           : enc_tile<4, U, false, uint16_t>(P, it, idx, t, seg, wb, stage, S, es);
             case 5:
-                return f32 ? enc_tile<5, U, false, float>(P, it, idx, t, seg, wb, S, es)
-                           : enc_tile<5, U, false, uint16_t>(P, it, idx, t, seg, wb, S, es);
+                return f32 ? enc_tile<5, U, false, float>(P, it, idx, t, seg, wb, stage, S, es)
+                           : enc_tile<5, U, false, uint16_t>(P, it, idx, t, seg, wb, stage, S, es);
             case 6:
-                return f32 ? enc_tile<6, U, false, float>(P, it, idx, t, seg, wb, S, es)
-                           : enc_tile<6, U, false, uint16_t>(P, it, idx, t, seg, wb, S, es);
+                return f32 ? enc_tile<6, U, false, float>(P, it, idx, t, seg, wb, stage, S, es)
+                           : enc_tile<6, U, false, uint16_t>(P, it, idx, t, seg, wb, stage, S, es);
             case 7:
-                return f32 ? enc_tile<7, U, false, float>(P, it, idx, t, seg, wb, S, es)
-                           : enc_tile<7, U, false, uint16_t>(P, it, idx, t, seg, wb, S, es);
+                return f32 ? enc_tile<7, U, false, float>(P, it, idx, t, seg, wb, stage, S, es)
+                           : enc_tile<7, U, false, uint16_t>(P, it, idx, t, seg, wb, stage, S, es);
             default: return enc_raw<U>(it, t, S);
             }
         },

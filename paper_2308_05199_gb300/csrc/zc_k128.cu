@@ -4,33 +4,33 @@
 namespace zc {
 
 template <typename K>
-static cudaError_t prepare(K kernel, int U)
+static cudaError_t prepare(K kernel, int U, bool single = false)
 {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                enc_smem_bytes(U));
+                                enc_smem_bytes(U, single));
 }
 
 template <int U>
 static cudaError_t compress_u(int x_dtype, const Launch& P, unsigned grid, cudaStream_t s)
 {
-    static const cudaError_t e32 = prepare(k_compress<7, U, float>, U);
-    static const cudaError_t e16 = prepare(k_compress<7, U, uint16_t>, U);
+    static const cudaError_t e32 = prepare(k_compress<7, U, float>, U, true);
+    static const cudaError_t e16 = prepare(k_compress<7, U, uint16_t>, U, true);
     if (e32 != cudaSuccess || e16 != cudaSuccess) return e32 != cudaSuccess ? e32 : e16;
-    if (x_dtype == ZC_F32) k_compress<7, U, float><<<grid, ENC_THREADS, enc_smem_bytes(U), s>>>(P);
-    else k_compress<7, U, uint16_t><<<grid, ENC_THREADS, enc_smem_bytes(U), s>>>(P);
+    if (x_dtype == ZC_F32) k_compress<7, U, float><<<grid, ENC_THREADS, enc_smem_bytes(U, true), s>>>(P);
+    else k_compress<7, U, uint16_t><<<grid, ENC_THREADS, enc_smem_bytes(U, true), s>>>(P);
     return cudaGetLastError();
 }
 
 // Block heads stored apart: 8-chunk tiles (64-row warp units) only.
 cudaError_t launch_compress_heads_l128(int x_dtype, const Launch& P, unsigned grid, cudaStream_t s)
 {
-    static const cudaError_t e32 = prepare(k_compress<7, 64, float, true>, 64);
-    static const cudaError_t e16 = prepare(k_compress<7, 64, uint16_t, true>, 64);
+    static const cudaError_t e32 = prepare(k_compress<7, 64, float, true>, 64, true);
+    static const cudaError_t e16 = prepare(k_compress<7, 64, uint16_t, true>, 64, true);
     if (e32 != cudaSuccess || e16 != cudaSuccess) return e32 != cudaSuccess ? e32 : e16;
     if (x_dtype == ZC_F32)
-        k_compress<7, 64, float, true><<<grid, ENC_THREADS, enc_smem_bytes(64), s>>>(P);
+        k_compress<7, 64, float, true><<<grid, ENC_THREADS, enc_smem_bytes(64, true), s>>>(P);
     else
-        k_compress<7, 64, uint16_t, true><<<grid, ENC_THREADS, enc_smem_bytes(64), s>>>(P);
+        k_compress<7, 64, uint16_t, true><<<grid, ENC_THREADS, enc_smem_bytes(64, true), s>>>(P);
     return cudaGetLastError();
 }
 
@@ -48,11 +48,11 @@ template <int U>
 static cudaError_t scatter_u(int x_dtype, const Launch& P, const ScatterParams& SP, unsigned grid,
                              cudaStream_t s)
 {
-    static const cudaError_t e32 = prepare(k_scatter<7, U, float>, U);
-    static const cudaError_t e16 = prepare(k_scatter<7, U, uint16_t>, U);
+    static const cudaError_t e32 = prepare(k_scatter<7, U, float>, U, true);
+    static const cudaError_t e16 = prepare(k_scatter<7, U, uint16_t>, U, true);
     if (e32 != cudaSuccess || e16 != cudaSuccess) return e32 != cudaSuccess ? e32 : e16;
-    if (x_dtype == ZC_F32) k_scatter<7, U, float><<<grid, ENC_THREADS, enc_smem_bytes(U), s>>>(P, SP);
-    else k_scatter<7, U, uint16_t><<<grid, ENC_THREADS, enc_smem_bytes(U), s>>>(P, SP);
+    if (x_dtype == ZC_F32) k_scatter<7, U, float><<<grid, ENC_THREADS, enc_smem_bytes(U, true), s>>>(P, SP);
+    else k_scatter<7, U, uint16_t><<<grid, ENC_THREADS, enc_smem_bytes(U, true), s>>>(P, SP);
     return cudaGetLastError();
 }
 
