@@ -820,6 +820,7 @@ def run_ours(args, rank, world):
     coll = collectives_report(torch, workloads, W.stream, dev,
                               [int(v) for v in args.collective_ranks.split(",") if v],
                               args.ring_side) if args.collective_ranks else None
+    W.step()  # the side reports reuse the step's buffers: sizes come from a step
     torch.cuda.synchronize()
     st, det = W.ws.status()
     if st != 0:
