@@ -247,7 +247,7 @@ typedef struct {
 typedef struct {
     int n_msgs;
     int tile_chunks;         /* compression tile: chunks of 2048 elements     */
-    int grid;                /* CTAs launched; 0 = one per tile               */
+    int grid;                /* CTAs launched; 0 = as many as allowed         */
     int decompress;          /* 0: compression plan, 1: decompression plan    */
     uint64_t total_tiles;    /* tiles of all messages together                */
     uint64_t total_chunks;   /* decompression: width-scan chunks              */
@@ -266,7 +266,8 @@ size_t zc_batch_max_bytes(int n_msgs, const zc_message* h_msgs);
 
 /* Plan the compression of h_msgs[0 .. n_msgs) into d_packed (16-byte
  * aligned).  tile_chunks: 4, 8, 16, or 0 for the current default
- * (zc_set_tile_chunks); grid: CTAs to launch, 0 = one per tile.  Validates
+ * (zc_set_tile_chunks); grid: CTAs to launch (at most one per tile, per
+ * ring of the workspace and 4 per SM), 0 = as many as allowed.  Validates
  * every message (ZC_ERR_ARG), checks that packed_cap holds at least every
  * header and width array (ZC_ERR_CAPACITY; the payload is checked on the
  * device), and copies the table to d_table with a synchronous cudaMemcpy. */
@@ -303,7 +304,7 @@ int zc_decompress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_st
 
 /* Autotuner for batched compression.  Times zc_compress_batch on the given
  * messages for every candidate tile size (4, 8, 16 chunks) and grid (1, 2 and
- * 4 CTAs per SM, and one CTA per tile), and, with tune_block != 0, every
+ * 4 CTAs per SM, and as many as allowed), and, with tune_block != 0, every
  * block size (16 .. 128, applied to all non-raw messages).  Each candidate
  * runs once untimed and `reps` times timed with CUDA events on s; its score
  * is the median time plus, for link_gbs > 0, the time to send the packed
@@ -317,7 +318,7 @@ int zc_decompress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_st
 typedef struct {
     int block;               /* block size of the non-raw messages; 0 = as given */
     int tile_chunks;
-    int grid;                /* 0 = one CTA per tile                           */
+    int grid;                /* 0 = as many CTAs as allowed                    */
     int status;              /* device status after the candidate's runs       */
     float ms;                /* median compression time                        */
     uint64_t packed_bytes;   /* packed length                                  */

@@ -97,7 +97,7 @@ int zc_autotune_batch(int n_msgs, const zc_message* h_msgs, int tune_block, doub
                     rc = st;
                     goto done;
                 }
-                if (G > 0 && (uint64_t)G >= plan.total_tiles) continue;  // same as one per tile
+                if (G > 0 && (uint64_t)G >= plan.total_tiles) continue;  // same as grid 0
                 zc_tune_point p;
                 std::memset(&p, 0, sizeof(p));
                 p.block = blk;
