@@ -851,8 +851,9 @@ struct EncShared {
 };
 
 // Encoder warp `warp`'s unit of one tile: quantize, delta-code and bit-plane
-// pack its U rows into its ring segment `seg` and width bytes `wb`; returns
-// the segment's size.  HAS_CIN: decode `it.cin` first (same block size, unit
+// pack its U rows, through its shared-memory `stage` (SR rows at a time),
+// into its ring segment `seg`, and its width bytes into `wb`; returns the
+// segment's size.  HAS_CIN: decode `it.cin` first (same block size, unit
 // offsets from k_wscan) and add the local chunk; the FP32 sum then goes to
 // `it.raw_out` when that is set.  Null pointers switch a step off.  HEADS
 // (block heads stored apart, single unpacked streams) writes the heads
