@@ -214,6 +214,15 @@ __device__ __forceinline__ int planes_of(int w) { return w ? w + 1 : 0; }
 
 __device__ __forceinline__ uint8_t width_byte(int np) { return (uint8_t)(np ? np - 1 : 0); }
 
+// width_byte of four blocks at once, from their plane counts packed one per
+// byte (each at most 32).  Adding 0x7f to a byte sets its top bit exactly when
+// its count is nonzero and carries into no neighbour, so subtracting those
+// bits, shifted down to bit 0, borrows across no byte.
+__device__ __forceinline__ uint32_t width_bytes4(uint32_t c)
+{
+    return c - (((c + 0x7f7f7f7fu) & 0x80808080u) >> 7);
+}
+
 // Inclusive prefix sum of exact FP32 integers over 32 lanes (FMA pipe).
 __device__ __forceinline__ float scan_incl_f(float v)
 {
@@ -614,6 +623,7 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
     const uint32_t hmask = hi ? 0xffffffffu : 0u;
     // the group's width bytes, gathered in registers and stored once (GR * 32 / L bytes)
     uint32_t wacc[4] = {0u, 0u, 0u, 0u};
+    uint32_t pk[GR / 2];  // L = 32: plane counts of the row pairs
     if (!any_wide) {
         // every value of the group fits 16 bits (the common case): paired (or
         // quadrupled) rows share a transpose, with no per-pair votes
@@ -624,8 +634,8 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                 const unsigned m = __ballot_sync(FULL, t != 0u);
                 const int na = 32 - __clz(m & 0xffffu), nb = 32 - __clz(m >> 16);
                 sts_u32_if(seg + 4 * k + lo + (hmask & (4 * na)), t, k, hi ? nb : na);
-                wacc[r / 4] |= ((uint32_t)max(na - 1, 0) | ((uint32_t)max(nb - 1, 0) << 8))
-                               << (8 * (r % 4));
+                // the pair's plane counts as bytes [na, nb, 0, 0]
+                pk[r / 2] = __byte_perm((uint32_t)na, (uint32_t)nb, 0x1140);
                 lo += 4 * (na + nb);
             } else if (L == 16) {
                 const uint32_t t = tpose(__byte_perm(u[r], u[r + 1], 0x5410), tc);
@@ -657,6 +667,12 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
                 wacc[0] |= (uint32_t)width_byte(np) << (8 * (r / 4));
                 lo += 16 * np;
             }
+        }
+        if (L == 32) {
+            // the width bytes of two pairs at a time
+#pragma unroll
+            for (int w = 0; w < GR / 4; ++w)
+                wacc[w] = width_bytes4(__byte_perm(pk[2 * w], pk[2 * w + 1], 0x5410));
         }
     } else {
     #pragma unroll
