@@ -104,6 +104,22 @@ def test_raw_messages_from_unaligned_inputs(zc):
     check_against_oracle(b, [x.cpu() for x in xs], [0] * 4, [0.0] * 4)
 
 
+@pytest.mark.parametrize("chunks", [4, 16])
+def test_coded_messages_from_unaligned_inputs(zc, chunks):
+    """Coded messages whose data start off a 16-byte boundary beside 16-byte
+    aligned ones, every block size, FP32 and BF16, in one launch: byte-exact
+    streams."""
+    big32 = W.student_t3(300007, 0.05, 13).cuda()
+    big16 = W.student_t3(300007, 0.05, 14, dtype=torch.bfloat16).cuda()
+    xs = [big32[1:], big16[1:], big32[4:], big16[8:200000], big32[2:], big16[3:], big32,
+          big16[16:250001]]
+    blocks = [32, 32, 16, 64, 128, 16, 64, 128]
+    ebs = [1e-5] * len(xs)
+    b = zc.BatchCompress(xs, blocks, ebs, tile_chunks=chunks)
+    b.run()
+    check_against_oracle(b, [x.cpu() for x in xs], blocks, ebs)
+
+
 def test_batch_decompress_matches_oracle(zc):
     xs, blocks, ebs = mixed_messages(5, SIZES_MIX)
     b = zc.BatchCompress([x.cuda() for x in xs], blocks, ebs)
