@@ -2,6 +2,7 @@
 // carving, tile planning and kernel launches.  No call allocates memory, reads
 // device memory back (except zc_get_device_status and the setup-time plan
 // builder) or synchronises the stream.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -136,14 +137,15 @@ int ws_view(void* ws, size_t bytes, WsView& v)
 // grid): at most one per ring and the resident CTAs of this GPU.
 uint64_t enc_grid(uint64_t want, int U, const WsView& w)
 {
-    static int sms[64];
+    static std::atomic<int> sms[64];  // SM count per device, 0 until queried
     int dev = 0;
     int n_sm = 152;
     if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
-        if (sms[dev] == 0 &&
-            cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            sms[dev] = 0;
-        if (sms[dev] > 0) n_sm = sms[dev];
+        int c = sms[dev].load(std::memory_order_relaxed);
+        if (c == 0 && cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            c > 0)
+            sms[dev].store(c, std::memory_order_relaxed);
+        if (c > 0) n_sm = c;
     }
     uint64_t g = want;
     const uint64_t rings = w.ring_bytes / ring_cta_bytes(U);

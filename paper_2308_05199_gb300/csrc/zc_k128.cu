@@ -3,18 +3,11 @@
 
 namespace zc {
 
-template <typename K>
-static cudaError_t prepare(K kernel, int U, bool single = false)
-{
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                enc_smem_bytes(U, single));
-}
-
 template <int U>
 static cudaError_t compress_u(int x_dtype, const Launch& P, unsigned grid, cudaStream_t s)
 {
-    static const cudaError_t e32 = prepare(k_compress<7, U, float>, U, true);
-    static const cudaError_t e16 = prepare(k_compress<7, U, uint16_t>, U, true);
+    const cudaError_t e32 = smem_limit<k_compress<7, U, float>>(enc_smem_bytes(U, true));
+    const cudaError_t e16 = smem_limit<k_compress<7, U, uint16_t>>(enc_smem_bytes(U, true));
     if (e32 != cudaSuccess || e16 != cudaSuccess) return e32 != cudaSuccess ? e32 : e16;
     if (x_dtype == ZC_F32) k_compress<7, U, float><<<grid, ENC_THREADS, enc_smem_bytes(U, true), s>>>(P);
     else k_compress<7, U, uint16_t><<<grid, ENC_THREADS, enc_smem_bytes(U, true), s>>>(P);
@@ -24,8 +17,8 @@ static cudaError_t compress_u(int x_dtype, const Launch& P, unsigned grid, cudaS
 // Block heads stored apart: 8-chunk tiles (64-row warp units) only.
 cudaError_t launch_compress_heads_l128(int x_dtype, const Launch& P, unsigned grid, cudaStream_t s)
 {
-    static const cudaError_t e32 = prepare(k_compress<7, 64, float, true>, 64, true);
-    static const cudaError_t e16 = prepare(k_compress<7, 64, uint16_t, true>, 64, true);
+    const cudaError_t e32 = smem_limit<k_compress<7, 64, float, true>>(enc_smem_bytes(64, true));
+    const cudaError_t e16 = smem_limit<k_compress<7, 64, uint16_t, true>>(enc_smem_bytes(64, true));
     if (e32 != cudaSuccess || e16 != cudaSuccess) return e32 != cudaSuccess ? e32 : e16;
     if (x_dtype == ZC_F32)
         k_compress<7, 64, float, true><<<grid, ENC_THREADS, enc_smem_bytes(64, true), s>>>(P);
@@ -48,8 +41,8 @@ template <int U>
 static cudaError_t scatter_u(int x_dtype, const Launch& P, const ScatterParams& SP, unsigned grid,
                              cudaStream_t s)
 {
-    static const cudaError_t e32 = prepare(k_scatter<7, U, float>, U, true);
-    static const cudaError_t e16 = prepare(k_scatter<7, U, uint16_t>, U, true);
+    const cudaError_t e32 = smem_limit<k_scatter<7, U, float>>(enc_smem_bytes(U, true));
+    const cudaError_t e16 = smem_limit<k_scatter<7, U, uint16_t>>(enc_smem_bytes(U, true));
     if (e32 != cudaSuccess || e16 != cudaSuccess) return e32 != cudaSuccess ? e32 : e16;
     if (x_dtype == ZC_F32) k_scatter<7, U, float><<<grid, ENC_THREADS, enc_smem_bytes(U, true), s>>>(P, SP);
     else k_scatter<7, U, uint16_t><<<grid, ENC_THREADS, enc_smem_bytes(U, true), s>>>(P, SP);
@@ -70,7 +63,7 @@ cudaError_t launch_scatter_l128(int chunks, int x_dtype, const Launch& P, const 
 template <int U>
 static cudaError_t reduce_u(const Launch& P, unsigned grid, cudaStream_t s)
 {
-    static const cudaError_t e = prepare(k_reduce<7, U>, U);
+    const cudaError_t e = smem_limit<k_reduce<7, U>>(enc_smem_bytes(U));
     if (e != cudaSuccess) return e;
     k_reduce<7, U><<<grid, ENC_THREADS, enc_smem_bytes(U), s>>>(P);
     return cudaGetLastError();

@@ -1,9 +1,28 @@
 // zc_launch.h -- host-side launch entry points of the kernel translation units.
 #pragma once
 
+#include <atomic>
+
 #include "zc_codec.cuh"
 
 namespace zc {
+
+// Raises kernel K's dynamic shared-memory limit to `bytes` on the current
+// device, once per device: the attribute belongs to the device's context, so
+// a process that drives several GPUs sets it on each of them.
+template <auto K>
+inline cudaError_t smem_limit(int bytes)
+{
+    static std::atomic<unsigned long long> done{0ull};  // bit d: set on device d
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? 1ull << dev : 0ull;
+    if (bit != 0ull && (done.load(std::memory_order_acquire) & bit) != 0ull) return cudaSuccess;
+    e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
 
 // One translation unit per block size instantiates the encoder kernels for
 // every tile size S (sub-tiles of 2048 elements per CTA tile); these pick the
@@ -32,8 +51,7 @@ cudaError_t launch_batch_c16(const Launch& P, unsigned grid, cudaStream_t s);
 template <int U>
 cudaError_t launch_batch_u(const Launch& P, unsigned grid, cudaStream_t s)
 {
-    static const cudaError_t e = cudaFuncSetAttribute(
-        k_batch<U>, cudaFuncAttributeMaxDynamicSharedMemorySize, enc_smem_bytes(U));
+    const cudaError_t e = smem_limit<k_batch<U>>(enc_smem_bytes(U));
     if (e != cudaSuccess) return e;
     k_batch<U><<<grid, ENC_THREADS, enc_smem_bytes(U), s>>>(P);
     return cudaGetLastError();

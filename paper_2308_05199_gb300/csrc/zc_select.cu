@@ -530,10 +530,8 @@ int zc_batch_chunk_stats(const zc_batch* plan, float* d_feat, zc_stream_t s)
 
 static cudaError_t mlp_prepare()
 {
-    static const cudaError_t e1 = cudaFuncSetAttribute(
-        k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem));
-    static const cudaError_t e2 = cudaFuncSetAttribute(
-        k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MlpSmem));
+    const cudaError_t e1 = smem_limit<k_mlp_forward>((int)sizeof(MlpSmem));
+    const cudaError_t e2 = smem_limit<k_mlp_grad>((int)sizeof(MlpSmem));
     return e1 != cudaSuccess ? e1 : e2;
 }
 
