@@ -156,6 +156,13 @@ class ClockSampler:
 HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal
 
 
+def kernel_times(samples):
+    """Mean, median and best (minimum) of every kernel's per-step durations."""
+    return ({k: statistics.mean(v) for k, v in samples.items()},
+            {k: statistics.median(v) for k, v in samples.items()},
+            {k: min(v) for k, v in samples.items()})
+
+
 # The sources the encoder kernels (k_compress, k_batch, k_reduce, k_scatter) are
 # built from: a DRAM-traffic figure taken with ncu stays valid while these are
 # unchanged.
@@ -859,8 +866,9 @@ def run_ours(args, rank, world):
         raise RuntimeError("device status %d at %d in the timed region" % (st, det))
     names = ["compress", "decompress", "ring_allreduce", "scatter_pack", "batched_compress",
              "selector_compress"]
-    per = {nm: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K))
-           for i, nm in enumerate(names)}
+    samples = {nm: [evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K)]
+               for i, nm in enumerate(names)}
+    per, med, best = kernel_times(samples)
     ms_per_step = total_ms / K
     value = job_gbs(step_bytes, world, ms_per_step)
     hbm, peak_kind = peaks()
@@ -892,6 +900,8 @@ def run_ours(args, rank, world):
         "ratio": round(4 * W.n / C, 3),
         "kernels_gbs": {k: round(v, 1) for k, v in kern_gbs.items()},
         "kernels_ms": {k: round(v, 4) for k, v in per.items()},
+        "kernels_ms_median": {k: round(v, 4) for k, v in med.items()},
+        "kernels_ms_best": {k: round(v, 4) for k, v in best.items()},
         "kernels_frac_of_hbm": {k: round(v / hbm, 4) for k, v in kern_gbs.items()},
         "roofline": roofline,
         "gpu_launches": W.launches_per_step * K,

@@ -1,6 +1,7 @@
-"""The bench's clock record (CPU only): nvidia-smi lines parsed into the median
-SM clock, the maximum clock and the throttle reasons seen, from the samples
-taken inside the timed region only."""
+"""The bench's clock record and kernel-time summary (CPU only): nvidia-smi
+lines parsed into the median SM clock, the maximum clock and the throttle
+reasons seen, from the samples taken inside the timed region only; every
+kernel's mean, median and best per-step duration."""
 import os
 import sys
 
@@ -48,3 +49,12 @@ def test_no_sample_inside_the_region_falls_back_to_all():
 def test_no_tool_gives_an_empty_record():
     s = sampler([], 0).summary()
     assert s == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_kernel_times_mean_median_best():
+    sys.path.insert(0, ROOT)
+    import bench
+    mean, med, best = bench.kernel_times({"a": [3.0, 1.0, 2.0, 10.0], "b": [0.5]})
+    assert mean == {"a": 4.0, "b": 0.5}
+    assert med == {"a": 2.5, "b": 0.5}
+    assert best == {"a": 1.0, "b": 0.5}
