@@ -422,8 +422,9 @@ int zc_batch_select(const zc_batch* plan, const float* d_feat, const float* d_pr
  * zc_graph_begin starts capturing s (a stream other than the legacy default
  * stream); the zc calls that follow on s are recorded, not run; zc_graph_end
  * stops the capture and instantiates the graph.  Make one ordinary call of
- * each entry point before capturing it (first calls set kernel attributes),
- * and build plans before the capture (planning copies synchronously). */
+ * each entry point on the device before capturing it (the first call of a
+ * kernel on each device sets its attributes), and build plans before the
+ * capture (planning copies synchronously). */
 typedef struct zc_graph_s* zc_graph;
 int zc_graph_begin(zc_stream_t s);
 int zc_graph_end(zc_stream_t s, zc_graph* g);
