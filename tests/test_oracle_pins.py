@@ -401,3 +401,68 @@ def test_brute_force_tiny_round_trips():
                 s = oracle.compress(x, 0.25, log2L)
                 np.testing.assert_array_equal(oracle.decode_q(s, n), qv.astype(np.int32))
                 np.testing.assert_array_equal(oracle.decompress(s, n), x)
+
+
+def _payload(stream, nb):
+    """Width bytes and the unpadded payload of a stream with nb blocks."""
+    h = oracle.header(stream)
+    wb = (nb + 15) // 16 * 16
+    s = np.frombuffer(stream, np.uint8)
+    return s[32:32 + nb], s[32 + wb:32 + wb + h["payload"]]
+
+
+@pytest.mark.parametrize("log2L", [4, 5, 6, 7])
+def test_blocks_are_independent(log2L):
+    """Blockwise Lorenzo (Sec. 3.3.2: cuSZp's blocks; head predicted from 0):
+    a stream's width bytes and payload are the concatenation of those of its
+    blocks compressed one by one, ragged last block included."""
+    L = 1 << log2L
+    rng = np.random.default_rng(40 + log2L)
+    n = 7 * L + L // 2 + 3
+    x = (np.cumsum(rng.normal(0, 0.02, n)) + rng.standard_t(3, n) * 1e-3).astype(np.float32)
+    eb = 1e-3
+    nb = (n + L - 1) // L
+    widths, payload = _payload(oracle.compress(x, eb, log2L), nb)
+    parts_w, parts_p = [], []
+    for b in range(nb):
+        wb, pb = _payload(oracle.compress(x[b * L:(b + 1) * L], eb, log2L), 1)
+        parts_w.append(wb)
+        parts_p.append(pb)
+    np.testing.assert_array_equal(widths, np.concatenate(parts_w))
+    np.testing.assert_array_equal(payload, np.concatenate(parts_p))
+
+
+@pytest.mark.parametrize("log2L", [4, 5, 7])
+def test_negation_symmetry(log2L):
+    """Round-half-even is odd-symmetric, so -x quantizes to -q: the widths are
+    the same, the decoded values are exactly negated."""
+    rng = np.random.default_rng(50 + log2L)
+    n = 3001
+    x = (rng.standard_t(3, n) * 0.05).astype(np.float32)
+    x[::97] = (rng.integers(-50, 51, x[::97].size) * 2e-3 + 1e-3).astype(np.float32)  # near ties
+    eb = 1e-3
+    nb = (n + (1 << log2L) - 1) >> log2L
+    sp, sn = oracle.compress(x, eb, log2L), oracle.compress(-x, eb, log2L)
+    np.testing.assert_array_equal(_width_bytes(sp, nb), _width_bytes(sn, nb))
+    assert len(sp) == len(sn)
+    np.testing.assert_array_equal(oracle.decode_q(sn, n), -oracle.decode_q(sp, n))
+    np.testing.assert_array_equal(oracle.decompress(sn, n), -oracle.decompress(sp, n))
+
+
+@pytest.mark.parametrize("k", [-3, 5])
+def test_power_of_two_scaling(k):
+    """x / (2 eb) is unchanged when x and eb are both scaled by 2^k (exact in
+    binary floating point): the streams differ only in the bound's header
+    field."""
+    rng = np.random.default_rng(60 + k)
+    n = 2500
+    x = (rng.standard_t(3, n) * 0.1).astype(np.float32)
+    eb = float(np.float32(1e-3))
+    xs = (x * np.float32(2.0 ** k)).astype(np.float32)
+    ebs = float(np.float32(eb) * np.float32(2.0 ** k))
+    for log2L in (4, 5, 6, 7):
+        a = oracle.compress(x, eb, log2L)
+        b = oracle.compress(xs, ebs, log2L)
+        assert len(a) == len(b)
+        assert a[:16] == b[:16] and a[20:] == b[20:]
+        assert oracle.header(b)["eb"] == ebs
