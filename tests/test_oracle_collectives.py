@@ -98,3 +98,15 @@ def test_ring_allreduce_bound_and_agreement(P):
         vals = [out[r][b[k]:b[k + 1]] for r in range(P) if r != owner]
         for v in vals[1:]:
             np.testing.assert_array_equal(v, vals[0])
+
+
+def test_redoub_bound_closed_form():
+    """The recursive-doubling bound written out for small N (worst case of
+    e_s = 2 e_(s-1) + eb over k steps, eb more for ranks that absorbed a
+    neighbour first, one more for a folded rank's returned result)."""
+    e = 1.0
+    assert [oracle.redoub_bound(2, i, e) for i in range(2)] == [1, 1]
+    assert [oracle.redoub_bound(4, i, e) for i in range(4)] == [3] * 4
+    assert [oracle.redoub_bound(8, i, e) for i in range(8)] == [7] * 8
+    assert [oracle.redoub_bound(3, i, e) for i in range(3)] == [4, 3, 3]
+    assert [oracle.redoub_bound(6, i, e) for i in range(6)] == [8, 7, 8, 7, 7, 7]

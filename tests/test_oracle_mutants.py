@@ -1,22 +1,27 @@
 """The oracle's pins catch plausible mistakes (CPU only).
 
-Each case plants one mistake in a temporary copy of oracle/zc_oracle.c (a
-dropped term, a wrong sign, index or bit order, an off-by-one, the wrong
-rounding), builds it with the oracle's own flags, swaps it in for the real
-oracle and runs a battery of the pins from test_oracle_pins.py: at least one
-pin must fail.  The real oracle passes the same battery."""
+Each case plants one mistake in a temporary copy of the oracle (a dropped
+term, a wrong sign, index or bit order, an off-by-one, the wrong rounding, the
+wrong ring neighbour or chunk): codec mistakes in a copy of
+oracle/zc_oracle.c, built with the oracle's own flags, collective mistakes in
+a copy of oracle/__init__.py loaded as a module of its own.  The copy is
+swapped in for the real oracle and a battery of pins runs against it: at
+least one pin must fail.  The real oracle passes the same batteries."""
 import contextlib
 import ctypes
 import os
 import subprocess
+import types
 
 import pytest
 
 import oracle
+import test_oracle_collectives as coll
 import test_oracle_pins as pins
 
-SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle",
-                   "zc_oracle.c")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "zc_oracle.c")
+PKG = os.path.join(ROOT, "oracle", "__init__.py")
 
 MUTANTS = {
     # block head predicted from the previous block's last value, not from 0
@@ -109,4 +114,77 @@ def test_real_oracle_passes_the_battery():
 def test_mutant_fails_a_pin(tmp_path, name):
     with oracle_built_from(build_mutant(tmp_path, MUTANTS[name])):
         failed = battery()
+    assert failed, "no pin caught the mutant %s" % name
+
+
+# ---- the simulated collectives ------------------------------------------------
+
+PY_MUTANTS = {
+    # ring step on the wrong chunk: (r - t) instead of (r - 1 - t) mod P
+    "ring_wrong_chunk": [(
+        "            c = (r - 1 - t) % P\n            s, sm = reduce_step(sent[(r - 1) % P], chunk(r, c), eb_abs, log2L, want_stream=True,",
+        "            c = (r - t) % P\n            s, sm = reduce_step(sent[(r - 1) % P], chunk(r, c), eb_abs, log2L, want_stream=True,")],
+    # stream taken from the right-hand neighbour
+    "ring_wrong_neighbour": [(
+        "reduce_step(sent[(r - 1) % P], chunk(r, c), eb_abs, log2L, want_stream=True,",
+        "reduce_step(sent[(r + 1) % P], chunk(r, c), eb_abs, log2L, want_stream=True,")],
+    # the absorbing rank adds the sender's buffer to the sender's own
+    "redoub_fold_adds_sender_buffer": [(
+        "cur[i + 1] = reduce_step(s, cur[i + 1], eb_abs",
+        "cur[i + 1] = reduce_step(s, cur[i], eb_abs")],
+    # the bound drops the absorbed neighbours' quantization
+    "redoub_bound_without_fold_term": [("    e0 = eb if r > 0 else 0.0", "    e0 = 0.0")],
+    # the bound drops the returned result's quantization
+    "redoub_bound_without_return_term": [("        e += eb\n    return e",
+                                          "        e += 0.0\n    return e")],
+}
+
+
+def collective_battery():
+    checks = [
+        ("redoub_2", coll.test_redoub_two_ranks_closed_form),
+        ("redoub_3", coll.test_redoub_three_ranks_closed_form),
+        ("redoub_schedule", coll.test_redoub_schedule),
+        ("redoub_bound_closed_form", coll.test_redoub_bound_closed_form),
+        ("ring_2", coll.test_ring_two_ranks_closed_form),
+    ]
+    checks += [("redoub_bound_%d" % N, lambda N=N: coll.test_redoub_error_bound(N))
+               for N in (3, 6, 8)]
+    checks += [("ring_bound_%d" % P, lambda P=P: coll.test_ring_allreduce_bound_and_agreement(P))
+               for P in (3, 5)]
+    failed = []
+    for name, fn in checks:
+        try:
+            fn()
+        except Exception:
+            failed.append(name)
+    return failed
+
+
+@contextlib.contextmanager
+def oracle_module_from(edits):
+    src = open(PKG).read()
+    for a, b in edits:
+        assert src.count(a) == 1, a
+        src = src.replace(a, b)
+    mod = types.ModuleType("oracle_mutant")
+    mod.__file__ = PKG
+    exec(compile(src, PKG, "exec"), mod.__dict__)
+    saved = coll.oracle
+    coll.oracle = mod
+    try:
+        yield
+    finally:
+        coll.oracle = saved
+
+
+def test_real_oracle_passes_the_collective_battery():
+    with oracle_module_from([]):
+        assert collective_battery() == []
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_collective_mutant_fails_a_pin(name):
+    with oracle_module_from(PY_MUTANTS[name]):
+        failed = collective_battery()
     assert failed, "no pin caught the mutant %s" % name
