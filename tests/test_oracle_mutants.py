@@ -2,9 +2,10 @@
 
 Each case plants one mistake in a temporary copy of the oracle (a dropped
 term, a wrong sign, index or bit order, an off-by-one, the wrong rounding, the
-wrong ring neighbour or chunk): codec mistakes in a copy of
-oracle/zc_oracle.c, built with the oracle's own flags, collective mistakes in
-a copy of oracle/__init__.py loaded as a module of its own.  The copy is
+wrong ring neighbour or chunk, a dropped derivative): codec mistakes in a
+copy of oracle/zc_oracle.c, built with the oracle's own flags, collective and
+selector mistakes in copies of oracle/__init__.py and oracle/selector.py
+loaded as modules of their own.  The copy is
 swapped in for the real oracle and a battery of pins runs against it: at
 least one pin must fail.  The real oracle passes the same batteries."""
 import contextlib
@@ -18,10 +19,12 @@ import pytest
 import oracle
 import test_oracle_collectives as coll
 import test_oracle_pins as pins
+import test_oracle_selector as tsel
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "zc_oracle.c")
 PKG = os.path.join(ROOT, "oracle", "__init__.py")
+SEL = os.path.join(ROOT, "oracle", "selector.py")
 
 MUTANTS = {
     # block head predicted from the previous block's last value, not from 0
@@ -187,4 +190,73 @@ def test_real_oracle_passes_the_collective_battery():
 def test_collective_mutant_fails_a_pin(name):
     with oracle_module_from(PY_MUTANTS[name]):
         failed = collective_battery()
+    assert failed, "no pin caught the mutant %s" % name
+
+
+# ---- the learned selector ----------------------------------------------------------
+
+SEL_MUTANTS = {
+    # the second ReLU's derivative left out of backpropagation
+    "relu_derivative_dropped": [('    dA2 = (dY @ P["W3"]) * (A2 > 0)', '    dA2 = (dY @ P["W3"])')],
+    # a transposed weight in backpropagation (square, so no shape error)
+    "transposed_weight": [('    dA1 = (dA2 @ P["W2"]) * (A1 > 0)',
+                           '    dA1 = (dA2 @ P["W2"].T) * (A1 > 0)')],
+    # a bias gradient lost
+    "bias_gradient_lost": [('    g["b1"] = dA1.sum(0)', '    g["b1"] = 0.0 * dA1.sum(0)')],
+    # the factor 2 of the squared error's derivative dropped
+    "loss_derivative_halved": [("    dY = 2.0 * R / (B * N_OUT)", "    dY = R / (B * N_OUT)")],
+    # the update climbs the gradient
+    "sgd_wrong_sign": [("    return np.asarray(p, np.float64) - lr * v, v",
+                        "    return np.asarray(p, np.float64) + lr * v, v")],
+    # the judge never rejects a prediction
+    "judge_ignored": [('    if abs(float(y[k]) - math.log2(f[k])) > cfg["judge_log2"]:',
+                       "    if False:")],
+    # a raw chunk's header not charged on the link
+    "raw_header_free": [('    raw = bytes_in * cfg["raw_ns_per_byte"] + (32.0 + bytes_in) / link',
+                         '    raw = bytes_in * cfg["raw_ns_per_byte"] + bytes_in / link')],
+}
+
+
+def selector_battery():
+    names = [n for n in dir(tsel) if n.startswith("test_")]
+    failed = []
+    for name in names:
+        fn = getattr(tsel, name)
+        args = [("f32",), ("bf16",)] if name == "test_sampled_bits_equal_the_codec_oracle_on_the_spans" else [()]
+        for a in args:
+            try:
+                fn(*a)
+            except Exception:
+                failed.append(name)
+                break
+    return failed
+
+
+@contextlib.contextmanager
+def selector_module_from(edits):
+    src = open(SEL).read()
+    for a, b in edits:
+        assert src.count(a) == 1, a
+        src = src.replace(a, b)
+    mod = types.ModuleType("oracle.selector_mutant")
+    mod.__file__ = SEL
+    mod.__package__ = "oracle"
+    exec(compile(src, SEL, "exec"), mod.__dict__)
+    saved = tsel.S
+    tsel.S = mod
+    try:
+        yield
+    finally:
+        tsel.S = saved
+
+
+def test_real_selector_oracle_passes_the_selector_battery():
+    with selector_module_from([]):
+        assert selector_battery() == []
+
+
+@pytest.mark.parametrize("name", sorted(SEL_MUTANTS))
+def test_selector_mutant_fails_a_pin(name):
+    with selector_module_from(SEL_MUTANTS[name]):
+        failed = selector_battery()
     assert failed, "no pin caught the mutant %s" % name
