@@ -18,6 +18,7 @@ import pytest
 
 import oracle
 import test_oracle_collectives as coll
+import test_oracle_heads as heads
 import test_oracle_pins as pins
 import test_oracle_selector as tsel
 
@@ -61,6 +62,13 @@ MUTANTS = {
         "            uint64_t e = j * L + i;\n            if (e < n) q[e] = acc;\n            acc += di;")],
     # reconstruction with eb instead of 2 eb
     "reconstruct_with_eb": [("        float two_eb = h.eb + h.eb;", "        float two_eb = h.eb;")],
+    # heads apart: a stored head read back without its 24-bit sign
+    "head_field_unsigned": [(
+        "            acc = (int32_t)v - ((v & 0x800000u) ? (int32_t)(1 << 24) : 0);  /* 24-bit signed */",
+        "            acc = (int32_t)v;")],
+    # heads apart: the head's own delta kept in the planes as well
+    "head_delta_kept": [("    if (i == 0) return heads ? 0 : q[e];",
+                         "    if (i == 0) return q[e];")],
 }
 
 
@@ -74,6 +82,10 @@ def battery():
         ("blocks_independent", lambda: pins.test_blocks_are_independent(5)),
         ("brute_force", pins.test_brute_force_tiny_round_trips),
         ("error_bound", lambda: pins.test_error_bound_and_q_round_trip("tdist", 5)),
+        ("heads_hand_stream", heads.test_hand_stream_l16),
+        ("heads_extremes", heads.test_negative_and_extreme_heads_round_trip),
+        ("heads_closed_form", lambda: heads.test_length_closed_form_and_same_values_as_plain(5)),
+        ("heads_constant_blocks", heads.test_constant_blocks_store_only_heads),
     ]
     failed = []
     for name, fn in checks:
