@@ -69,6 +69,17 @@ MUTANTS = {
     # heads apart: the head's own delta kept in the planes as well
     "head_delta_kept": [("    if (i == 0) return heads ? 0 : q[e];",
                          "    if (i == 0) return q[e];")],
+    # ring step: the received chunk decoded but not added
+    "reduce_drops_decoded": [("        for (uint64_t i = 0; i < n; ++i) acc[i] = acc[i] + local[i];",
+                              "        for (uint64_t i = 0; i < n; ++i) acc[i] = local[i];")],
+    # scatter pack: every segment read from the first displacement
+    "scatter_wrong_displacement": [(
+        "        const uint8_t* base = (const uint8_t*)x + displs[p] * (uint64_t)es;",
+        "        const uint8_t* base = (const uint8_t*)x + displs[0] * (uint64_t)es;")],
+    # scatter pack: each offset recorded after its own stream
+    "scatter_offset_after_stream": [
+        ("        seg_off[p] = pos;\n        uint64_t len = 0;", "        uint64_t len = 0;"),
+        ("        pos += len;\n    }", "        pos += len;\n        seg_off[p] = pos;\n    }")],
 }
 
 
@@ -86,6 +97,8 @@ def battery():
         ("heads_extremes", heads.test_negative_and_extreme_heads_round_trip),
         ("heads_closed_form", lambda: heads.test_length_closed_form_and_same_values_as_plain(5)),
         ("heads_constant_blocks", heads.test_constant_blocks_store_only_heads),
+        ("reduce_step", pins.test_reduce_step_is_decode_add_encode),
+        ("scatter_pack", pins.test_scatter_pack_is_concatenation),
     ]
     failed = []
     for name, fn in checks:
