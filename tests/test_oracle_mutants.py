@@ -76,6 +76,11 @@ MUTANTS = {
     "scatter_wrong_displacement": [(
         "        const uint8_t* base = (const uint8_t*)x + displs[p] * (uint64_t)es;",
         "        const uint8_t* base = (const uint8_t*)x + displs[0] * (uint64_t)es;")],
+    # range in FP32 instead of FP64 from the FP32 extremes
+    "range_in_fp32": [("    return rel * ((double)mx - (double)mn);",
+                       "    return rel * (double)(mx - mn);")],
+    # the running minimum seeded with 0 instead of the first element
+    "minmax_seeded_with_zero": [("        if (i == 0 || v < lo) lo = v;", "        if (v < lo) lo = v;")],
     # scatter pack: each offset recorded after its own stream
     "scatter_offset_after_stream": [
         ("        seg_off[p] = pos;\n        uint64_t len = 0;", "        uint64_t len = 0;"),
@@ -98,6 +103,8 @@ def battery():
         ("heads_closed_form", lambda: heads.test_length_closed_form_and_same_values_as_plain(5)),
         ("heads_constant_blocks", heads.test_constant_blocks_store_only_heads),
         ("reduce_step", pins.test_reduce_step_is_decode_add_encode),
+        ("relative_bound", pins.test_relative_bound_resolution),
+        ("bf16_input", pins.test_bf16_input_matches_widened_fp32),
         ("scatter_pack", pins.test_scatter_pack_is_concatenation),
     ]
     failed = []

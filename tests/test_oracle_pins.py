@@ -268,6 +268,13 @@ def test_relative_bound_resolution():
         assert oracle.eb_from_rel(rel, mn, mx) == rel * (float(x.max()) - float(x.min()))
     assert oracle.eb_from_rel(1e-3, 0.25, 0.25) == 1e-3
     assert oracle.eb_from_rel(1e-3, -7.5, -7.5) == 1e-3 * 7.5
+    # a range FP32 cannot hold: 2^24 + 2 - 1 = 2^24 + 1 is exact only in FP64
+    assert oracle.eb_from_rel(1.0, 1.0, 16777218.0) == 16777217.0
+    # extremes of one-signed inputs (neither is 0)
+    pos = np.float32([5.0, 3.0, 7.0, 4.5])
+    assert oracle.minmax(pos) == (3.0, 7.0)
+    assert oracle.minmax(-pos) == (-7.0, -3.0)
+    assert oracle.minmax(np.float32([2.5])) == (2.5, 2.5)
 
 
 def test_error_codes():
