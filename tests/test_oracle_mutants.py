@@ -25,6 +25,9 @@ import test_oracle_selector as tsel
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "zc_oracle.c")
 PKG = os.path.join(ROOT, "oracle", "__init__.py")
+# what a failing pin raises: an assertion, an oracle status error, or
+# pytest's own failure (pytest.raises that saw nothing raised)
+FAILURES = (Exception, pytest.fail.Exception)
 SEL = os.path.join(ROOT, "oracle", "selector.py")
 
 MUTANTS = {
@@ -81,6 +84,16 @@ MUTANTS = {
                        "    return rel * (double)(mx - mn);")],
     # the running minimum seeded with 0 instead of the first element
     "minmax_seeded_with_zero": [("        if (i == 0 || v < lo) lo = v;", "        if (v < lo) lo = v;")],
+    # BF16 output truncated instead of rounded to nearest even
+    "bf16_output_truncated": [("    u += 0x7fffu + lsb;", "    u += 0u * lsb;")],
+    # |q| = 2^22 rejected although it is in range
+    "range_limit_exclusive": [("    if (fabs(r) > 4194304.0) return O_ERR_RANGE;",
+                               "    if (fabs(r) >= 4194304.0) return O_ERR_RANGE;")],
+    # non-finite input not rejected
+    "nonfinite_unchecked": [("    if (!isfinite(x)) return O_ERR_NONFINITE;\n    double t",
+                             "    double t")],
+    # a stream whose width bytes disagree with its payload length accepted
+    "payload_sum_unchecked": [("    if (sum != h->payload) return O_ERR_FORMAT;", "")],
     # scatter pack: each offset recorded after its own stream
     "scatter_offset_after_stream": [
         ("        seg_off[p] = pos;\n        uint64_t len = 0;", "        uint64_t len = 0;"),
@@ -105,13 +118,15 @@ def battery():
         ("reduce_step", pins.test_reduce_step_is_decode_add_encode),
         ("relative_bound", pins.test_relative_bound_resolution),
         ("bf16_input", pins.test_bf16_input_matches_widened_fp32),
+        ("error_codes", pins.test_error_codes),
+        ("format_errors", pins.test_format_errors),
         ("scatter_pack", pins.test_scatter_pack_is_concatenation),
     ]
     failed = []
     for name, fn in checks:
         try:
             fn()
-        except Exception:  # an assertion or an oracle status error
+        except FAILURES:
             failed.append(name)
     return failed
 
@@ -191,7 +206,7 @@ def collective_battery():
     for name, fn in checks:
         try:
             fn()
-        except Exception:
+        except FAILURES:
             failed.append(name)
     return failed
 
@@ -258,7 +273,7 @@ def selector_battery():
         for a in args:
             try:
                 fn(*a)
-            except Exception:
+            except FAILURES:
                 failed.append(name)
                 break
     return failed

@@ -295,6 +295,13 @@ def test_error_codes():
     with pytest.raises(oracle.OracleError) as e:
         oracle.compress(big, 1e-3)
     assert e.value.status == oracle.ERR_RANGE
+    # |q| = 2^22 is the last level in range, on both sides (2 eb = 2^-9)
+    edge = np.float32([8192.0, -8192.0, 0.0])
+    np.testing.assert_array_equal(oracle.quantize(edge, 2.0 ** -10), [1 << 22, -(1 << 22), 0])
+    for v in (8192.001953125, -8192.001953125):
+        with pytest.raises(oracle.OracleError) as e:
+            oracle.quantize(np.float32([v]), 2.0 ** -10)
+        assert e.value.status == oracle.ERR_RANGE
     for eb in (0.0, -1.0, float("nan"), float("inf"), 1e-300):
         with pytest.raises(oracle.OracleError) as e:
             oracle.compress(x, eb)
@@ -311,6 +318,8 @@ def test_format_errors():
         lambda b: b.__setitem__(32, 25),               # width beyond 24
         lambda b: b.__setitem__(20, 9),                # nb inconsistent with n
         lambda b: b.__setitem__(24, b[24] ^ 4),        # payload size
+        lambda b: b.__setitem__(24, b[24] - 16),       # payload 16 short: still fits the stream
+        lambda b: b.__setitem__(32, b[32] + 1),        # a width that the payload size disagrees with
     ):
         b = bytearray(s)
         mutate(b)
