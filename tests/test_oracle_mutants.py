@@ -258,6 +258,31 @@ SEL_MUTANTS = {
     # the judge never rejects a prediction
     "judge_ignored": [('    if abs(float(y[k]) - math.log2(f[k])) > cfg["judge_log2"]:',
                        "    if False:")],
+    # statistics: sampled spans spaced from the wrong count
+    "span_spacing": [("    return [(SPAN * ((j * (m - 1)) // (S - 1)), SPAN) for j in range(S)]",
+                      "    return [(SPAN * ((j * m) // S), SPAN) for j in range(S)]")],
+    # statistics: spread of the spans' bits as a sample standard deviation
+    "spread_with_ddof1": [("    f[13] = float(np.sqrt(np.mean((per_span - per_span.mean()) ** 2)))",
+                           "    f[13] = float(np.std(per_span, ddof=1)) if len(per_span) > 1 else 0.0")],
+    # statistics: sign changes that count zero deltas too
+    "sign_changes_with_zeros": [("        f[11] = sum(int((v[1:] * v[:-1] < 0).sum()) for v in d) / nd2",
+                                 "        f[11] = sum(int((v[1:] * v[:-1] <= 0).sum()) for v in d) / nd2")],
+    # statistics: block heads taken every 16 elements instead of every 32
+    "head_stride": [("    heads = [bitlen(abs(int(q[b0]))) for q in qs for b0 in range(0, len(q), 32)]",
+                     "    heads = [bitlen(abs(int(q[b0]))) for q in qs for b0 in range(0, len(q), 16)]")],
+    # statistics: zero-delta share over the second differences' count
+    "zero_delta_share": [("        f[7] = sum(int((v == 0).sum()) for v in d) / nd",
+                          "        f[7] = sum(int((v == 0).sum()) for v in d) / max(nd - len(d), 1)")],
+    # statistics: share of nonzero instead of zero levels
+    "zero_level_share": [("    f[8] = int((allq == 0).sum()) / tot", "    f[8] = int((allq != 0).sum()) / tot")],
+    # statistics: raw bits of FP32 and BF16 swapped
+    "raw_bits_swapped": [("    raw_bits = 32 if x.dtype == np.float32 else 16",
+                          "    raw_bits = 16 if x.dtype == np.float32 else 32")],
+    # statistics: natural instead of binary logarithm of the chunk length
+    "length_natural_log": [("    f[15] = math.log2(n_c) / 16.0", "    f[15] = math.log(n_c) / 16.0")],
+    # statistics: the level range without its +1
+    "range_without_one": [("    f[4] = math.log2(1 + int(allq.max()) - int(allq.min()))",
+                           "    f[4] = math.log2(max(int(allq.max()) - int(allq.min()), 1))")],
     # a raw chunk's header not charged on the link
     "raw_header_free": [('    raw = bytes_in * cfg["raw_ns_per_byte"] + (32.0 + bytes_in) / link',
                          '    raw = bytes_in * cfg["raw_ns_per_byte"] + bytes_in / link')],

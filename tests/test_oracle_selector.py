@@ -2,6 +2,7 @@
 values, the codec oracle's own encoder and finite differences -- nothing here
 re-types the oracle's formulas."""
 import math
+import statistics
 
 import numpy as np
 import pytest
@@ -74,6 +75,13 @@ def test_ramp_widths_by_hand():
         assert f[k] == pytest.approx(bits / 2048 + 8.0 / L + 256.0 / n, rel=1e-15)
     assert f[7] == 0 and f[11] == 0 and f[10] == 0  # constant unit steps
     assert f[5] == pytest.approx(1.0)
+    # block heads every 32 elements of a span: q = a at element a
+    heads = [(128 * s + b).bit_length() for s in hand for b in (0, 32, 64, 96)]
+    assert f[12] == pytest.approx(sum(heads) / len(heads) / 24.0, rel=1e-15)
+    # spread (population standard deviation) of the spans' L = 32 bits per element
+    per_span = [sum((max(a, 1).bit_length() + 1) * 32 for a in range(128 * s, 128 * s + 128, 32))
+                / 128 for s in hand]
+    assert f[13] == pytest.approx(statistics.pstdev(per_span), rel=1e-12)
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
