@@ -94,6 +94,17 @@ MUTANTS = {
                              "    double t")],
     # a stream whose width bytes disagree with its payload length accepted
     "payload_sum_unchecked": [("    if (sum != h->payload) return O_ERR_FORMAT;", "")],
+    # quotient taken in FP32 (a second rounding before rint)
+    "quotient_in_fp32": [("    double t = (double)x / (double)two_eb;",
+                          "    double t = (double)(x / two_eb);")],
+    # raw stream not padded to 16 bytes
+    "raw_unpadded": [("    uint64_t total = O_HEADER + pad16(payload);\n    *out_len = total;\n    if (total > cap) return O_ERR_CAPACITY;\n    memset(out, 0, total);\n    write_header(out, dtype, 5, 1,",
+                      "    uint64_t total = O_HEADER + payload;\n    *out_len = total;\n    if (total > cap) return O_ERR_CAPACITY;\n    memset(out, 0, total);\n    write_header(out, dtype, 5, 1,")],
+    # heads apart: head field written big-endian
+    "head_field_big_endian": [("            p[0] = (uint8_t)h;\n            p[1] = (uint8_t)(h >> 8);\n            p[2] = (uint8_t)(h >> 16);",
+                               "            p[2] = (uint8_t)h;\n            p[1] = (uint8_t)(h >> 8);\n            p[0] = (uint8_t)(h >> 16);")],
+    # the block count recorded one too high
+    "block_count_plus_one": [("    put_u32(out + 20, nb);", "    put_u32(out + 20, nb + (nb > 0));")],
     # scatter pack: each offset recorded after its own stream
     "scatter_offset_after_stream": [
         ("        seg_off[p] = pos;\n        uint64_t len = 0;", "        uint64_t len = 0;"),
@@ -119,6 +130,7 @@ def battery():
         ("relative_bound", pins.test_relative_bound_resolution),
         ("bf16_input", pins.test_bf16_input_matches_widened_fp32),
         ("error_codes", pins.test_error_codes),
+        ("raw_stream", pins.test_raw_stream_round_trip),
         ("format_errors", pins.test_format_errors),
         ("scatter_pack", pins.test_scatter_pack_is_concatenation),
     ]
