@@ -47,6 +47,8 @@
  * form of the stream length, exact-rational checks of the quantizer, the
  * elementwise error bound, brute-force round trips on tiny inputs and the
  * special cases (zeros, constants, ramps) whose streams follow by hand.
+ * tests/test_oracle_mutants.py plants one mistake at a time in a copy of this
+ * file and checks that a pin fails.
  */
 #include <math.h>
 #include <stdint.h>
