@@ -400,6 +400,17 @@ def test_format_errors(zc):
         ws = zc.Workspace(5000, 1)
         zc.decompress(cmp, 5000, ws=ws)
         assert ws.status()[0] == zc.ERR_FORMAT, pos
+    # width bytes that disagree with the header's payload size, while every
+    # plane still lies inside the buffer: the width scan's total decides
+    short = bytearray(good)
+    short[24:32] = (oracle.header(good)["payload"] - 16).to_bytes(8, "little")
+    wider = bytearray(good)
+    wider[32] = wider[32] + 1 if wider[32] < 24 else 23
+    for b in (short, wider):
+        cmp = torch.frombuffer(b, dtype=torch.uint8).cuda()
+        ws = zc.Workspace(5000, 1)
+        zc.decompress(cmp, 5000, ws=ws)
+        assert ws.status()[0] == zc.ERR_FORMAT
     cmp = torch.frombuffer(bytearray(good), dtype=torch.uint8).cuda()
     ws = zc.Workspace(5000, 1)
     zc.decompress(cmp, 4999, ws=ws)  # wrong n
