@@ -1045,10 +1045,10 @@ def cpu_fields(side):
     ring = [workloads.stacking_rank(base, r, seed=3000).cpu().numpy() for r in range(P_RING)]
     msgs, tot = [], 0
     for sp in workloads.message_specs(1000):
+        if tot + sp["n"] * (4 if sp["dtype"] == "f32" else 2) > 16 << 20:
+            continue  # keep the sample bounded: skip (without drawing) what does not fit
         t = workloads.message(sp, device=dev)
         a = t.cpu().numpy() if t.dtype == torch.float32 else workloads.bf16_bits(t)
-        if tot + a.nbytes > 16 << 20:
-            continue  # keep the sample bounded: skip what does not fit
         msgs.append((a, sp["eb"]))
         tot += a.nbytes
         if len(msgs) >= 64:
