@@ -336,18 +336,22 @@ def chunk_bounds(n: int, P: int):
     return b
 
 
-def ring_allreduce(ranks, eb_abs: float, log2L: int = 5):
+def ring_allreduce(ranks, eb_abs: float, log2L: int = 5, stage_bytes=None):
     """Simulated ring Allreduce (Sec. 3.3.3): the reduce-scatter of
     ``ring_reduce_scatter`` whose last step also re-encodes the full sum (the
     Allgather stage's one compression), then the Allgather stage: every rank
     decodes the P - 1 chunks it does not own; it keeps its own chunk as the
     FP32 sum.  Returns the P result buffers and the P final chunk streams
-    (stream c encodes chunk c)."""
+    (stream c encodes chunk c).  If ``stage_bytes`` is a list, the total
+    length of the P streams written at every stage (the first compression,
+    then each step) is appended to it (bookkeeping only)."""
     P = len(ranks)
     n = ranks[0].size
     bounds = chunk_bounds(n, P)
     chunk = lambda r, c: ranks[r][bounds[c]:bounds[c + 1]]
     sent = [reduce_step(None, chunk(r, r), eb_abs, log2L)[0] for r in range(P)]
+    if stage_bytes is not None:
+        stage_bytes.append(sum(map(len, sent)))
     own = [None] * P
     final = [None] * P
     for t in range(P - 1):
@@ -362,6 +366,8 @@ def ring_allreduce(ranks, eb_abs: float, log2L: int = 5):
                 own[r] = sm
                 final[c] = s
         sent = new
+        if stage_bytes is not None:
+            stage_bytes.append(sum(map(len, sent)))
     if P == 1:
         own[0] = np.asarray(ranks[0], np.float32).copy()
         final[0] = sent[0]

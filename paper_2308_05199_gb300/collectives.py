@@ -30,6 +30,39 @@ import torch
 from . import zc
 
 
+U32 = 2.0 ** -24  # unit roundoff of FP32 round-to-nearest
+
+
+def ring_error_bounds(P: int, eb: float, abs_sum):
+    """Worst-case |result - exact sum| per element of the ring Allreduce of P
+    ranks at the absolute bound eb (the FP32 bound the codec uses); abs_sum
+    is sum_r |x_r| of the element (a float or an array).
+
+    A decoded value carries at most eb of quantization error (Sec. 3.3.3:
+    one compression per reduce-scatter step, N - 1 in all) plus the FP32
+    rounding of q * 2eb; an FP32 addition rounds once more.  Every partial
+    sum is at most abs_sum + E in magnitude, E the bound itself, so after
+    the P - 1 steps
+        E = (P - 1) eb + 2 (P - 1) u (abs_sum + E),   u = 2^-24,
+    solved for E: the bound of the chunk a rank reduced itself (kept as the
+    FP32 sum).  The chunks a rank decodes in the Allgather stage carry one
+    more compression and one more rounding:
+        E_dec = E + eb + u (abs_sum + E + eb).
+    Returns (E, E_dec)."""
+    k = P - 1
+    own = (k * eb + 2 * k * U32 * abs_sum) / (1.0 - 2 * k * U32)
+    dec = own + eb + U32 * (abs_sum + own + eb)
+    return own, dec
+
+
+def ring_target_bound(P: int, eb: float, abs_sum):
+    """The stated per-element target for the reduced sums, (P - 1) eb +
+    1e-6 sum_r |x_r|.  Its sum term covers the worst-case FP32 roundings
+    only while 2 (P - 1) 2^-24 <= 1e-6 (P <= 9); for larger rings it is a
+    measured property of the data."""
+    return (P - 1) * eb + 1e-6 * abs_sum
+
+
 def chunk_bounds(n: int, P: int):
     """Chunk c of a rank buffer is [b[c], b[c + 1]): equal parts, the remainder
     spread over the first chunks."""
