@@ -166,9 +166,8 @@ def kernel_times(samples):
 # The sources the encoder kernels (k_compress, k_batch, k_reduce, k_scatter) are
 # built from: a DRAM-traffic figure taken with ncu stays valid while these are
 # unchanged.
-ENCODER_SOURCES = ("zc_device.cuh", "zc_codec.cuh", "zc_launch.h", "zc_kbatch4.cu",
-                   "zc_kbatch8.cu", "zc_kbatch16.cu", "zc_k16.cu", "zc_k32.cu", "zc_k64.cu",
-                   "zc_k128.cu")
+ENCODER_SOURCES = ("zc_device.cuh", "zc_codec.cuh", "zc_launch.h", "zc_kbatch.cu",
+                   "zc_kenc.cu")
 
 
 def source_hash() -> str:
@@ -669,6 +668,70 @@ def heads_report(torch, zc, W, reps=5):
     return out
 
 
+L2_BYTES = 129 << 20  # GB300 L2
+
+
+def config1_report(torch, zc, workloads, stream, device, reps=20):
+    """The small correctness workload: 2^20 FP32 sinusoids (4 MiB, fits in
+    L2), absolute bound 1e-4, L = 32.  Before every timed call a buffer of
+    twice the L2 size is written, so the input starts in HBM; compression
+    and decompression are timed alone (CUDA events on the launch stream),
+    best and median of `reps`.  GB/s on algorithmic bytes (compress: 4n + |C|;
+    decompress: |C| + 4n); ratio; largest |x - x^| over eb."""
+    n, eb = 1 << 20, 1e-4
+    with torch.cuda.stream(stream):
+        x = workloads.sinusoids_1d(n, seed=1000, device=device)
+    stream.synchronize()
+    s = stream.cuda_stream
+    ws = zc.Workspace(n, 1, device, stream)
+    cap = zc.zc_max_compressed_bytes(n, BLOCK)
+    cmp = torch.empty(cap, dtype=torch.uint8, device=device)
+    nb = torch.zeros(1, dtype=torch.int64, device=device)
+    y = torch.empty(n, dtype=torch.float32, device=device)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=device)
+
+    def comp():
+        zc._check(zc.zc_compress(x.data_ptr(), n, zc.F32, zc.EB_ABS, eb, BLOCK, cmp.data_ptr(),
+                                 cap, nb.data_ptr(), ws.ptr, ws.nbytes, s), "zc_compress")
+
+    def dec():
+        zc._check(zc.zc_decompress(cmp.data_ptr(), cap, y.data_ptr(), n, zc.F32, ws.ptr,
+                                   ws.nbytes, s), "zc_decompress")
+
+    def timed(f):
+        ts = []
+        for i in range(reps + 3):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f()
+            e1.record(stream)
+            e1.synchronize()
+            if i >= 3:
+                ts.append(e0.elapsed_time(e1))
+        return min(ts), statistics.median(ts)
+
+    cb, cm = timed(comp)
+    C = int(nb.item())
+    db, dm = timed(dec)
+    with torch.cuda.stream(stream):
+        err = float((y.double() - x.double()).abs().max())
+    st, _ = ws.status(stream)
+    del flush
+    torch.cuda.empty_cache()
+    eb_f = float(torch.tensor(eb, dtype=torch.float32))
+    return {"n": n, "eb_abs": eb, "block": BLOCK, "status": st, "ratio": round(4 * n / C, 3),
+            "compress_ms_best": round(cb, 4), "compress_ms_median": round(cm, 4),
+            "compress_gbs_best": round((4 * n + C) / cb / 1e6, 1),
+            "compress_gbs_median": round((4 * n + C) / cm / 1e6, 1),
+            "decompress_ms_best": round(db, 4), "decompress_ms_median": round(dm, 4),
+            "decompress_gbs_best": round((4 * n + C) / db / 1e6, 1),
+            "decompress_gbs_median": round((4 * n + C) / dm / 1e6, 1),
+            "max_err_over_eb": round(err / eb_f, 6),
+            "l2": "flushed before every call (%d MB written)" % (2 * L2_BYTES >> 20)}
+
+
 def bound_sweep(torch, zc, W, rels=(1e-2, 1e-3, 1e-4), reps=5):
     """The 512^3 field at three relative bounds (range + compress, and
     decompress, L = 32): ratio, GB/s (algorithmic bytes as the step's rows)
@@ -878,6 +941,7 @@ def run_ours(args, rank, world):
     sweep = size_sweep(torch, zc, workloads, W.stream, dev) if args.sweep else None
     heads = heads_report(torch, zc, W)
     bounds = bound_sweep(torch, zc, W)
+    cfg1 = config1_report(torch, zc, workloads, W.stream, dev)
     coll = collectives_report(torch, workloads, W.stream, dev,
                               [int(v) for v in args.collective_ranks.split(",") if v],
                               args.ring_side) if args.collective_ranks else None
@@ -959,6 +1023,7 @@ def run_ours(args, rank, world):
         "size_sweep": sweep,
         "heads_apart": heads,
         "bound_sweep": bounds,
+        "config1": cfg1,
     }
     if not args.no_e2e:
         out["e2e"] = e2e_ours(torch, W, args, step_bytes, world)
@@ -1167,6 +1232,31 @@ def cpu_parallel(x, msgs, sample_n):
             "seconds": round(secs, 2)}
 
 
+def oracle_config1(reps=5):
+    """The oracle on the small correctness workload (2^20 FP32 sinusoids,
+    absolute bound 1e-4, L = 32), single-threaded: best and median of reps
+    compressions and decompressions, GB/s on the same algorithmic bytes as
+    the GPU's."""
+    import oracle
+    from paper_2308_05199_gb300 import workloads
+    x = workloads.sinusoids_1d(1 << 20, seed=1000).numpy()
+    n = x.size
+    tc, td = [], []
+    for _ in range(reps):
+        t = time.perf_counter()
+        s = oracle.compress(x, 1e-4, 5)
+        tc.append(time.perf_counter() - t)
+        t = time.perf_counter()
+        oracle.decompress(s, n)
+        td.append(time.perf_counter() - t)
+    b = 4 * n + len(s)
+    return {"cores": 1, "ratio": round(4 * n / len(s), 3),
+            "compress_gbs_best": round(b / min(tc) / 1e9, 4),
+            "compress_gbs_median": round(b / statistics.median(tc) / 1e9, 4),
+            "decompress_gbs_best": round(b / min(td) / 1e9, 4),
+            "decompress_gbs_median": round(b / statistics.median(td) / 1e9, 4)}
+
+
 def cpu_baseline(side, sample_n=1 << 25):
     x, ring, msgs, chunks = cpu_fields(side)
     sample_n = min(sample_n, x.size)
@@ -1178,7 +1268,8 @@ def cpu_baseline(side, sample_n=1 << 25):
                       "1000 messages, %d chunks of 64 KiB through the selector; single-threaded "
                       "plain C and numpy" % (sample_n, len(msgs), len(chunks)),
             "seconds": round(secs, 2),
-            "parallel": cpu_parallel(x, msgs, x.size)}
+            "parallel": cpu_parallel(x, msgs, x.size),
+            "config1": oracle_config1()}
 
 
 def run_reference(args):

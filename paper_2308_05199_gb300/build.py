@@ -34,8 +34,27 @@ def _flags(extra=()):
                    "-I", os.path.join(ROOT, "include"), "-I", CSRC] + list(extra)
 
 
+# Sources compiled more than once, with one macro value per object: the
+# encoder kernels once per block size, the batch kernel once per tile size
+# (the heavy instantiations then compile in parallel).
+VARIANTS = {
+    "zc_kenc.cu": [("zc_kenc_l%d" % (1 << lg), ["-DZC_LOG2L=%d" % lg]) for lg in (4, 5, 6, 7)],
+    "zc_kbatch.cu": [("zc_kbatch_u%d" % u, ["-DZC_BATCH_U=%d" % u]) for u in (32, 64, 128)],
+}
+
+
 def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+
+
+def _units():
+    """(source, object name, extra flags) of every object of the library."""
+    out = []
+    for src in _sources():
+        name = os.path.basename(src)
+        for obj, defs in VARIANTS.get(name, [(name[:-3], [])]):
+            out.append((src, obj, defs))
+    return out
 
 
 def _deps():
@@ -57,9 +76,10 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     cc = nvcc()
     objs = []
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, "-c", src, "-o", obj] + _flags(extra)
+    def compile_one(unit):
+        src, name, defs = unit
+        obj = os.path.join(BUILD, name + ".o")
+        cmd = [cc, "-c", src, "-o", obj] + _flags(list(defs) + list(extra))
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))
@@ -67,9 +87,9 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             sys.stderr.write(r.stdout + r.stderr)
         return obj
 
-    srcs = _sources()
-    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(compile_one, srcs))
+    units = _units()
+    with cf.ThreadPoolExecutor(max_workers=min(len(units), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(compile_one, units))
     tmp = LIB + ".%d.tmp" % os.getpid()
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-ldl",
                                                          "-lpthread"]

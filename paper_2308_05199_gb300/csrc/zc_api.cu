@@ -186,20 +186,20 @@ cudaError_t launch_compress_any(int lg, int S, int dt, const Launch& P, unsigned
                                 cudaStream_t s)
 {
     switch (lg) {
-    case 4: return launch_compress_l16(S, dt, P, grid, s);
-    case 5: return launch_compress_l32(S, dt, P, grid, s);
-    case 6: return launch_compress_l64(S, dt, P, grid, s);
-    default: return launch_compress_l128(S, dt, P, grid, s);
+    case 4: return launch_compress_lg<4>(S, dt, P, grid, s);
+    case 5: return launch_compress_lg<5>(S, dt, P, grid, s);
+    case 6: return launch_compress_lg<6>(S, dt, P, grid, s);
+    default: return launch_compress_lg<7>(S, dt, P, grid, s);
     }
 }
 
 cudaError_t launch_reduce_any(int lg, int S, const Launch& P, unsigned grid, cudaStream_t s)
 {
     switch (lg) {
-    case 4: return launch_reduce_l16(S, P, grid, s);
-    case 5: return launch_reduce_l32(S, P, grid, s);
-    case 6: return launch_reduce_l64(S, P, grid, s);
-    default: return launch_reduce_l128(S, P, grid, s);
+    case 4: return launch_reduce_lg<4>(S, P, grid, s);
+    case 5: return launch_reduce_lg<5>(S, P, grid, s);
+    case 6: return launch_reduce_lg<6>(S, P, grid, s);
+    default: return launch_reduce_lg<7>(S, P, grid, s);
     }
 }
 
@@ -207,19 +207,19 @@ cudaError_t launch_scatter_any(int lg, int C, int dt, const Launch& P, const Sca
                                unsigned grid, cudaStream_t s)
 {
     switch (lg) {
-    case 4: return launch_scatter_l16(C, dt, P, S, grid, s);
-    case 5: return launch_scatter_l32(C, dt, P, S, grid, s);
-    case 6: return launch_scatter_l64(C, dt, P, S, grid, s);
-    default: return launch_scatter_l128(C, dt, P, S, grid, s);
+    case 4: return launch_scatter_lg<4>(C, dt, P, S, grid, s);
+    case 5: return launch_scatter_lg<5>(C, dt, P, S, grid, s);
+    case 6: return launch_scatter_lg<6>(C, dt, P, S, grid, s);
+    default: return launch_scatter_lg<7>(C, dt, P, S, grid, s);
     }
 }
 
 cudaError_t launch_batch(int C, const Launch& P, unsigned grid, cudaStream_t s)
 {
     switch (C) {
-    case 4: return launch_batch_c4(P, grid, s);
-    case 8: return launch_batch_c8(P, grid, s);
-    default: return launch_batch_c16(P, grid, s);
+    case 4: return launch_batch_u<32>(P, grid, s);
+    case 8: return launch_batch_u<64>(P, grid, s);
+    default: return launch_batch_u<128>(P, grid, s);
     }
 }
 
@@ -292,10 +292,10 @@ cudaError_t launch_compress_heads_any(int lg, int dt, const Launch& P, unsigned 
                                       cudaStream_t s)
 {
     switch (lg) {
-    case 4: return launch_compress_heads_l16(dt, P, grid, s);
-    case 5: return launch_compress_heads_l32(dt, P, grid, s);
-    case 6: return launch_compress_heads_l64(dt, P, grid, s);
-    default: return launch_compress_heads_l128(dt, P, grid, s);
+    case 4: return launch_compress_heads_lg<4>(dt, P, grid, s);
+    case 5: return launch_compress_heads_lg<5>(dt, P, grid, s);
+    case 6: return launch_compress_heads_lg<6>(dt, P, grid, s);
+    default: return launch_compress_heads_lg<7>(dt, P, grid, s);
     }
 }
 

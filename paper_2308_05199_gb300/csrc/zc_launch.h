@@ -24,38 +24,23 @@ inline cudaError_t smem_limit(int bytes)
     return e;
 }
 
-// One translation unit per block size instantiates the encoder kernels for
-// every tile size S (sub-tiles of 2048 elements per CTA tile); these pick the
-// instantiation at run time.
-cudaError_t launch_compress_l16(int S, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_compress_l32(int S, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_compress_l64(int S, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_compress_l128(int S, int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_compress_heads_l16(int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_compress_heads_l32(int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_compress_heads_l64(int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_compress_heads_l128(int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_reduce_l16(int S, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_reduce_l32(int S, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_reduce_l64(int S, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_reduce_l128(int S, const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_scatter_l16(int S, int x_dtype, const Launch& P, const ScatterParams& SP, unsigned grid, cudaStream_t s);
-cudaError_t launch_scatter_l32(int S, int x_dtype, const Launch& P, const ScatterParams& SP, unsigned grid, cudaStream_t s);
-cudaError_t launch_scatter_l64(int S, int x_dtype, const Launch& P, const ScatterParams& SP, unsigned grid, cudaStream_t s);
-cudaError_t launch_scatter_l128(int S, int x_dtype, const Launch& P, const ScatterParams& SP, unsigned grid, cudaStream_t s);
-// Batched compression (one translation unit per tile size).
-cudaError_t launch_batch_c4(const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_batch_c8(const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_batch_c16(const Launch& P, unsigned grid, cudaStream_t s);
-
+// Launchers of the encoder kernels at block size 2^LG; each is defined and
+// explicitly instantiated by the object of zc_kenc.cu built for that LG.
+// `chunks` is the tile size in 2048-element chunks (4, 8 or 16); these pick
+// the kernel instantiation at run time.
+template <int LG>
+cudaError_t launch_compress_lg(int chunks, int x_dtype, const Launch& P, unsigned grid,
+                               cudaStream_t s);
+template <int LG>
+cudaError_t launch_compress_heads_lg(int x_dtype, const Launch& P, unsigned grid, cudaStream_t s);
+template <int LG>
+cudaError_t launch_reduce_lg(int chunks, const Launch& P, unsigned grid, cudaStream_t s);
+template <int LG>
+cudaError_t launch_scatter_lg(int chunks, int x_dtype, const Launch& P, const ScatterParams& SP,
+                              unsigned grid, cudaStream_t s);
+// Batched compression with warp units of U rows (defined per U by zc_kbatch.cu).
 template <int U>
-cudaError_t launch_batch_u(const Launch& P, unsigned grid, cudaStream_t s)
-{
-    const cudaError_t e = smem_limit<k_batch<U>>(enc_smem_bytes(U));
-    if (e != cudaSuccess) return e;
-    k_batch<U><<<grid, ENC_THREADS, enc_smem_bytes(U), s>>>(P);
-    return cudaGetLastError();
-}
+cudaError_t launch_batch_u(const Launch& P, unsigned grid, cudaStream_t s);
 
 cudaError_t launch_wscan(const Launch& P, unsigned grid, cudaStream_t s);
 cudaError_t launch_decompress(const Launch& P, unsigned grid, cudaStream_t s);
