@@ -715,12 +715,15 @@ def config1_report(torch, zc, workloads, stream, device, reps=20):
     cb, cm = timed(comp)
     C = int(nb.item())
     db, dm = timed(dec)
+    eb_f = float(torch.tensor(eb, dtype=torch.float32))
     with torch.cuda.stream(stream):
-        err = float((y.double() - x.double()).abs().max())
+        e = (y.double() - x.double()).abs()
+        err = float(e.max())
+        # the codec's bound: eb (of the quantization) plus half an FP32 ulp of x^
+        over = float((e / (eb_f + 2.0 ** -24 * y.double().abs())).max())
     st, _ = ws.status(stream)
     del flush
     torch.cuda.empty_cache()
-    eb_f = float(torch.tensor(eb, dtype=torch.float32))
     return {"n": n, "eb_abs": eb, "block": BLOCK, "status": st, "ratio": round(4 * n / C, 3),
             "compress_ms_best": round(cb, 4), "compress_ms_median": round(cm, 4),
             "compress_gbs_best": round((4 * n + C) / cb / 1e6, 1),
@@ -728,7 +731,8 @@ def config1_report(torch, zc, workloads, stream, device, reps=20):
             "decompress_ms_best": round(db, 4), "decompress_ms_median": round(dm, 4),
             "decompress_gbs_best": round((4 * n + C) / db / 1e6, 1),
             "decompress_gbs_median": round((4 * n + C) / dm / 1e6, 1),
-            "max_err_over_eb": round(err / eb_f, 6),
+            "max_err_over_eb": round(err / eb_f, 6), "max_err_over_bound": round(over, 6),
+            "bound": "eb + 2^-24 |x^| per element",
             "l2": "flushed before every call (%d MB written)" % (2 * L2_BYTES >> 20)}
 
 
@@ -764,11 +768,15 @@ def bound_sweep(torch, zc, W, rels=(1e-2, 1e-3, 1e-4), reps=5):
         td = timed(d)
         eb = float(torch.tensor(rel * (hi - lo), dtype=torch.float32))
         with torch.cuda.stream(st):
-            err = float((W.dec - W.field).abs().max())
+            e = (W.dec.double() - W.field.double()).abs()
+            err = float(e.max())
+            over = float((e / (eb + 2.0 ** -24 * W.dec.double().abs())).max())
+            del e
         out.append({"rel": rel, "eb_abs": eb, "ratio": round(4 * n / C, 3),
                     "compress_gbs": round((8 * n + C) / tc / 1e6, 1),
                     "decompress_gbs": round((4 * n + C) / td / 1e6, 1),
-                    "max_err_over_eb": round(err / eb, 4)})
+                    "max_err_over_eb": round(err / eb, 4),
+                    "max_err_over_bound": round(over, 6)})
     st.synchronize()
     return {"status": W.ws.status()[0], "points": out}
 

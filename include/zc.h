@@ -75,7 +75,10 @@ typedef enum {
     ZC_ERR_FORMAT = 5,    /* malformed or mismatched input stream              */
     ZC_ERR_TIMEOUT = 6,   /* a device-side wait gave up (see zc_set_wait_limit)*/
     ZC_ERR_CUDA = 7,      /* a CUDA runtime call failed                        */
-    ZC_ERR_WORKSPACE = 8  /* workspace too small or not initialised            */
+    ZC_ERR_WORKSPACE = 8, /* workspace too small or not initialised            */
+    ZC_ERR_BOUNDS = 9     /* bounds-checked build only: a kernel access fell
+                             outside its buffer and was skipped (the status
+                             detail is the offending offset)                  */
 } zc_status;
 
 typedef enum { ZC_F32 = 0, ZC_BF16 = 1 } zc_dtype;
@@ -249,6 +252,8 @@ typedef struct {
     int tile_chunks;         /* compression tile: chunks of 2048 elements     */
     int grid;                /* CTAs launched; 0 = as many as allowed         */
     int decompress;          /* 0: compression plan, 1: decompression plan    */
+    int grouped;             /* 1: streams packed grouped by block size
+                                (zc_batch_set_grouped); 0 after planning      */
     uint64_t total_tiles;    /* tiles of all messages together                */
     uint64_t total_chunks;   /* decompression: width-scan chunks              */
     const void* d_table;     /* the descriptor table (device)                 */
@@ -301,6 +306,26 @@ int zc_plan_decompress_streams(zc_batch* plan, int n_msgs, const void* const* h_
 
 /* Launch a decompression plan on s (a width-scan and a decode kernel). */
 int zc_decompress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_stream_t s);
+
+/* Group a batch by block size (no counterpart in the paper).  A batch whose
+ * neighbouring tiles use different block sizes makes the CTAs of one SM run
+ * different encoder variants at once, which measured about twice as slow as
+ * one block size throughout; grouped, a mixed batch runs at the mean of the
+ * block sizes' own rates.  On a compression plan (grouped = 1), every
+ * zc_compress_batch launch first orders the messages' tiles by block size
+ * (raw, 16, 32, 64, 128; message order within a size) from the block sizes
+ * in the device table at that moment -- so a selection written there by
+ * zc_batch_select earlier on the same stream takes effect, also inside a
+ * CUDA graph -- and packs the streams in that order: d_msg_off[i] is still
+ * message i's start and d_msg_off[M] the packed length, but stream i need
+ * not end where stream i + 1 starts (its header gives its length).  Three
+ * small extra launches; the table's tile starts are rewritten on the device
+ * (set again after every zc_plan_compress_batch, which clears the flag).  On
+ * a decompression plan made with zc_plan_decompress_batch (grouped = 1), a
+ * stream is bounded by d_msg_off[M] instead of d_msg_off[i + 1].  The streams
+ * themselves are unchanged.  Host-only; ZC_ERR_ARG for a null plan, a value
+ * other than 0 or 1, or a decompression plan without stream offsets. */
+int zc_batch_set_grouped(zc_batch* plan, int grouped);
 
 /* Autotuner for batched compression.  Times zc_compress_batch on the given
  * messages for every candidate tile size (4, 8, 16 chunks) and grid (1, 2 and

@@ -19,6 +19,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libzc.so")
+# The bounds-checked variant (-DZC_DEBUG): every checked kernel access is
+# tested against its buffer; a failed check reports ZC_ERR_BOUNDS and skips
+# the access.  Loaded instead of the release library when ZC_LIBRARY=debug.
+DEBUG_BUILD = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(DEBUG_BUILD, "libzc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -62,23 +67,28 @@ def _deps():
         glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(ROOT, "include", "zc.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and not extra and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), debug: bool = False) -> str:
+    """Compile the library (the bounds-checked variant when `debug`) unless it
+    is newer than every source; returns its path."""
+    out_dir, lib = (DEBUG_BUILD, DEBUG_LIB) if debug else (BUILD, LIB)
+    if not force and not extra and up_to_date(lib):
+        return lib
+    if debug:
+        extra = ["-DZC_DEBUG"] + list(extra)
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     objs = []
 
     def compile_one(unit):
         src, name, defs = unit
-        obj = os.path.join(BUILD, name + ".o")
+        obj = os.path.join(out_dir, name + ".o")
         cmd = [cc, "-c", src, "-o", obj] + _flags(list(defs) + list(extra))
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -90,14 +100,14 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     units = _units()
     with cf.ThreadPoolExecutor(max_workers=min(len(units), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, units))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-ldl",
                                                          "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -167,6 +167,7 @@ Launch base_launch(const WsView& w)
     P.urows = DEC_U;
     P.ring = w.ring;
     P.ring_bytes = w.ring_bytes;
+    P.ws_cap = w.cap;
     P.wc.limit_ns = g_wait_ns;
     P.wc.withhold = g_withhold;
     return P;
@@ -229,7 +230,11 @@ inline uint64_t elem_bytes(int dtype) { return dtype == ZC_F32 ? 4 : 2; }
 
 extern "C" {
 
+#ifdef ZC_DEBUG
+const char* zc_version(void) { return "zc 0.1 (sm_103a, bounds-checked)"; }
+#else
 const char* zc_version(void) { return "zc 0.1 (sm_103a)"; }
+#endif
 
 size_t zc_max_compressed_bytes(uint64_t n, int block)
 {
@@ -729,7 +734,17 @@ int zc_compress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_stre
     if (grid > plan->total_tiles) grid = plan->total_tiles;
     grid = enc_grid(grid, unit_rows(C), w);
     if (grid == 0) return ZC_ERR_WORKSPACE;
-    if (plan->n_msgs > 1) {
+    if (plan->grouped) {
+        // first tickets by block size, rewritten on the device from the table's
+        // current block sizes (a selection made earlier on this stream included);
+        // the per-CTA class sums use the decoder offsets' array, idle here
+        if ((uint64_t)((plan->n_msgs + 255) / 256) * 5 > 2 * w.cap) return ZC_ERR_WORKSPACE;
+        if (launch_group((Item*)plan->d_table, P.n_items, (unsigned*)w.offs, w.tile_map,
+                         (cudaStream_t)s) != cudaSuccess)
+            return ZC_ERR_CUDA;
+        P.tile_map = w.tile_map;
+        P.grouped = 1;
+    } else if (plan->n_msgs > 1) {
         if (launch_tile_map(P.items, P.n_items, P.total_tiles, w.tile_map, (cudaStream_t)s) !=
             cudaSuccess)
             return ZC_ERR_CUDA;
@@ -844,6 +859,7 @@ int zc_decompress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_st
     P.in_base = (const uint8_t*)plan->d_packed;
     P.in_off = (const unsigned long long*)plan->d_msg_off;
     P.in_cap = plan->packed_cap;
+    P.grouped = plan->grouped;
     P.total_tiles = (unsigned)plan->total_chunks;
     if (launch_wscan(P, (unsigned)plan->total_chunks, (cudaStream_t)s) != cudaSuccess)
         return ZC_ERR_CUDA;
@@ -855,6 +871,14 @@ int zc_decompress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_st
         P.tile_map = w.tile_map;
     }
     return cuda_status(launch_decompress(P, (unsigned)plan->total_tiles, (cudaStream_t)s));
+}
+
+int zc_batch_set_grouped(zc_batch* plan, int grouped)
+{
+    if (plan == nullptr || (grouped != 0 && grouped != 1)) return ZC_ERR_ARG;
+    if (grouped && plan->decompress == 1 && plan->d_msg_off == nullptr) return ZC_ERR_ARG;
+    plan->grouped = grouped;
+    return ZC_OK;
 }
 
 int zc_get_device_status(const void* d_ws, zc_stream_t s, int* status, uint64_t* detail)

@@ -82,6 +82,11 @@ struct Launch {
     // encoder launches: the CTAs' tile rings (ring_cta_bytes each, in CTA order)
     uint8_t* ring;
     unsigned long long ring_bytes;
+    unsigned long long ws_cap;  // entries of every workspace array (bounds-checked builds)
+    // grouped batch (packed mode): the streams lie in ticket order, not item
+    // order, so seg_off[i] is only item i's start and seg_off[n_items] the
+    // packed total; a decoder bounds a stream by seg_off[n_items]
+    int grouped;
 };
 
 struct Smem {
@@ -251,6 +256,29 @@ __device__ __forceinline__ float scan_incl_f16(float v)
 }
 
 // ---- decoding ------------------------------------------------------------------
+// Two rows' sign-magnitude words u_a | u_b << 16 (each below 2^11: |d| <=
+// 1023) -> d_a + B | (d_b + B) << 16 with B = 1024: both halves in [1, 2047],
+// so an integer prefix sum over 32 lanes (at most 65504 per half) carries
+// nothing from one half into the other and two rows scan with one shuffle per
+// step.  Sum at lane j: q_j - q_-1 + (j + 1) B, q_-1 the value before the row.
+constexpr uint32_t PAIR_B = 1024u;
+constexpr int PAIR_MAX_PLANES = 11;
+__device__ __forceinline__ uint32_t biased_pair(uint32_t t)
+{
+    const uint32_t m2 = (t >> 1) & 0x7fff7fffu;                  // magnitudes
+    const uint32_t plus = (PAIR_B | PAIR_B << 16) + m2;
+    const uint32_t minus = (PAIR_B | PAIR_B << 16) - m2;         // no borrow: each half >= 1
+    const uint32_t neg = (t & 0x00010001u) * 0xffffu;            // all-ones halves where d < 0
+    return (plus & ~neg) | (minus & neg);
+}
+// Exact FP32 of a half of a biased pair scan: (half + kbits) holds the float
+// bits of q + 1.5 * 2^23 (|q| < 2^22), kbits = 0x4b400000 - (j + 1) B (+ the
+// value before the row when it is nonzero, added by the caller in FP32).
+__device__ __forceinline__ float pair_half_f(uint32_t half, uint32_t kbits)
+{
+    return __fsub_rn(__uint_as_float(half + kbits), 12582912.0f);
+}
+
 // Block planes and payload offsets of one warp unit of an input stream:
 // meta[b] = (planes, byte offset from the unit's payload start) for the
 // unit's blocks.  Returns the unit's payload start in the stream; a unit whose
@@ -258,7 +286,7 @@ __device__ __forceinline__ float scan_incl_f16(float v)
 template <int LOG2L, int U, bool HEADS = false>
 __device__ __forceinline__ unsigned long long unit_meta(const Launch& P, const Item& it,
                                                         unsigned slot, unsigned long long ue0,
-                                                        int2* meta, bool& narrow)
+                                                        int2* meta, bool& narrow, bool& narrow11)
 {
     constexpr int L = 1 << LOG2L;
     constexpr int PB = L / 8;
@@ -305,13 +333,17 @@ __device__ __forceinline__ unsigned long long unit_meta(const Launch& P, const I
 #pragma unroll
         for (int i = 0; i < BPL; ++i) npmax = max(npmax, np[i]);
         narrow = __all_sync(FULL, npmax <= 16);
+        narrow11 = !HEADS && __all_sync(FULL, npmax <= PAIR_MAX_PLANES);
     }
     int tot;
     int off = warp_excl_scan(sum, lane, tot);
+    const bool slot_ok = dcheck(P.ctl, slot < P.ws_cap, slot);
     const unsigned long long base =
-        32ull + ceil16(nb) + (HEADS ? ceil16(3ull * nb) : 0ull) + P.offs[slot];
-    const bool ok = base + (unsigned long long)tot <= it.cin_cap;
+        32ull + ceil16(nb) + (HEADS ? ceil16(3ull * nb) : 0ull) + (slot_ok ? P.offs[slot] : 0ull);
+    const bool ok = slot_ok && base + (unsigned long long)tot <= it.cin_cap;
     if (!ok && lane == 0) fail(P.ctl, ZC_ERR_FORMAT, slot);
+    if (DEBUG_BUILD && mine && lane == (BU >= 32 ? 31 : BU - 1))
+        dcheck(P.ctl, off + sum == tot, slot);  // the last block's planes end at the unit's
     __syncwarp();  // earlier readers of meta are done
     if (mine) {
 #pragma unroll
@@ -356,7 +388,7 @@ __device__ __forceinline__ int load_head(const uint8_t* p)
     return (int)v - ((v & 0x800000u) ? (1 << 24) : 0);
 }
 
-template <int LOG2L, bool NARROW, bool HEADS = false>
+template <int LOG2L, bool NARROW, bool HEADS = false, bool BIASED = false>
 __device__ __forceinline__ void decode_group(const uint8_t* src, const int2* meta, int g,
                                              float two_eb, float acc[GR], const TpC& tc,
                                              const uint8_t* hsrc = nullptr)
@@ -385,6 +417,7 @@ __device__ __forceinline__ void decode_group(const uint8_t* src, const int2* met
     }
     uint32_t wv[NS][NR];
     unsigned paired = 0;  // bit s: step s has at most 16 planes per block
+    static_assert(!BIASED || (NARROW && !HEADS), "the biased pair scan: narrow plain units");
 #pragma unroll
     for (int st = 0; st < NS; ++st) {
         const int r = st * NR;
@@ -449,6 +482,28 @@ __device__ __forceinline__ void decode_group(const uint8_t* src, const int2* met
 #pragma unroll
     for (int st = 0; st < NS; ++st) {
         const int r = st * NR;
+        if (BIASED) {
+            // lane position within its block row
+            const uint32_t kbits = 0x4b400000u - ((uint32_t)(L == 16 ? k : lane) + 1u) * PAIR_B;
+            // two rows per integer scan: (q + (j + 1) B) of both rows in one word
+            float carry = 0.0f;
+#pragma unroll
+            for (int h2 = 0; h2 < NR; h2 += 2) {
+                uint32_t v = biased_pair(tpose(wv[st][h2 / 2], tc));
+                v = (uint32_t)(L == 16 ? scan_incl<16>((int)v) : scan_incl<32>((int)v));
+                float fa = pair_half_f(v & 0xffffu, kbits);
+                float fb = pair_half_f(v >> 16, kbits);
+                if (L >= 64) {
+                    // rows of one block: each continues from the last value of the row before
+                    if (((r + h2) % RPB) != 0) fa = __fadd_rn(fa, carry);
+                    fb = __fadd_rn(fb, __shfl_sync(FULL, fa, 31));
+                    if (((r + h2 + 1) % RPB) != RPB - 1) carry = __shfl_sync(FULL, fb, 31);
+                }
+                acc[r + h2] = __fmul_rn(fa, two_eb);
+                acc[r + h2 + 1] = __fmul_rn(fb, two_eb);
+            }
+            continue;
+        }
         uint32_t u[4];
         const bool pr = NARROW || ((paired >> st) & 1u);
         if (pr) {
@@ -857,6 +912,7 @@ struct TileSlot {
     int segsz[NWARPS];            // payload bytes of every warp unit
     unsigned long long ex, start; // place in the chain, start of its stream
     int ok;                       // ex and start are usable: store the tile
+    int nfin;                     // encoder warps done with the tile
 };
 
 struct EncShared {
@@ -932,7 +988,8 @@ __device__ __forceinline__ int enc_tile(const Launch& P, const Item& it, unsigne
     const unsigned stage_s = (unsigned)__cvta_generic_to_shared(stage);
     int sbase = 0;
     auto flush = [&](int lo_end) {
-        const int n16 = (lo_end - sbase + 15) >> 4;
+        int n16 = (lo_end - sbase + 15) >> 4;
+        if (!dcheck(ctl, sbase + 16 * n16 <= seg_bytes(U), ue0)) n16 = 0;
         for (int i = lane; i < n16; i += 32)
             ((uint4*)(seg + sbase))[i] = ((const uint4*)stage)[i];
         const int nbase = lo_end & ~15;
@@ -957,11 +1014,12 @@ __device__ __forceinline__ int enc_tile(const Launch& P, const Item& it, unsigne
         }
         const uint8_t* src = nullptr;
         int2* meta = nullptr;
-        bool narrow = false;
+        bool narrow = false, narrow11 = false;
         if constexpr (HAS_CIN) {
             meta = meta_all[warp];
             if (do_cin)
-                src = it.cin + unit_meta<LOG2L, U>(P, it, S.g * NWARPS + warp, ue0, meta, narrow);
+                src = it.cin + unit_meta<LOG2L, U>(P, it, S.g * NWARPS + warp, ue0, meta, narrow,
+                                                   narrow11);
         }
 #pragma unroll 1
         for (int gi = 0; gi < U / GR; ++gi) {
@@ -971,7 +1029,8 @@ __device__ __forceinline__ int enc_tile(const Launch& P, const Item& it, unsigne
             if constexpr (HAS_CIN) {
                 if (do_cin) {
                     float dv[GR];
-                    if (narrow) decode_group<LOG2L, true>(src, meta, gi, two_eb_in, dv, tc);
+                    if (narrow11) decode_group<LOG2L, true, false, true>(src, meta, gi, two_eb_in, dv, tc);
+                    else if (narrow) decode_group<LOG2L, true>(src, meta, gi, two_eb_in, dv, tc);
                     else decode_group<LOG2L, false>(src, meta, gi, two_eb_in, dv, tc);
 #pragma unroll
                     for (int r = 0; r < GR; ++r) acc[r] = __fadd_rn(dv[r], acc[r]);
@@ -985,18 +1044,23 @@ __device__ __forceinline__ int enc_tile(const Launch& P, const Item& it, unsigne
             const int b0 = L >= 32 ? gi * GR / (L / 32) : gi * GR * 2;
             uint8_t* hout = nullptr;
             if (HEADS) hout = it.out + 32 + wbytes + 3ull * ((ue0 >> LOG2L) + b0);
-            lo = encode_group<LOG2L, true, HEADS>(acc, GR * 32, eb, two_eb, inv, stage_s - sbase, lo,
-                                                  wb + b0, err, tc, hout);
+            if (HEADS && DEBUG_BUILD)
+                dcheck(ctl, 32 + wbytes + 3ull * ((ue0 >> LOG2L) + b0 + GR * 32 / L) <= it.out_cap,
+                       ue0);
+            if (dcheck(ctl, lo - sbase + seg_bytes(GR) <= stage_bytes(SR), ue0))
+                lo = encode_group<LOG2L, true, HEADS>(acc, GR * 32, eb, two_eb, inv, stage_s - sbase,
+                                                      lo, wb + b0, err, tc, hout);
             if ((gi + 1) % (SR / GR) == 0) flush(lo);
         }
     } else if (ue0 < n) {
         const uint8_t* src = nullptr;
         int2* meta = nullptr;
-        bool narrow = false;
+        bool narrow = false, narrow11 = false;
         if constexpr (HAS_CIN) {
             meta = meta_all[warp];
             if (do_cin)
-                src = it.cin + unit_meta<LOG2L, U>(P, it, S.g * NWARPS + warp, ue0, meta, narrow);
+                src = it.cin + unit_meta<LOG2L, U>(P, it, S.g * NWARPS + warp, ue0, meta, narrow,
+                                                   narrow11);
         }
         // the next group's input is loaded while the current one is encoded
         float xn[GR];
@@ -1031,7 +1095,8 @@ __device__ __forceinline__ int enc_tile(const Launch& P, const Item& it, unsigne
             if constexpr (HAS_CIN) {
                 if (do_cin) {
                     float dv[GR];
-                    if (narrow) decode_group<LOG2L, true>(src, meta, gi, two_eb_in, dv, tc);
+                    if (narrow11) decode_group<LOG2L, true, false, true>(src, meta, gi, two_eb_in, dv, tc);
+                    else if (narrow) decode_group<LOG2L, true>(src, meta, gi, two_eb_in, dv, tc);
                     else decode_group<LOG2L, false>(src, meta, gi, two_eb_in, dv, tc);
 #pragma unroll
                     for (int r = 0; r < GR; ++r) acc[r] = __fadd_rn(dv[r], acc[r]);
@@ -1052,7 +1117,9 @@ __device__ __forceinline__ int enc_tile(const Launch& P, const Item& it, unsigne
                 const int b0 = L >= 32 ? gi * GR / (L / 32) : gi * GR * 2;
                 uint8_t* hout = nullptr;
                 if (HEADS) hout = it.out + 32 + wbytes + 3ull * ((ue0 >> LOG2L) + b0);
-                if (nrem == GR * 32)
+                if (!dcheck(ctl, lo - sbase + seg_bytes(GR) <= stage_bytes(SR), e0))
+                    ;
+                else if (nrem == GR * 32)
                     lo = encode_group<LOG2L, true, HEADS>(acc, nrem, eb, two_eb, inv,
                                                           stage_s - sbase, lo, wb + b0, err, tc,
                                                           hout);
@@ -1104,7 +1171,8 @@ __device__ __forceinline__ void fin_tile(const Launch& P, const Item& it, unsign
     uint8_t* const out = it.out;
     const unsigned long long end = base + payload;  // unpadded end of this tile's payload
     if (base + payload <= cap) {
-        ring_copy<PB>(out + base + segoff, seg, S.segsz[warp]);
+        if (dcheck(P.ctl, S.segsz[warp] <= seg_bytes(U), g))
+            ring_copy<PB>(out + base + segoff, seg, S.segsz[warp]);
     } else if (tid == 0) {
         fail(P.ctl, ZC_ERR_CAPACITY, g);
     }
@@ -1149,7 +1217,8 @@ __device__ __forceinline__ void fin_tile(const Launch& P, const Item& it, unsign
         }
         if (tid == 0) {
             if (it.out_bytes) *it.out_bytes = total - start;
-            if (P.packed) P.seg_off[item_idx + 1] = total;
+            if (P.packed && !P.grouped) P.seg_off[item_idx + 1] = total;
+            else if (P.packed && g + 1 == P.total_tiles) P.seg_off[P.n_items] = total;
         }
     }
 }
@@ -1228,7 +1297,8 @@ __device__ __forceinline__ void fin_raw(const Launch& P, const Item& it, unsigne
         }
         if (tid == 0) {
             if (it.out_bytes) *it.out_bytes = total - start;
-            if (P.packed) P.seg_off[item_idx + 1] = total;
+            if (P.packed && !P.grouped) P.seg_off[item_idx + 1] = total;
+            else if (P.packed && g + 1 == P.total_tiles) P.seg_off[P.n_items] = total;
         }
     }
 }
@@ -1286,13 +1356,32 @@ struct ScatterSrc {
     }
 };
 
+// Published by the last encoder warp to finish a tile: the tile's aggregate
+// (its byte count), so that the look-backs of the tiles after it need not wait
+// until this CTA's resolver warp reaches it (the resolver handles its tiles in
+// order, and a tile it is still waiting on would hold back this one's
+// aggregate).  The resolver publishes the same aggregate again, then the
+// tile's inclusive prefix.  A chain's first tile publishes its prefix at once
+// (resolver), and a withheld tile (test hook) publishes nothing.
+__device__ __forceinline__ void publish_aggregate(const Launch& P, const TileSlot& S, unsigned E)
+{
+    if (!S.valid || !S.pub) return;
+    const unsigned g0 = P.packed ? 0u : S.g - S.tile;
+    if (S.g == g0 || (long long)S.g == P.wc.withhold || S.g >= P.ws_cap) return;
+    unsigned long long agg = S.head;
+#pragma unroll
+    for (int w = 0; w < NWARPS; ++w) agg += (unsigned long long)S.segsz[w];
+    if (agg > AGG_INLINE_MAX) st_relaxed(P.chB.aggw + S.g, agg);
+    st_release(P.chB.flag + S.g, make_flag(E, ST_AGG, S.last != 0, agg));
+}
+
 // Resolver warp: the tile's place in the chain (look-back over the tiles
 // before it) and, in packed mode, its stream's start.
 __device__ __forceinline__ void resolve_slot(const Launch& P, TileSlot& S, unsigned E)
 {
     int ok = 0;
     unsigned long long ex = 0ull, start = 0ull;
-    if (S.pub) {
+    if (S.pub && dcheck(P.ctl, S.g < P.ws_cap && S.item < max(P.n_items, 1u), S.g)) {
         unsigned long long agg = S.head;
 #pragma unroll
         for (int w = 0; w < NWARPS; ++w) agg += (unsigned long long)S.segsz[w];
@@ -1373,6 +1462,7 @@ __device__ __forceinline__ void enc_pipeline(const Launch& P, const Src& src, En
                 S.valid = g < P.total_tiles;
                 S.item = g < P.total_tiles ? src.find(g) : 0u;
                 S.pub = 0;
+                S.nfin = 0;
             }
             bar_sync_n(BAR_ENCW, NTHREADS);
             TileSlot& S = slots[s];
@@ -1384,7 +1474,14 @@ __device__ __forceinline__ void enc_pipeline(const Launch& P, const Src& src, En
                 if (tid == 0) S.tile = t;
                 lo = enc(it, S.item, t, seg_of(s), wb_of(s), stage_of(), S, es);
             }
-            if (lane == 0) S.segsz[warp] = lo;
+            if (lane == 0) {
+                S.segsz[warp] = lo;
+                __threadfence_block();
+                if (atomicAdd(&S.nfin, 1) == NWARPS - 1) {  // the tile's last encoder warp
+                    __threadfence_block();
+                    publish_aggregate(P, S, E);
+                }
+            }
             bar_arrive_n(BAR_ENC + s, ENC_THREADS);
             if (!valid) {
                 // the tiles still waiting for their stores, oldest first
@@ -1506,7 +1603,8 @@ __global__ void __launch_bounds__(ENC_THREADS, ENC_CTAS_PER_SM) k_batch(const La
 __device__ __forceinline__ void resolve_packed(const Launch& P, Item& it, unsigned idx)
 {
     if (P.in_off == nullptr) return;
-    const unsigned long long a = P.in_off[idx], b = P.in_off[idx + 1];
+    const unsigned long long a = P.in_off[idx];
+    const unsigned long long b = P.in_off[P.grouped ? P.n_items : idx + 1];
     const bool ok = (a & 15ull) == 0 && a <= b && b <= P.in_cap;
     it.cin = P.in_base + (ok ? a : 0ull);
     it.cin_cap = ok ? b - a : 0ull;
@@ -1528,6 +1626,124 @@ __global__ void __launch_bounds__(NTHREADS) k_tile_map(const Item* items, unsign
         else hi = mid;
     }
     map[g] = lo;
+}
+
+// ---- grouped batches ------------------------------------------------------------
+// The tiles of all messages of one block size (classes: raw, 16, 32, 64, 128)
+// take consecutive tickets, so the CTAs running at any time mostly run one
+// encoder variant.  Within a class, messages keep their order.  Three small
+// launches over GROUP_T messages per CTA: per-CTA tile sums of every class;
+// one CTA turns them into every CTA's first ticket per class; each CTA then
+// gives its messages their first tickets and fills the ticket -> item map.
+constexpr int GROUP_T = 256;
+constexpr int GROUP_CLASSES = 5;
+__device__ __forceinline__ int group_class(int log2L) { return log2L < 4 ? 0 : log2L - 3; }
+
+__global__ void __launch_bounds__(GROUP_T) k_group_count(const Item* items, unsigned n_items,
+                                                         unsigned* part)
+{
+    __shared__ unsigned red[GROUP_CLASSES][GROUP_T / 32];
+    const unsigned i = blockIdx.x * GROUP_T + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int c = -1;
+    unsigned t = 0;
+    if (i < n_items) {
+        c = group_class(__ldg(&items[i].log2L));
+        t = __ldg(&items[i].ntiles);
+    }
+#pragma unroll
+    for (int k = 0; k < GROUP_CLASSES; ++k) {
+        const unsigned v = __reduce_add_sync(FULL, c == k ? t : 0u);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < GROUP_CLASSES) {
+        unsigned v = 0;
+        for (int w = 0; w < GROUP_T / 32; ++w) v += red[threadIdx.x][w];
+        part[(size_t)blockIdx.x * GROUP_CLASSES + threadIdx.x] = v;
+    }
+}
+
+// One CTA of 1024 threads: part[b][c] (tiles of class c in CTA b's messages)
+// becomes the first ticket of class c in CTA b: the class's base (the tiles
+// of all smaller classes) plus the class's tiles in CTAs before b.
+__global__ void __launch_bounds__(1024) k_group_scan(unsigned* part, unsigned nblk)
+{
+    __shared__ unsigned wsum[32];
+    __shared__ unsigned carry[GROUP_CLASSES];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < GROUP_CLASSES) carry[tid] = 0;
+    __syncthreads();
+    // pass over the classes: exclusive scans within each class
+    for (int c = 0; c < GROUP_CLASSES; ++c) {
+        for (unsigned b0 = 0; b0 < nblk; b0 += 1024) {
+            const unsigned b = b0 + tid;
+            const unsigned v = b < nblk ? part[(size_t)b * GROUP_CLASSES + c] : 0u;
+            unsigned s = v;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned o = __shfl_up_sync(FULL, s, off);
+                if (lane >= off) s += o;
+            }
+            if (lane == 31) wsum[warp] = s;
+            __syncthreads();
+            if (warp == 0) {
+                unsigned w = wsum[lane];
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const unsigned o = __shfl_up_sync(FULL, w, off);
+                    if (lane >= off) w += o;
+                }
+                wsum[lane] = w;  // inclusive over warps
+            }
+            __syncthreads();
+            const unsigned excl = carry[c] + (warp ? wsum[warp - 1] : 0u) + s - v;
+            if (b < nblk) part[(size_t)b * GROUP_CLASSES + c] = excl;
+            __syncthreads();
+            if (tid == 0) carry[c] += wsum[31];
+            __syncthreads();
+        }
+    }
+    // class bases: the tiles of the smaller classes
+    unsigned base = 0;
+    for (int c = 0; c < GROUP_CLASSES; ++c) {
+        const unsigned tot = carry[c];
+        for (unsigned b = tid; b < nblk; b += 1024) part[(size_t)b * GROUP_CLASSES + c] += base;
+        base += tot;
+    }
+}
+
+__global__ void __launch_bounds__(GROUP_T) k_group_place(Item* items, unsigned n_items,
+                                                         const unsigned* part, unsigned* map)
+{
+    __shared__ unsigned wsum[GROUP_CLASSES][GROUP_T / 32];
+    const unsigned i = blockIdx.x * GROUP_T + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int c = -1;
+    unsigned t = 0;
+    if (i < n_items) {
+        c = group_class(items[i].log2L);
+        t = items[i].ntiles;
+    }
+    unsigned mine = 0;  // exclusive sum of this class's tiles before message i within the warp
+#pragma unroll
+    for (int k = 0; k < GROUP_CLASSES; ++k) {
+        const unsigned v = c == k ? t : 0u;
+        unsigned s = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned o = __shfl_up_sync(FULL, s, off);
+            if (lane >= off) s += o;
+        }
+        if (lane == 31) wsum[k][warp] = s;
+        if (c == k) mine = s - v;
+    }
+    __syncthreads();
+    if (i >= n_items) return;
+    unsigned first = part[(size_t)blockIdx.x * GROUP_CLASSES + c] + mine;
+    for (int w = 0; w < warp; ++w) first += wsum[c][w];
+    items[i].tile_begin = first;
+    for (unsigned k = 0; k < t; ++k) map[first + k] = i;
 }
 
 // ---- width scan: payload offset of every decode tile --------------------------
@@ -1621,10 +1837,12 @@ __global__ void __launch_bounds__(NTHREADS) k_wscan(const Launch P)
             cagg += wsum[w];
         }
         bool to = false;
+        if (DEBUG_BUILD && tid == 0) dcheck(P.ctl, c < P.ws_cap, c);
         const unsigned long long cex =
             lookback_cta(P.chC, c, it.chunk_begin, cagg, false, sm.E, P.wc, P.ctl, to, sm.lb);
         if (to) continue;
-        if (k < ntile) P.offs[(unsigned long long)it.tile_begin * NWARPS + k] = cex + wbase + ex;
+        const unsigned long long oslot = (unsigned long long)it.tile_begin * NWARPS + k;
+        if (k < ntile && dcheck(P.ctl, oslot < P.ws_cap, oslot)) P.offs[oslot] = cex + wbase + ex;
         if (chunk + 1 == it.nchunks && tid == 0) {
             const unsigned long long payload = __ldg((const unsigned long long*)it.cin + 3);
             if (cex + cagg != payload) fail(P.ctl, ZC_ERR_FORMAT, sm.item);
@@ -1663,7 +1881,9 @@ __device__ __forceinline__ void unit_decode(const Launch& P, const Item& it, uns
     const int lane = threadIdx.x & 31;
     const TpC tc = tp_consts(lane);
     bool narrow;
-    const uint8_t* src = it.cin + unit_meta<LOG2L, DEC_U, HEADS>(P, it, slot, ue0, meta, narrow);
+    bool narrow11;
+    const uint8_t* src =
+        it.cin + unit_meta<LOG2L, DEC_U, HEADS>(P, it, slot, ue0, meta, narrow, narrow11);
     const uint8_t* hsrc = nullptr;  // heads apart: the heads of this unit's blocks
     if (HEADS) {
         const unsigned long long nb = (it.n + (1ull << LOG2L) - 1) >> LOG2L;
@@ -1675,7 +1895,8 @@ __device__ __forceinline__ void unit_decode(const Launch& P, const Item& it, uns
         if (e0 >= it.n) break;
         const int nrem = (int)min(it.n - e0, (unsigned long long)(GR * 32));
         float acc[GR];
-        if (narrow) decode_group<LOG2L, true, HEADS>(src, meta, gi, two_eb, acc, tc, hsrc);
+        if (!HEADS && narrow11) decode_group<LOG2L, true, false, true>(src, meta, gi, two_eb, acc, tc);
+        else if (narrow) decode_group<LOG2L, true, HEADS>(src, meta, gi, two_eb, acc, tc, hsrc);
         else decode_group<LOG2L, false, HEADS>(src, meta, gi, two_eb, acc, tc, hsrc);
         TO* op = (TO*)it.raw_out + e0 + lane;
         if (nrem == GR * 32) {

@@ -61,6 +61,14 @@ __device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long 
 {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+// Acquire fence: a relaxed load that observed a value written by a release
+// store, followed by this fence, sees everything written before that store.
+// Polling with relaxed loads and fencing once after the last one keeps the
+// (costly) acquire out of the polling loops.
+__device__ __forceinline__ void fence_acquire_gpu()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
 __device__ __forceinline__ unsigned ld_volatile_u32(const unsigned* p)
 {
     return *(const volatile unsigned*)p;
@@ -77,6 +85,22 @@ __device__ __forceinline__ void fail(Ctl* c, unsigned code, unsigned long long d
 {
     if (atomicCAS(&c->status, 0u, code) == 0u) c->detail = detail;
 }
+
+// Bounds-checked builds (compiled with -DZC_DEBUG): a checked access is
+// tested against its buffer first; a failed check records ZC_ERR_BOUNDS with
+// the offending offset (first error wins) and the caller skips the access.
+// Release builds compile every check to `true`.
+#ifdef ZC_DEBUG
+constexpr bool DEBUG_BUILD = true;
+__device__ __forceinline__ bool dcheck(Ctl* c, bool ok, unsigned long long detail)
+{
+    if (!ok) fail(c, ZC_ERR_BOUNDS, detail);
+    return ok;
+}
+#else
+constexpr bool DEBUG_BUILD = false;
+__device__ __forceinline__ bool dcheck(Ctl*, bool, unsigned long long) { return true; }
+#endif
 
 // Normal (not zero, subnormal, infinite or NaN) FP32 value.
 __device__ __forceinline__ bool is_normal(float f)
@@ -347,7 +371,7 @@ __device__ __forceinline__ unsigned long long lookback_warp(const Chain& ch, uns
                 f[i] = 0ull;
                 valid |= 1u << i;
             } else {
-                f[i] = ld_acquire(ch.flag + j);
+                f[i] = ld_relaxed(ch.flag + j);
                 if (flag_valid(f[i], E)) valid |= 1u << i;
             }
         }
@@ -360,11 +384,13 @@ __device__ __forceinline__ unsigned long long lookback_warp(const Chain& ch, uns
 #pragma unroll
             for (int i = 0; i < LB_PER_LANE; ++i) {
                 if (!((valid >> i) & 1u)) {
-                    f[i] = ld_acquire(ch.flag + (j0 + i));
+                    f[i] = ld_relaxed(ch.flag + (j0 + i));
                     if (flag_valid(f[i], E)) valid |= 1u << i;
                 }
             }
         }
+        // the wide aggregates and the prefix read below were stored before the flags
+        fence_acquire_gpu();
         if (expired) {
             if (lane == 0) fail(ctl, ZC_ERR_TIMEOUT, g);
             excl = 0ull;
@@ -458,8 +484,11 @@ __device__ __forceinline__ bool wait_flag(const unsigned long long* flag, unsign
     unsigned long long t0 = 0ull;
     unsigned ns = 32;
     while (true) {
-        const unsigned long long f = ld_acquire(flag);
-        if ((unsigned)(f >> 32) == E && (unsigned)f != 0u) return true;
+        const unsigned long long f = ld_relaxed(flag);
+        if ((unsigned)(f >> 32) == E && (unsigned)f != 0u) {
+            fence_acquire_gpu();
+            return true;
+        }
         const unsigned long long now = globaltimer();
         if (t0 == 0ull) t0 = now;
         else if (now - t0 > limit_ns) return false;

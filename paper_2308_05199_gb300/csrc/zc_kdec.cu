@@ -18,6 +18,16 @@ cudaError_t launch_tile_map(const Item* items, unsigned n_items, unsigned total_
     return cudaGetLastError();
 }
 
+cudaError_t launch_group(Item* items, unsigned n_items, unsigned* part, unsigned* map,
+                         cudaStream_t s)
+{
+    const unsigned nblk = (n_items + GROUP_T - 1) / GROUP_T;
+    k_group_count<<<nblk, GROUP_T, 0, s>>>(items, n_items, part);
+    k_group_scan<<<1, 1024, 0, s>>>(part, nblk);
+    k_group_place<<<nblk, GROUP_T, 0, s>>>(items, n_items, part, map);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_decompress(const Launch& P, unsigned grid, cudaStream_t s)
 {
     k_decompress<<<grid, NTHREADS, 0, s>>>(P);

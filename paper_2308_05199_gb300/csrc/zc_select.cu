@@ -13,6 +13,7 @@
 namespace zc {
 
 constexpr int N_STATS = ZC_STATS;
+constexpr unsigned FULL_MASK_ALL = 0xffffffffu;
 constexpr int ST_SPANS = 16;
 constexpr int ST_SPAN = 128;
 
@@ -34,110 +35,136 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
     return v;
 }
 
-__device__ __forceinline__ float load_elem(const Item& it, unsigned long long i)
-{
-    return it.x_dtype == ZC_F32 ? __ldg((const float*)it.x + i)
-                                : bf16_to_f32(__ldg((const unsigned short*)it.x + i));
-}
-
 // ---- chunk statistics: one warp per item ----------------------------------------
-// Lane-partial sums of one chunk's sampled spans.
+// Lane l holds elements 4l .. 4l + 3 of a 128-element span (one 16-byte load
+// of FP32, one 8-byte load of BF16, when the chunk is aligned for it), so
+// three of every four differences are taken within the lane and a block of
+// L elements is L / 4 consecutive lanes: its largest |delta| is one segmented
+// warp reduction.  Per-lane sums stay 32-bit (64 sampled elements per lane at
+// most: |q| < 2^23, |d| < 2^24, |d2| < 2^25) and are widened for the warp sum.
 struct StatAcc {
-    unsigned b16 = 0, b32 = 0, b64 = 0, b128 = 0;  // codec block bits per L
-    unsigned long long sum_ad = 0, sum_aq = 0, sum_ad2 = 0;
+    unsigned b16 = 0, b32 = 0, b64 = 0, b128 = 0;  // codec block bits per L (block-first lanes)
+    unsigned sum_ad = 0, sum_aq = 0, sum_ad2 = 0;
     unsigned max_ad = 0, nz_d = 0, nz_q = 0, n_sc = 0, head_bits = 0;
     int qmin = 0x7fffffff, qmax = -0x7fffffff - 1;
     int bad = 0;
 };
 
-// One span of cnt elements (lane i holds elements i, 32 + i, 64 + i, 96 + i;
-// xs already loaded): quantize, differences, block widths; returns the span's
-// L = 32 block bits (warp-uniform).
-__device__ __forceinline__ unsigned stat_span(const float xs[4], int cnt, const Item& it,
+// The four elements of this lane in span [s0, s0 + cnt) (zero beyond cnt).
+__device__ __forceinline__ void load_span4(const Item& it, bool vec, unsigned long long s0, int cnt,
+                                           float v[4])
+{
+    const int lane = threadIdx.x & 31;
+    const int i0 = 4 * lane;
+    if (it.x_dtype == ZC_F32) {
+        const float* p = (const float*)it.x + s0 + i0;
+        if (vec && i0 + 4 <= cnt) {
+            const float4 w = __ldg((const float4*)p);
+            v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
+        } else {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) v[m] = i0 + m < cnt ? __ldg(p + m) : 0.0f;
+        }
+    } else {
+        const unsigned short* p = (const unsigned short*)it.x + s0 + i0;
+        if (vec && i0 + 4 <= cnt) {
+            const uint2 w = __ldg((const uint2*)p);
+            v[0] = __uint_as_float(w.x << 16);
+            v[1] = __uint_as_float(w.x & 0xffff0000u);
+            v[2] = __uint_as_float(w.y << 16);
+            v[3] = __uint_as_float(w.y & 0xffff0000u);
+        } else {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) v[m] = i0 + m < cnt ? bf16_to_f32(__ldg(p + m)) : 0.0f;
+        }
+    }
+}
+
+// Largest block |delta| of the lane's block at blocks of G lanes (L = 4G):
+// the block's first lane contributes |q| of its first element (the head is
+// predicted from 0), every other lane |d| of its first element.
+template <int G>
+__device__ __forceinline__ unsigned block_max(unsigned rest, unsigned e0q, unsigned e0d)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned v = max(rest, (lane & (G - 1)) == 0 ? e0q : e0d);
+    const unsigned seg = G == 32 ? FULL : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    return __reduce_max_sync(seg, v);
+}
+
+// One span of cnt elements (v: this lane's four); returns the span's L = 32
+// block bits (the same in every lane).  FULL: cnt == 128.  Branch-free:
+// elements outside the span, and the differences that do not exist at the
+// span's start, are masked out.
+template <bool FULL>
+__device__ __forceinline__ unsigned stat_span(const float v[4], int cnt, const Item& it,
                                               StatAcc& A)
 {
     const int lane = threadIdx.x & 31;
-    int q[4], d[4], pd[4];
-    bool v[4];
-    // the exact quantizer: the fast rounding for all four rows, the exact slow
-    // path only when some lane's fast result may be off (one vote)
+    const int i0 = 4 * lane;
+    int q[4];
+    bool ok[4];
+    // the exact quantizer: fast rounding for all four, the exact slow path
+    // only when some lane's fast result may be off (one vote)
     bool slow = false;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int i = 32 * r + lane;
-        v[r] = i < cnt;
-        slow |= !quantize_fast(v[r] ? xs[r] : 0.0f, it.inv, q[r]);
+    for (int m = 0; m < 4; ++m) {
+        ok[m] = FULL || i0 + m < cnt;
+        slow |= !quantize_fast(ok[m] ? v[m] : 0.0f, it.inv, q[m]);
     }
-    if (__any_sync(FULL, slow)) {
+    if (__any_sync(FULL_MASK_ALL, slow)) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int m = 0; m < 4; ++m) {
             int qq = 0;
-            if (v[r] && quantize(xs[r], it.eb, it.two_eb, it.inv, qq) != 0) {
+            if (ok[m] && quantize(v[m], it.eb, it.two_eb, it.inv, qq) != 0) {
                 A.bad = 1;
                 qq = 0;
             }
-            q[r] = qq;
+            q[m] = qq;
         }
     }
-    // d_i = q_i - q_{i-1}, and d_{i-1} (for the second differences)
+    // first differences d (element i >= 1) and the previous one pd (i >= 2)
+    int d[4], pd[4];
+    d[0] = q[0] - __shfl_up_sync(FULL_MASK_ALL, q[3], 1);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int up = __shfl_up_sync(FULL, q[r], 1);
-        const int prev_row = __shfl_sync(FULL, q[r > 0 ? r - 1 : 0], 31);
-        d[r] = q[r] - (lane ? up : (r ? prev_row : 0));
-    }
+    for (int m = 1; m < 4; ++m) d[m] = q[m] - q[m - 1];
+    pd[0] = __shfl_up_sync(FULL_MASK_ALL, d[3], 1);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int up = __shfl_up_sync(FULL, d[r], 1);
-        const int prev_row = __shfl_sync(FULL, d[r > 0 ? r - 1 : 0], 31);
-        pd[r] = lane ? up : (r ? prev_row : 0);
-    }
-    unsigned aq[4], ad[4];
+    for (int m = 1; m < 4; ++m) pd[m] = d[m - 1];
+    unsigned rest = 0;  // largest |d| of elements 1..3 of the lane
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int i = 32 * r + lane;
-        aq[r] = v[r] ? (unsigned)abs(q[r]) : 0u;
-        ad[r] = (v[r] && i >= 1) ? (unsigned)abs(d[r]) : 0u;
-        if (v[r]) {
-            A.nz_q += q[r] == 0;
-            A.sum_aq += aq[r];
-            A.qmin = min(A.qmin, q[r]);
-            A.qmax = max(A.qmax, q[r]);
-            if (i >= 1) {
-                A.sum_ad += ad[r];
-                A.max_ad = max(A.max_ad, ad[r]);
-                A.nz_d += d[r] == 0;
-            }
-            if (i >= 2) {
-                A.sum_ad2 += (unsigned)abs(d[r] - pd[r]);
-                A.n_sc += (d[r] > 0 && pd[r] < 0) || (d[r] < 0 && pd[r] > 0);
-            }
-        }
+    for (int m = 0; m < 4; ++m) {
+        const bool v0 = ok[m];
+        const bool v1 = v0 && (m > 0 || lane > 0);   // element i >= 1
+        const bool v2 = v0 && (m > 1 || lane > 0);   // element i >= 2
+        const unsigned aq = v0 ? (unsigned)abs(q[m]) : 0u;
+        const unsigned ad = v1 ? (unsigned)abs(d[m]) : 0u;
+        const unsigned ad2 = v2 ? (unsigned)abs(d[m] - pd[m]) : 0u;
+        A.nz_q += (v0 && q[m] == 0) ? 1u : 0u;
+        A.sum_aq += aq;
+        A.qmin = min(A.qmin, v0 ? q[m] : 0x7fffffff);
+        A.qmax = max(A.qmax, v0 ? q[m] : -0x7fffffff - 1);
+        A.sum_ad += ad;
+        A.max_ad = max(A.max_ad, ad);
+        A.nz_d += (v1 && d[m] == 0) ? 1u : 0u;
+        if (m > 0) rest = max(rest, ad);
+        A.sum_ad2 += ad2;
+        const bool sc = (d[m] > 0 && pd[m] < 0) || (d[m] < 0 && pd[m] > 0);
+        A.n_sc += (v2 && sc) ? 1u : 0u;
     }
-    // the codec's block bits at every L: the block head's delta is |q|
-    unsigned sb32 = 0;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        unsigned a = (lane & 15) == 0 ? aq[r] : ad[r];
-#pragma unroll
-        for (int off = 8; off; off >>= 1) a = max(a, __shfl_xor_sync(FULL, a, off));
-        if ((lane & 15) == 0 && a) A.b16 += (bitlen_u(a) + 1) * 16;
-        const unsigned m32 = __reduce_max_sync(FULL, lane == 0 ? aq[r] : ad[r]);
-        if (m32) sb32 += (bitlen_u(m32) + 1) * 32;
-        if (lane == 0 && v[r]) A.head_bits += bitlen_u(aq[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < 4; r += 2) {
-        const unsigned m64 = __reduce_max_sync(FULL, max(lane == 0 ? aq[r] : ad[r], ad[r + 1]));
-        if (lane == 0 && m64) A.b64 += (bitlen_u(m64) + 1) * 64;
-    }
-    {
-        const unsigned a = max(max(lane == 0 ? aq[0] : ad[0], ad[1]), max(ad[2], ad[3]));
-        const unsigned m128 = __reduce_max_sync(FULL, a);
-        if (lane == 0 && m128) A.b128 += (bitlen_u(m128) + 1) * 128;
-    }
-    if (lane == 0) A.b32 += sb32;
-    return sb32;
+    const unsigned e0q = ok[0] ? (unsigned)abs(q[0]) : 0u;
+    const unsigned e0d = (ok[0] && i0 >= 1) ? (unsigned)abs(d[0]) : 0u;
+    const unsigned m16 = block_max<4>(rest, e0q, e0d);
+    const unsigned m32 = block_max<8>(rest, e0q, e0d);
+    const unsigned m64 = block_max<16>(rest, e0q, e0d);
+    const unsigned m128 = block_max<32>(rest, e0q, e0d);
+    const unsigned b32 = ((lane & 7) == 0 && m32) ? (bitlen_u(m32) + 1) * 32 : 0u;
+    A.b16 += ((lane & 3) == 0 && m16) ? (bitlen_u(m16) + 1) * 16 : 0u;
+    A.b64 += ((lane & 15) == 0 && m64) ? (bitlen_u(m64) + 1) * 64 : 0u;
+    A.b128 += (lane == 0 && m128) ? (bitlen_u(m128) + 1) * 128 : 0u;
+    A.b32 += b32;
+    A.head_bits += ((lane & 7) == 0 && ok[0]) ? bitlen_u(e0q) : 0u;
+    return __reduce_add_sync(FULL_MASK_ALL, b32);
 }
 
 __global__ void __launch_bounds__(256, 4) k_chunk_stats(const Item* items, unsigned n_items,
@@ -156,33 +183,42 @@ __global__ void __launch_bounds__(256, 4) k_chunk_stats(const Item* items, unsig
     const unsigned long long m = n / ST_SPAN;
     const int S = m == 0 ? 1 : (int)(m < ST_SPANS ? m : ST_SPANS);
     const int cnt = m == 0 ? (int)n : ST_SPAN;  // elements of every sampled span
+    // spans start at multiples of 128 elements: aligned loads when the chunk is
+    const bool vec = ((uintptr_t)it.x & (it.x_dtype == ZC_F32 ? 15u : 7u)) == 0u;
+    auto span0 = [&](int jj) -> unsigned long long {
+        return (m == 0 || S == 1) ? 0ull
+                                  : (unsigned long long)ST_SPAN * (((unsigned long long)jj * (m - 1)) / (S - 1));
+    };
     StatAcc A;
-    unsigned span_b32[ST_SPANS];  // per-span L = 32 bits (warp-uniform; used by lane 0)
-    // two spans per step: both spans' loads are in flight together
-    for (int j = 0; j < S; j += 2) {
-        float xs[2][4];
+    unsigned span_b32[ST_SPANS];  // per-span L = 32 bits (warp-uniform)
+    if (cnt == ST_SPAN) {
+        // full spans: two loaded ahead of the one being summarised
+        float xa[4], xb[4], xc[4];
+        load_span4(it, vec, span0(0), cnt, xa);
+        if (S > 1) load_span4(it, vec, span0(1), cnt, xb);
+#pragma unroll 1
+        for (int j = 0; j < S; ++j) {
+            if (j + 2 < S) load_span4(it, vec, span0(j + 2), cnt, xc);
+            span_b32[j] = stat_span<true>(xa, cnt, it, A);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int jj = j + h;
-            const unsigned long long s0 =
-                (m == 0 || S == 1) ? 0ull
-                                   : (unsigned long long)ST_SPAN * (((unsigned long long)jj * (m - 1)) / (S - 1));
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int i = 32 * r + lane;
-                xs[h][r] = (jj < S && i < cnt) ? load_elem(it, s0 + i) : 0.0f;
+            for (int k = 0; k < 4; ++k) {
+                xa[k] = xb[k];
+                xb[k] = xc[k];
             }
         }
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-            if (j + h < S) span_b32[j + h] = stat_span(xs[h], cnt, it, A);
+    } else {
+        float xa[4];
+        load_span4(it, vec, 0ull, cnt, xa);
+        span_b32[0] = stat_span<false>(xa, cnt, it, A);
     }
     const unsigned long long B16 = warp_sum_u64(A.b16), B32 = warp_sum_u64(A.b32);
     const unsigned long long B64 = warp_sum_u64(A.b64), B128 = warp_sum_u64(A.b128);
     const unsigned long long SAD = warp_sum_u64(A.sum_ad), SAQ = warp_sum_u64(A.sum_aq);
     const unsigned long long SAD2 = warp_sum_u64(A.sum_ad2);
-    const unsigned long long NZD = warp_sum_u64(A.nz_d), NZQ = warp_sum_u64(A.nz_q);
-    const unsigned long long NSC = warp_sum_u64(A.n_sc), HB = warp_sum_u64(A.head_bits);
+    const unsigned long long NZD = __reduce_add_sync(FULL, A.nz_d);
+    const unsigned long long NZQ = __reduce_add_sync(FULL, A.nz_q);
+    const unsigned long long NSC = __reduce_add_sync(FULL, A.n_sc);
+    const unsigned long long HB = __reduce_add_sync(FULL, A.head_bits);
     const unsigned MAD = __reduce_max_sync(FULL, A.max_ad);
     const int QMN = __reduce_min_sync(FULL, A.qmin), QMX = __reduce_max_sync(FULL, A.qmax);
     const int BAD = __any_sync(FULL, A.bad);

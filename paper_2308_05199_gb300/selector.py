@@ -124,16 +124,27 @@ class ChunkBatch:
         self.n = np.array([v.numel() for v in views], np.int64)
         self.es = np.array([v.element_size() for v in views], np.int64)
         self.stream = stream
+        # grouped: whatever block sizes the selection writes, tiles of one size
+        # run together (a batch that alternates sizes tile by tile compresses
+        # about twice as slowly)
         self.batch = zc.BatchCompress(views, [32] * self.M, ebs, cap=packed_capacity(views),
-                                      stream=stream)
+                                      stream=stream, grouped=True)
         dev = views[0].device
         self.outs = [torch.empty(v.numel(), dtype=v.dtype, device=dev) for v in views]
         self.dec = zc.BatchDecompress(self.batch.packed, self.batch.msg_off, self.outs,
-                                      stream=stream)
+                                      stream=stream, grouped=True)
         self.feat = torch.empty((self.M, zc.N_STATS), dtype=torch.float32, device=dev)
         self.pred = torch.empty((self.M, 4), dtype=torch.float32, device=dev)
         self.choice = torch.zeros(self.M, dtype=torch.int32, device=dev)
         self.counts = torch.zeros(2, dtype=torch.int32, device=dev)
+
+    def sync(self):
+        """Wait for the plan's stream (a torch pool stream does not order
+        itself with the default stream that host reads use)."""
+        if self.stream is not None:
+            self.stream.synchronize()
+        else:
+            torch.cuda.current_stream().synchronize()
 
     @property
     def raw_bytes(self) -> int:
@@ -145,8 +156,18 @@ class ChunkBatch:
         self.batch.replan(self.batch.plan.tile_chunks, self.batch.plan.grid)
 
     def sizes(self) -> np.ndarray:
+        """Stream length of every chunk (from the streams' headers)."""
+        self.sync()
         off = self.batch.msg_off.cpu().numpy()
-        return np.diff(off)
+        hdr = self.batch.packed[:int(off[-1])].view(-1)
+        idx = torch.from_numpy(off[:-1, None] + np.arange(32)[None, :]).to(hdr.device)
+        h = np.ascontiguousarray(hdr[idx].cpu().numpy())
+        flags = h[:, 6].astype(np.int64)
+        nb = h[:, 20:24].copy().view(np.uint32)[:, 0].astype(np.int64)
+        payload = h[:, 24:32].copy().view(np.uint64)[:, 0].astype(np.int64)
+        pad = lambda v: (v + 15) // 16 * 16
+        coded = 32 + pad(nb) + np.where(flags & 2, pad(3 * nb), 0) + pad(payload)
+        return np.where(flags & 1, 32 + pad(payload), coded)
 
     def stats(self):
         zc._check(zc.zc_batch_chunk_stats(self.batch.plan, self.feat.data_ptr(),
@@ -182,29 +203,27 @@ class ChunkBatch:
         return (float(np.median([t[0] for t in ts])), float(np.median([t[1] for t in ts])))
 
     def cost_model(self, link_gbs: float, judge_log2: float = 1.0, reps: int = 5):
-        """Measured codec ns per input byte (compression + decompression), as
-        a zc_select_cfg.  Raw storage is timed on its own.  Coded storage is
-        timed with the block sizes assigned round-robin over the chunks -- the
-        mixed plans a selector produces: per-L times measured on uniform
-        plans (kept in self.uniform_ns_per_byte) differ by up to 20 %, but a
-        mixed plan runs at the mixed rate whatever chunk gets which L, so every
-        L is charged that rate and the choice between block sizes is made on
-        the predicted bytes."""
+        """The codec's time per input byte at each choice, measured on this
+        batch (compression + decompression, CUDA events), as a zc_select_cfg:
+        every block size timed on a plan that uses it throughout, raw storage
+        likewise.  The batch is grouped by block size, so a mixed selection
+        runs each chunk at its block size's own rate; the round-robin mix
+        (every tile a different size) is timed too, for the record
+        (self.mixed_ns_per_byte)."""
         cfg = zc.ZcSelectCfg()
         cfg.link_gbs = link_gbs
         cfg.judge_log2 = judge_log2
         self.uniform_ns_per_byte = []
-        for L in BLOCKS:
+        for k, L in enumerate(BLOCKS):
             self.set_all(L)
             c, d = self.time_ms(reps)
             self.uniform_ns_per_byte.append((c + d) * 1e6 / self.raw_bytes)
+            cfg.ns_per_byte[k] = self.uniform_ns_per_byte[-1]
         for i in range(self.M):
             self.batch.msgs[i].block = BLOCKS[i % 4]
         self.batch.replan(self.batch.plan.tile_chunks, self.batch.plan.grid)
         c, d = self.time_ms(reps)
-        mixed = (c + d) * 1e6 / self.raw_bytes
-        for k in range(4):
-            cfg.ns_per_byte[k] = mixed
+        self.mixed_ns_per_byte = (c + d) * 1e6 / self.raw_bytes
         self.set_all(zc.RAW)
         c, d = self.time_ms(reps)
         cfg.raw_ns_per_byte = (c + d) * 1e6 / self.raw_bytes
@@ -286,9 +305,12 @@ class Mlp:
         g = torch.Generator(device=X.device)
         g.manual_seed(seed)
         s = zc._stream(stream)
+        ts = stream if stream is not None else torch.cuda.current_stream()
+        ts.wait_stream(torch.cuda.current_stream())  # X, T and the buffers above
         hist = []
         for _ in range(epochs):
-            idx.copy_(torch.randperm(N, generator=g, device=X.device).to(torch.int32))
+            with torch.cuda.stream(ts):
+                idx.copy_(torch.randperm(N, generator=g, device=X.device).to(torch.int32))
             for k in range(steps):
                 b0 = k * batch
                 B = min(batch, N - b0)
@@ -299,7 +321,10 @@ class Mlp:
                           "zc_mlp_grad")
                 zc._check(zc.zc_mlp_sgd(self.params.data_ptr(), self.vel.data_ptr(),
                                         self.grad.data_ptr(), lr, momentum, s), "zc_mlp_sgd")
-            hist.append(float(losses.mean()))
+            with torch.cuda.stream(ts):
+                m = losses.mean()
+            ts.synchronize()
+            hist.append(float(m))
         return hist
 
 
@@ -333,7 +358,9 @@ def evaluate(choice: np.ndarray, n, es, true_bits, cfg) -> dict:
 def dataset(cb: ChunkBatch):
     """Features and labels (log2 true bits per element) of a chunk batch,
     rows with a NaN feature removed; returns (X, T, keep mask, true bits)."""
-    X = cb.stats().clone()
+    cb.stats()
+    cb.sync()
+    X = cb.feat.clone()
     bits = cb.true_bits()
     keep = torch.isfinite(X).all(1).cpu().numpy() & np.all(bits > 0, 1)
     T = torch.from_numpy(np.log2(np.where(bits > 0, bits, 1.0)).astype(np.float32)).to(X.device)

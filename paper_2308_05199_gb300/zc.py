@@ -20,7 +20,7 @@ import torch
 from . import build as _build
 
 OK, ERR_ARG, ERR_RANGE, ERR_NONFINITE, ERR_CAPACITY, ERR_FORMAT, ERR_TIMEOUT, ERR_CUDA, \
-    ERR_WORKSPACE = range(9)
+    ERR_WORKSPACE, ERR_BOUNDS = range(10)
 F32, BF16 = 0, 1
 EB_ABS, EB_REL = 0, 1
 HEADER = 32
@@ -58,7 +58,8 @@ class ZcMessage(ctypes.Structure):
 
 class ZcBatch(ctypes.Structure):
     _fields_ = [("n_msgs", ctypes.c_int), ("tile_chunks", ctypes.c_int), ("grid", ctypes.c_int),
-                ("decompress", ctypes.c_int), ("total_tiles", ctypes.c_uint64),
+                ("decompress", ctypes.c_int), ("grouped", ctypes.c_int),
+                ("total_tiles", ctypes.c_uint64),
                 ("total_chunks", ctypes.c_uint64), ("d_table", ctypes.c_void_p),
                 ("d_packed", ctypes.c_void_p), ("packed_cap", ctypes.c_size_t),
                 ("d_msg_off", ctypes.c_void_p)]
@@ -83,7 +84,9 @@ MLP_PARAMS = 5508
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The library this process loads: the release build, or the
+    bounds-checked one when the environment sets ZC_LIBRARY=debug."""
+    return _build.DEBUG_LIB if os.environ.get("ZC_LIBRARY") == "debug" else _build.LIB
 
 
 def lib():
@@ -91,7 +94,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
+            path = lib_path()
             if not os.path.exists(path):
                 raise RuntimeError("libzc.so is not built (%s); run "
                                    "paper_2308_05199_gb300.build.build()" % path)
@@ -129,6 +132,7 @@ def _declare(L):
         "zc_plan_decompress_batch": (i32, [c.POINTER(ZcBatch), i32, c.POINTER(ZcMessage), vp, sz,
                                            vp, vp, sz]),
         "zc_decompress_batch": (i32, [c.POINTER(ZcBatch), vp, sz, vp]),
+        "zc_batch_set_grouped": (i32, [c.POINTER(ZcBatch), i32]),
         "zc_plan_decompress_streams": (i32, [c.POINTER(ZcBatch), i32, vp, vp,
                                              c.POINTER(ZcMessage), vp, sz]),
         "zc_autotune_batch": (i32, [i32, c.POINTER(ZcMessage), i32, dbl, i32, vp, sz, vp, vp, sz,
@@ -165,7 +169,8 @@ def exported_names():
             "zc_plan_table_bytes", "zc_plan_reduce", "zc_reduce_step_batch", "zc_scatter_pack",
             "zc_compress_noalloc", "zc_batch_table_bytes", "zc_batch_max_bytes",
             "zc_plan_compress_batch", "zc_compress_batch", "zc_plan_decompress_batch",
-            "zc_decompress_batch", "zc_plan_decompress_streams", "zc_autotune_batch", "zc_batch_chunk_stats", "zc_mlp_forward",
+            "zc_decompress_batch", "zc_batch_set_grouped", "zc_plan_decompress_streams",
+            "zc_autotune_batch", "zc_batch_chunk_stats", "zc_mlp_forward",
             "zc_mlp_scratch_bytes", "zc_mlp_grad", "zc_mlp_sgd", "zc_batch_select",
             "zc_graph_begin", "zc_graph_end",
             "zc_graph_launch", "zc_graph_destroy",
@@ -299,6 +304,10 @@ def zc_plan_decompress_streams(plan, n_msgs, h_streams, h_caps, h_msgs, d_table,
                                table_bytes) -> int:
     return lib().zc_plan_decompress_streams(ctypes.byref(plan), n_msgs, h_streams, h_caps,
                                             h_msgs, d_table, table_bytes)
+
+
+def zc_batch_set_grouped(plan, grouped: int) -> int:
+    return lib().zc_batch_set_grouped(plan, grouped)
 
 
 def zc_decompress_batch(plan, d_ws, ws_bytes, stream) -> int:
@@ -499,7 +508,8 @@ class BatchCompress:
 
     def __init__(self, xs, blocks, ebs, tile_chunks: int = 0, grid: int = 0,
                  ws: Workspace | None = None, cap: int | None = None, packed=None,
-                 stream=None):
+                 stream=None, grouped: bool = False):
+        self.grouped = bool(grouped)
         self.xs = [x.contiguous() for x in xs]
         M = len(self.xs)
         dev = self.xs[0].device
@@ -546,6 +556,8 @@ class BatchCompress:
                                       self.packed.data_ptr(), self.cap, self.msg_off.data_ptr(),
                                       self.table.data_ptr(), self.table.numel()),
                "zc_plan_compress_batch")
+        if self.grouped:
+            _check(zc_batch_set_grouped(self.plan, 1), "zc_batch_set_grouped")
 
     def run(self, stream=None):
         _check(zc_compress_batch(self.plan, self.ws.ptr, self.ws.nbytes, _stream(stream)),
@@ -571,14 +583,31 @@ class BatchCompress:
         """Host copies of every message's stream (synchronises)."""
         off = self.msg_off.cpu().tolist()
         buf = self.packed[:off[-1]].cpu().numpy().tobytes()
-        return [buf[off[i]:off[i + 1]] for i in range(len(self.xs))]
+        M = len(self.xs)
+        if not self.grouped:
+            return [buf[off[i]:off[i + 1]] for i in range(M)]
+        return [buf[off[i]:off[i] + stream_length(buf[off[i]:off[i] + 32])] for i in range(M)]
+
+
+def stream_length(header: bytes) -> int:
+    """Length of a stream from its 32-byte header (host bookkeeping): header,
+    padded width bytes (and block heads when stored apart), padded payload."""
+    h = bytes(header[:32])
+    flags = h[6]
+    nb = int.from_bytes(h[20:24], "little")
+    payload = int.from_bytes(h[24:32], "little")
+    pad = lambda v: (v + 15) // 16 * 16
+    if flags & 1:
+        return 32 + pad(payload)
+    return 32 + pad(nb) + (pad(3 * nb) if flags & 2 else 0) + pad(payload)
 
 
 class BatchDecompress:
-    """Plan for decoding a packed buffer of M streams into ``outs``."""
+    """Plan for decoding a packed buffer of M streams into ``outs`` (grouped:
+    the streams were packed by a grouped compression plan)."""
 
     def __init__(self, packed: torch.Tensor, msg_off: torch.Tensor, outs,
-                 ws: Workspace | None = None, stream=None):
+                 ws: Workspace | None = None, stream=None, grouped: bool = False):
         self.outs = outs
         M = len(outs)
         self.msgs = _messages(M)
@@ -598,6 +627,8 @@ class BatchDecompress:
         _check(zc_plan_decompress_batch(self.plan, M, self.msgs, packed.data_ptr(), packed.numel(),
                                         msg_off.data_ptr(), self.table.data_ptr(),
                                         self.table.numel()), "zc_plan_decompress_batch")
+        if grouped:
+            _check(zc_batch_set_grouped(self.plan, 1), "zc_batch_set_grouped")
 
     def run(self, stream=None):
         _check(zc_decompress_batch(self.plan, self.ws.ptr, self.ws.nbytes, _stream(stream)),

@@ -176,3 +176,15 @@ def test_heads_bound_holds_on_extreme_data(zc):
                 assert len(oracle.compress_heads(v, eb, log2L)) <= bound
     assert zc.zc_max_compressed_bytes_heads(10, 3) == 0
     assert zc.zc_max_compressed_bytes_heads(0, 32) == oracle.max_stream_bytes(0, 5)
+
+
+def test_batch_set_grouped_arguments(zc):
+    p = zc.ZcBatch()
+    assert zc.zc_batch_set_grouped(None, 1) == zc.ERR_ARG
+    assert zc.zc_batch_set_grouped(p, 2) == zc.ERR_ARG
+    assert zc.zc_batch_set_grouped(p, -1) == zc.ERR_ARG
+    p.decompress = 1                      # a decompression plan without stream offsets
+    assert zc.zc_batch_set_grouped(p, 1) == zc.ERR_ARG
+    p.d_msg_off = FAKE
+    assert zc.zc_batch_set_grouped(p, 1) == zc.OK and p.grouped == 1
+    assert zc.zc_batch_set_grouped(p, 0) == zc.OK and p.grouped == 0

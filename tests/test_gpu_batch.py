@@ -206,3 +206,68 @@ def test_autotuner_picks_the_best_valid_candidate(zc):
     b.run()
     tuned = [best["block"] if blk else 0 for blk in blocks]
     check_against_oracle(b, xs, tuned, ebs)
+
+
+@pytest.mark.parametrize("chunks", [4, 8])
+def test_grouped_batch_streams_and_layout(zc, chunks):
+    """A grouped plan packs the streams by block size (raw, 16, 32, 64, 128;
+    message order within a size): every message's stream, found at
+    msg_off[i] with its header's length, is the oracle's; msg_off[M] is the
+    packed total; decoding from the grouped buffer matches the oracle."""
+    sizes = SIZES_MIX * 3
+    xs, blocks, ebs = mixed_messages(40 + chunks, sizes)
+    b = zc.BatchCompress([x.cuda() for x in xs], blocks, ebs, tile_chunks=chunks, grouped=True)
+    for _ in range(2):  # the device rewrite of the tile starts repeats identically
+        b.packed.zero_()
+        b.run()
+        assert b.ws.status()[0] == 0, b.ws.status()
+        streams = b.streams()
+        off = b.msg_off.cpu().tolist()
+        refs = [oracle_stream(x, blk, eb) for x, blk, eb in zip(xs, blocks, ebs)]
+        for i in range(len(xs)):
+            assert streams[i] == refs[i], (i, xs[i].numel(), blocks[i])
+        assert off[-1] == sum(len(r) for r in refs)
+        cls = {0: 0, 16: 1, 32: 2, 64: 3, 128: 4}
+        order = sorted(range(len(xs)), key=lambda i: off[i])
+        keys = [(cls[blocks[i]], i) for i in order]
+        assert keys == sorted(keys)  # grouped by size, message order within a size
+    outs = [torch.empty(x.numel(), dtype=x.dtype, device="cuda") for x in xs]
+    d = zc.BatchDecompress(b.packed, b.msg_off, outs, grouped=True)
+    d.run()
+    assert d.ws.status()[0] == 0, d.ws.status()
+    for i, x in enumerate(xs):
+        code = 0 if x.dtype == torch.float32 else 1
+        np.testing.assert_array_equal(np_of(outs[i]), oracle.decompress(refs[i], x.numel(), code))
+
+
+def test_grouped_batch_follows_block_sizes_changed_on_the_device(zc):
+    """The grouping is derived on the device at every launch, so block sizes
+    written into the table after planning (as the selector does, here by a
+    plain copy) take effect, also when the launch is replayed from a graph."""
+    xs, blocks, ebs = mixed_messages(77, [3000, 20000, 70001, 5, 16384, 40000],
+                                     blocks_from=(32,))
+    dev = [x.cuda() for x in xs]
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    b = zc.BatchCompress(dev, blocks, ebs, grouped=True, stream=s)
+    b.run(s)
+    s.synchronize()
+    g = zc.Graph(s)
+    with g.capture():
+        b.run(s)
+    # the same plan (same output buffer) with other block sizes, planned
+    # elsewhere: copy its table over
+    new_blocks = [128, 16, 0, 64, 16, 128]
+    b2 = zc.BatchCompress(dev, new_blocks, ebs, cap=b.cap, packed=b.packed)
+    torch.cuda.synchronize()
+    b.table.copy_(b2.table)
+    torch.cuda.synchronize()
+    g.launch()
+    s.synchronize()
+    assert b.ws.status()[0] == 0
+    off = b.msg_off.cpu().tolist()
+    buf = b.packed[:off[-1]].cpu().numpy().tobytes()
+    for i, (x, blk, eb) in enumerate(zip(xs, new_blocks, ebs)):
+        ref = oracle_stream(x, blk, eb)
+        assert buf[off[i]:off[i] + len(ref)] == ref, i
+    assert off[-1] == sum(len(oracle_stream(x, blk, eb)) for x, blk, eb in zip(xs, new_blocks, ebs))

@@ -224,7 +224,8 @@ def test_selector_heldout_streams_from_graph(zc):
     picks = np.unique(np.concatenate([rng.choice(cb.M, 150, replace=False), [0, cb.M - 1]]))
     for j in picks:
         a = np_of(hv[j])
-        s = packed[int(off[j]):int(off[j + 1])].cpu().numpy().tobytes()
+        hdr = packed[int(off[j]):int(off[j]) + 32].cpu().numpy().tobytes()
+        s = packed[int(off[j]):int(off[j]) + zc.stream_length(hdr)].cpu().numpy().tobytes()
         c = int(choice[j])
         ref = oracle.compress_raw(a) if c == 0 else oracle.compress(a, he[j], c.bit_length() - 1)
         assert s == ref, (j, c)

@@ -58,6 +58,16 @@ def test_noalloc_matches_workspace_entry_point_on_consecutive_calls(zc):
         assert _noalloc(zc, x, eb, block, mode) == ref
 
 
+def test_noalloc_matches_the_oracle_on_the_smallest_case(zc):
+    """Independently of zc_compress: the stream of a small ragged input is
+    the oracle's byte for byte, on two calls in a row."""
+    import oracle
+    x = _input(5000 + 17, 4, torch.float32)
+    ref = oracle.compress(x.cpu().numpy(), 1e-3, 5)
+    assert _noalloc(zc, x, 1e-3, 32, zc.EB_ABS) == ref
+    assert _noalloc(zc, x, 1e-3, 32, zc.EB_ABS) == ref
+
+
 def test_noalloc_rejects_sizes_beyond_its_limit(zc):
     n = zc.NOALLOC_MAX_N + 1
     st = zc.zc_compress_noalloc(1 << 20, n, zc.F32, zc.EB_ABS, 1e-3, 32, 1 << 20, 1 << 30,
