@@ -91,7 +91,7 @@ struct WsView {
     float2* partial;
     unsigned long long* offs;
     Chain chB, chC;
-    unsigned long long* seg_flag;
+    ulonglong2* seg_rec;
     unsigned* tile_map;
     uint64_t cap;  // decode tiles (and tiles, chunks, items) the workspace can hold
     uint8_t* ring;
@@ -107,9 +107,12 @@ void ws_carve(void* ws, uint64_t cap, uint8_t* ring, uint64_t ring_bytes, WsView
     v.ctl = (Ctl*)ws;
     v.partial = (float2*)((char*)ws + WS_CTL_BYTES);
     v.offs = base;
-    v.chB = Chain{base + cap, base + 2 * cap, base + 3 * cap};
-    v.chC = Chain{base + 4 * cap, base + 5 * cap, base + 6 * cap};
-    v.seg_flag = base + 7 * cap;
+    // look-back records (16 bytes per slot; cap is even, so they are 16-byte
+    // aligned): encoder tiles in [cap, 3 cap), width-scan chunks in
+    // [4 cap, 6 cap), stream starts of packed items in [7 cap, 8 cap)
+    v.chB = Chain{(ulonglong2*)(base + cap)};
+    v.chC = Chain{(ulonglong2*)(base + 4 * cap)};
+    v.seg_rec = (ulonglong2*)(base + 7 * cap);
     v.tile_map = (unsigned*)(base + 8 * cap);
     v.cap = cap;
     v.ring = ring;
@@ -129,6 +132,7 @@ int ws_view(void* ws, size_t bytes, WsView& v)
         if (ws_total(mid) <= bytes) lo = mid;
         else hi = mid;
     }
+    lo &= ~1ull;  // even: the look-back records stay 16-byte aligned (ws_total(lo) still fits)
     ws_carve(ws, lo, (uint8_t*)ws + ring_offset(lo), ring_ctas(lo) * RING_UNIT, v);
     return ZC_OK;
 }
@@ -163,7 +167,7 @@ Launch base_launch(const WsView& w)
     P.chB = w.chB;
     P.chC = w.chC;
     P.offs = w.offs;
-    P.seg_flag = w.seg_flag;
+    P.seg_rec = w.seg_rec;
     P.urows = DEC_U;
     P.ring = w.ring;
     P.ring_bytes = w.ring_bytes;
@@ -256,7 +260,7 @@ size_t zc_workspace_bytes(uint64_t n_total, int n_items)
     if (n_items < 1) n_items = 1;
     // decode slots: one per warp unit of at least 32 rows (1024 elements),
     // plus the partial tiles of every item
-    const uint64_t cap = n_total / 1024 + 16ull * (uint64_t)n_items + 2;
+    const uint64_t cap = (n_total / 1024 + 16ull * (uint64_t)n_items + 3) & ~1ull;  // even
     return ws_total(cap);
 }
 

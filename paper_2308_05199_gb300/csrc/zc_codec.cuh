@@ -62,7 +62,7 @@ struct Launch {
     Chain chB;                        // encoder tiles
     Chain chC;                        // width-scan chunks
     unsigned long long* offs;         // payload offset of every decode tile (global slot)
-    unsigned long long* seg_flag;     // packed mode: stream start published per item
+    ulonglong2* seg_rec;              // packed mode: stream start published per item
     unsigned long long* seg_off;      // packed mode: P + 1 stream offsets (caller's)
     const Item* items;                // device items, or null for `one`
     Item one;
@@ -884,17 +884,16 @@ __device__ __forceinline__ bool packed_start_warp(const Launch& P, bool first, u
     if (first) {
         start = ex;
         if (lane == 0) {
-            st_relaxed(P.seg_off + item_idx, ex);
-            st_release(P.seg_flag + item_idx, ((unsigned long long)E << 32) | 1ull);
+            P.seg_off[item_idx] = ex;
+            rec_store(P.seg_rec + item_idx, E, ST_PREFIX, false, ex);
         }
         return true;
     }
     int ok = 1;
     unsigned long long v = 0ull;
     if (lane == 0) {
-        ok = wait_flag(P.seg_flag + item_idx, E, P.wc.limit_ns);
+        ok = wait_rec(P.seg_rec + item_idx, E, P.wc.limit_ns, v);
         if (!ok) fail(P.ctl, ZC_ERR_TIMEOUT, g);
-        else v = ld_relaxed(P.seg_off + item_idx);
     }
     ok = __shfl_sync(FULL, ok, 0);
     start = __shfl_sync(FULL, v, 0);
@@ -1360,9 +1359,9 @@ struct ScatterSrc {
 // (its byte count), so that the look-backs of the tiles after it need not wait
 // until this CTA's resolver warp reaches it (the resolver handles its tiles in
 // order, and a tile it is still waiting on would hold back this one's
-// aggregate).  The resolver publishes the same aggregate again, then the
-// tile's inclusive prefix.  A chain's first tile publishes its prefix at once
-// (resolver), and a withheld tile (test hook) publishes nothing.
+// aggregate).  The resolver then publishes the tile's inclusive prefix.  A
+// chain's first tile publishes its prefix at once (resolver), and a withheld
+// tile (test hook) publishes nothing.
 __device__ __forceinline__ void publish_aggregate(const Launch& P, const TileSlot& S, unsigned E)
 {
     if (!S.valid || !S.pub) return;
@@ -1371,8 +1370,7 @@ __device__ __forceinline__ void publish_aggregate(const Launch& P, const TileSlo
     unsigned long long agg = S.head;
 #pragma unroll
     for (int w = 0; w < NWARPS; ++w) agg += (unsigned long long)S.segsz[w];
-    if (agg > AGG_INLINE_MAX) st_relaxed(P.chB.aggw + S.g, agg);
-    st_release(P.chB.flag + S.g, make_flag(E, ST_AGG, S.last != 0, agg));
+    rec_store(P.chB.rec + S.g, E, ST_AGG, S.last != 0, agg);
 }
 
 // Resolver warp: the tile's place in the chain (look-back over the tiles
@@ -1387,7 +1385,8 @@ __device__ __forceinline__ void resolve_slot(const Launch& P, TileSlot& S, unsig
         for (int w = 0; w < NWARPS; ++w) agg += (unsigned long long)S.segsz[w];
         const unsigned g0 = P.packed ? 0u : S.g - S.tile;
         bool expired = false;
-        ex = lookback_warp(P.chB, S.g, g0, agg, S.last != 0, E, P.wc, P.ctl, expired);
+        // the encoder warps published the aggregate already (publish_aggregate)
+        ex = lookback_warp(P.chB, S.g, g0, agg, S.last != 0, E, P.wc, P.ctl, expired, true);
         ok = !expired && packed_start_warp(P, S.first != 0, S.item, ex, S.g, E, start);
     }
     if ((threadIdx.x & 31) == 0) {

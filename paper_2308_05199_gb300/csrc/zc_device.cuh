@@ -286,25 +286,48 @@ __device__ __forceinline__ Xf xf_shfl(const Xf& f, int src)
     return o;
 }
 
-// Flag word of a tile: [63:32] epoch, [31:30] state, [29] h, [28] big,
-// [27:0] aggregate (when not big; else the aggregate is in the value word).
+// Look-back record of a tile: 16 bytes, written by one 16-byte store and
+// read by one 16-byte load, so the state and its value travel together and
+// no fence orders them.  x: [63:32] launch generation E, [31:30] state,
+// [29] h (the tile ends a stream).  y: [63:40] the low 24 bits of E again, a
+// check that the value belongs to the same store as the state, [39:0] the
+// value: the tile's aggregate (state AGG) or inclusive prefix (PREFIX).
+// Values are byte counts below 2^40.
 constexpr unsigned ST_AGG = 1u, ST_PREFIX = 2u;
-constexpr unsigned long long AGG_INLINE_MAX = (1ull << 28) - 1;
+constexpr int REC_VAL_BITS = 40;
+constexpr unsigned long long REC_VAL_MASK = (1ull << REC_VAL_BITS) - 1ull;
 
 struct Chain {
-    unsigned long long* flag;   // per tile
-    unsigned long long* aggw;   // per tile: aggregate when too large for the flag
-    unsigned long long* pref;   // per tile: inclusive prefix
+    ulonglong2* rec;  // per tile (16-byte aligned)
 };
 
-__device__ __forceinline__ unsigned long long make_flag(unsigned E, unsigned st, bool h,
-                                                        unsigned long long agg)
+__device__ __forceinline__ void rec_store(ulonglong2* p, unsigned E, unsigned st, bool h,
+                                          unsigned long long v)
 {
-    const bool big = agg > AGG_INLINE_MAX;
-    return ((unsigned long long)E << 32) | ((unsigned long long)st << 30) |
-           ((unsigned long long)h << 29) | ((unsigned long long)big << 28) |
-           (big ? 0ull : agg);
+    const unsigned long long x = ((unsigned long long)E << 32) | ((unsigned long long)st << 30) |
+                                 ((unsigned long long)h << 29);
+    const unsigned long long y = ((unsigned long long)(E & 0xffffffu) << REC_VAL_BITS) |
+                                 (v & REC_VAL_MASK);
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(x), "l"(y)
+                 : "memory");
 }
+__device__ __forceinline__ ulonglong2 rec_load(const ulonglong2* p)
+{
+    ulonglong2 r;
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];"
+                 : "=l"(r.x), "=l"(r.y)
+                 : "l"(p)
+                 : "memory");
+    return r;
+}
+__device__ __forceinline__ bool rec_valid(const ulonglong2& r, unsigned E)
+{
+    return (unsigned)(r.x >> 32) == E && ((r.x >> 30) & 3u) != 0u &&
+           (unsigned)(r.y >> REC_VAL_BITS) == (E & 0xffffffu);
+}
+__device__ __forceinline__ unsigned rec_state(const ulonglong2& r) { return (unsigned)(r.x >> 30) & 3u; }
+__device__ __forceinline__ bool rec_h(const ulonglong2& r) { return ((r.x >> 29) & 1ull) != 0ull; }
+__device__ __forceinline__ unsigned long long rec_val(const ulonglong2& r) { return r.y & REC_VAL_MASK; }
 
 struct WaitCfg {
     unsigned long long limit_ns;
@@ -317,44 +340,34 @@ struct LbSmem {
     int timed_out;
 };
 
-constexpr int LB_PER_LANE = 8;                 // predecessors inspected per lane
+constexpr int LB_PER_LANE = 4;                 // predecessors inspected per lane
 constexpr int LB_WINDOW = 32 * LB_PER_LANE;    // predecessors per look-back round
 
-__device__ __forceinline__ bool flag_valid(unsigned long long f, unsigned E)
-{
-    return (unsigned)(f >> 32) == E && ((f >> 30) & 3u) != 0u;
-}
-
 // Run by one whole warp.  g: this tile's slot; g0: first slot of its chain
-// (whose exclusive value is 0).  Publishes g's aggregate, then inspects the
-// LB_WINDOW preceding slots (LB_PER_LANE consecutive slots per lane), waits
-// until all of them have published, composes the aggregates after the nearest
-// inclusive prefix, and repeats further back if there is none.  Publishes g's
-// inclusive prefix and returns g's exclusive value (the same in every lane).
-// If the wait runs out, records ZC_ERR_TIMEOUT, sets `expired` and returns 0
-// (the prefix is still published, so the chain moves on; the status word
-// already marks the result unusable).
+// (whose exclusive value is 0).  Publishes g's aggregate (unless the caller
+// already has: agg_out), then inspects the LB_WINDOW preceding slots
+// (LB_PER_LANE consecutive slots per lane), waits until all of them have
+// published, composes the aggregates after the nearest inclusive prefix, and
+// repeats further back if there is none.  Publishes g's inclusive prefix and
+// returns g's exclusive value (the same in every lane).  If the wait runs
+// out, records ZC_ERR_TIMEOUT, sets `expired` and returns 0 (the prefix is
+// still published, so the chain moves on; the status word already marks the
+// result unusable).
 __device__ __forceinline__ unsigned long long lookback_warp(const Chain& ch, unsigned g,
                                                             unsigned g0, unsigned long long agg,
                                                             bool h, unsigned E, const WaitCfg& wc,
-                                                            Ctl* ctl, bool& expired)
+                                                            Ctl* ctl, bool& expired,
+                                                            bool agg_out = false)
 {
     const int lane = threadIdx.x & 31;
     const bool publish = (long long)g != wc.withhold;
     const Xf self{agg, 0ull, h};
     expired = false;
     if (g == g0) {
-        if (lane == 0 && publish) {
-            st_relaxed(ch.pref + g, xf_apply(self, 0ull));
-            if (agg > AGG_INLINE_MAX) st_relaxed(ch.aggw + g, agg);
-            st_release(ch.flag + g, make_flag(E, ST_PREFIX, h, agg));
-        }
+        if (lane == 0 && publish) rec_store(ch.rec + g, E, ST_PREFIX, h, xf_apply(self, 0ull));
         return 0ull;
     }
-    if (lane == 0 && publish) {
-        if (agg > AGG_INLINE_MAX) st_relaxed(ch.aggw + g, agg);
-        st_release(ch.flag + g, make_flag(E, ST_AGG, h, agg));
-    }
+    if (lane == 0 && publish && !agg_out) rec_store(ch.rec + g, E, ST_AGG, h, agg);
     Xf acc = xf_id();
     long long hi = (long long)g - 1;
     unsigned long long excl = 0ull;
@@ -362,17 +375,17 @@ __device__ __forceinline__ unsigned long long lookback_warp(const Chain& ch, uns
     while (true) {
         // slots j0 .. j0 + LB_PER_LANE - 1 of this lane, oldest first
         const long long j0 = hi - (LB_WINDOW - 1) + (long long)lane * LB_PER_LANE;
-        unsigned long long f[LB_PER_LANE];
+        ulonglong2 f[LB_PER_LANE];
         unsigned valid = 0;
 #pragma unroll
         for (int i = 0; i < LB_PER_LANE; ++i) {
             const long long j = j0 + i;
             if (j < (long long)g0) {
-                f[i] = 0ull;
+                f[i] = make_ulonglong2(0ull, 0ull);
                 valid |= 1u << i;
             } else {
-                f[i] = ld_relaxed(ch.flag + j);
-                if (flag_valid(f[i], E)) valid |= 1u << i;
+                f[i] = rec_load(ch.rec + j);
+                if (rec_valid(f[i], E)) valid |= 1u << i;
             }
         }
         unsigned ns = 32;
@@ -384,13 +397,11 @@ __device__ __forceinline__ unsigned long long lookback_warp(const Chain& ch, uns
 #pragma unroll
             for (int i = 0; i < LB_PER_LANE; ++i) {
                 if (!((valid >> i) & 1u)) {
-                    f[i] = ld_relaxed(ch.flag + (j0 + i));
-                    if (flag_valid(f[i], E)) valid |= 1u << i;
+                    f[i] = rec_load(ch.rec + (j0 + i));
+                    if (rec_valid(f[i], E)) valid |= 1u << i;
                 }
             }
         }
-        // the wide aggregates and the prefix read below were stored before the flags
-        fence_acquire_gpu();
         if (expired) {
             if (lane == 0) fail(ctl, ZC_ERR_TIMEOUT, g);
             excl = 0ull;
@@ -400,7 +411,7 @@ __device__ __forceinline__ unsigned long long lookback_warp(const Chain& ch, uns
         int pi = -1;
 #pragma unroll
         for (int i = 0; i < LB_PER_LANE; ++i) {
-            const bool is_pref = (j0 + i < (long long)g0) || ((f[i] >> 30) & 3u) == ST_PREFIX;
+            const bool is_pref = (j0 + i < (long long)g0) || rec_state(f[i]) == ST_PREFIX;
             if (is_pref) pi = i;
         }
         const unsigned pm = __ballot_sync(FULL, pi >= 0);
@@ -413,8 +424,8 @@ __device__ __forceinline__ unsigned long long lookback_warp(const Chain& ch, uns
                 const long long j = j0 + i;
                 if (j >= (long long)g0 && (lane > pl || i > pi)) {
                     Xf x;
-                    x.h = (f[i] >> 29) & 1u;
-                    x.a = ((f[i] >> 28) & 1u) ? ld_relaxed(ch.aggw + j) : (f[i] & AGG_INLINE_MAX);
+                    x.h = rec_h(f[i]);
+                    x.a = rec_val(f[i]);
                     x.b = 0ull;
                     t = xf_compose(t, x);
                 }
@@ -428,17 +439,17 @@ __device__ __forceinline__ unsigned long long lookback_warp(const Chain& ch, uns
         acc = xf_compose(xf_shfl(t, 31), acc);
         if (pl >= 0) {
             unsigned long long pv = 0ull;
-            if (lane == pl && j0 + pi >= (long long)g0) pv = ld_relaxed(ch.pref + (j0 + pi));
+#pragma unroll
+            for (int i = 0; i < LB_PER_LANE; ++i)
+                if (lane == pl && i == pi && j0 + pi >= (long long)g0) pv = rec_val(f[i]);
             pv = __shfl_sync(FULL, pv, pl);
             excl = xf_apply(acc, pv);
             break;
         }
         hi -= LB_WINDOW;
     }
-    if (lane == 0 && publish) {
-        st_relaxed(ch.pref + g, xf_apply(self, expired ? 0ull : excl));
-        st_release(ch.flag + g, make_flag(E, ST_PREFIX, h, agg));
-    }
+    if (lane == 0 && publish)
+        rec_store(ch.rec + g, E, ST_PREFIX, h, xf_apply(self, expired ? 0ull : excl));
     return excl;
 }
 
@@ -476,17 +487,17 @@ __device__ __forceinline__ void bar_arrive_n(unsigned id, unsigned n)
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-// Bounded wait for a value published with st_release on `flag` (epoch E in
-// the high word, nonzero low word); returns false if the wait ran out.
-__device__ __forceinline__ bool wait_flag(const unsigned long long* flag, unsigned E,
-                                          unsigned long long limit_ns)
+// Bounded wait for a record published with rec_store (generation E, any
+// state); returns false if the wait ran out, else its value in `v`.
+__device__ __forceinline__ bool wait_rec(const ulonglong2* p, unsigned E,
+                                         unsigned long long limit_ns, unsigned long long& v)
 {
     unsigned long long t0 = 0ull;
     unsigned ns = 32;
     while (true) {
-        const unsigned long long f = ld_relaxed(flag);
-        if ((unsigned)(f >> 32) == E && (unsigned)f != 0u) {
-            fence_acquire_gpu();
+        const ulonglong2 r = rec_load(p);
+        if (rec_valid(r, E)) {
+            v = rec_val(r);
             return true;
         }
         const unsigned long long now = globaltimer();
