@@ -14,8 +14,8 @@ resident in HBM:
   scatter pack       8 segments compressed as independent packed streams
   batched compress   1000 messages, 4 KiB - 64 MiB log-uniform, half FP32 /
                      half BF16, Student-t(3) x sigma, eb = 1e-3 sigma: one
-                     persistent launch (autotuned tile and grid) from a CUDA
-                     graph
+                     persistent launch (autotuned block size, tile and grid)
+                     from a CUDA graph
   selector path      a held-out mixed workload (about 4 GiB of the four
                      workload kinds) cut into 64 KiB chunks: statistics, MLP,
                      selection of block size or raw, batched compression, all
@@ -407,8 +407,9 @@ class RingRow:
 
 class BatchRow:
     """Batched compression of the 1000-message workload: one persistent
-    launch (tile size and grid from the library's autotuner) in a CUDA graph,
-    against the plain form (one zc_compress per message)."""
+    launch (block size, tile size and grid from the library's autotuner) in a
+    CUDA graph, against the plain form (one zc_compress per message at the
+    same block size)."""
 
     def __init__(self, torch, zc, workloads, stream, device, M=1000):
         self.torch, self.zc, self.stream = torch, zc, stream
@@ -423,7 +424,9 @@ class BatchRow:
         self.raw = sum(x.numel() * x.element_size() for x in self.xs)
         self.n_f32 = sum(1 for sp in specs if sp["dtype"] == "f32")
         self.b = zc.BatchCompress(self.xs, [32] * self.M, self.ebs, stream=stream)
-        self.best, self.points = self.b.autotune(tune_block=False, link_gbs=0.0, reps=3,
+        # the library's autotuner over block size, tile size and grid (the
+        # fastest candidate: no link term)
+        self.best, self.points = self.b.autotune(tune_block=True, link_gbs=0.0, reps=3,
                                                  stream=stream)
         self.b.run(stream)
         stream.synchronize()
@@ -438,15 +441,17 @@ class BatchRow:
         """Device ms of the graph launch vs the per-message loop (same streams
         byte for byte: checked on the total length)."""
         torch, zc, st = self.torch, self.zc, self.stream
-        outs = [torch.empty(zc.zc_max_compressed_bytes(x.numel(), 32), dtype=torch.uint8,
+        outs = [torch.empty(zc.zc_max_compressed_bytes(x.numel(), 16), dtype=torch.uint8,
                             device=x.device) for x in self.xs]
         obs = torch.zeros(self.M, dtype=torch.int64, device=self.xs[0].device)
         ws = self.b.ws
 
+        L = self.best["block"]
+
         def loop():
             for i, x in enumerate(self.xs):
                 zc._check(zc.zc_compress(x.data_ptr(), x.numel(), zc.dtype_code(x), zc.EB_ABS,
-                                         self.ebs[i], 32, outs[i].data_ptr(), outs[i].numel(),
+                                         self.ebs[i], L, outs[i].data_ptr(), outs[i].numel(),
                                          obs.data_ptr() + 8 * i, ws.ptr, ws.nbytes,
                                          st.cuda_stream), "zc_compress")
 
@@ -471,8 +476,8 @@ class BatchRow:
                 "per_message_loop_gbs": round(self.step_bytes() / loop_ms / 1e6, 1),
                 "batched_gbs": round(self.step_bytes() / batch_ms / 1e6, 1),
                 "same_total_bytes": same,
-                "autotuned": {"tile_chunks": self.best["tile_chunks"], "grid": self.best["grid"],
-                              "candidates": len(self.points)}}
+                "autotuned": {"block": self.best["block"], "tile_chunks": self.best["tile_chunks"],
+                              "grid": self.best["grid"], "candidates": len(self.points)}}
 
 
 class SelectorRow:
@@ -1010,6 +1015,7 @@ def run_ours(args, rank, world):
                                "+selector_heldout",
                    "n": W.n, "rel_eb": REL,
                    "eb_abs_ring": W.ring_row.eb_abs, "block": BLOCK,
+                   "batch_block": W.batch_row.best["block"],
                    "ring_ranks": W.ring_row.P, "ring_n_per_rank": W.ring_row.n,
                    "scatter_segments": P_RING, "batch_messages": W.batch_row.M,
                    "selector_heldout_bytes": W.sel_row.cb.raw_bytes,

@@ -83,13 +83,17 @@ __device__ __forceinline__ void load_span4(const Item& it, bool vec, unsigned lo
 // Largest block |delta| of the lane's block at blocks of G lanes (L = 4G):
 // the block's first lane contributes |q| of its first element (the head is
 // predicted from 0), every other lane |d| of its first element.
+// (xor shuffles within aligned groups of G lanes: every lane takes part with
+// the full mask, so no group waits for another)
 template <int G>
 __device__ __forceinline__ unsigned block_max(unsigned rest, unsigned e0q, unsigned e0d)
 {
     const int lane = threadIdx.x & 31;
-    const unsigned v = max(rest, (lane & (G - 1)) == 0 ? e0q : e0d);
-    const unsigned seg = G == 32 ? FULL : (((1u << G) - 1u) << (lane & ~(G - 1)));
-    return __reduce_max_sync(seg, v);
+    unsigned v = max(rest, (lane & (G - 1)) == 0 ? e0q : e0d);
+    if (G == 32) return __reduce_max_sync(FULL, v);
+#pragma unroll
+    for (int off = G / 2; off; off >>= 1) v = max(v, __shfl_xor_sync(FULL, v, off));
+    return v;
 }
 
 // One span of cnt elements (v: this lane's four); returns the span's L = 32
@@ -185,20 +189,32 @@ __global__ void __launch_bounds__(256, 4) k_chunk_stats(const Item* items, unsig
     const int cnt = m == 0 ? (int)n : ST_SPAN;  // elements of every sampled span
     // spans start at multiples of 128 elements: aligned loads when the chunk is
     const bool vec = ((uintptr_t)it.x & (it.x_dtype == ZC_F32 ? 15u : 7u)) == 0u;
-    auto span0 = [&](int jj) -> unsigned long long {
-        return (m == 0 || S == 1) ? 0ull
-                                  : (unsigned long long)ST_SPAN * (((unsigned long long)jj * (m - 1)) / (S - 1));
+    // span j starts at 128 floor(j (m - 1) / (S - 1)): stepped without a
+    // division per span (quotient and remainder of (m - 1) / (S - 1) once)
+    const unsigned long long den = S > 1 ? (unsigned long long)(S - 1) : 1ull;
+    const unsigned long long num = m > 0 ? m - 1 : 0ull;
+    const unsigned long long qa = num / den, ra = num % den;
+    unsigned long long sq = 0ull, sr = 0ull;  // floor(j num / den) and its remainder, next span
+    auto next_span0 = [&]() -> unsigned long long {
+        const unsigned long long v = (unsigned long long)ST_SPAN * sq;
+        sq += qa;
+        sr += ra;
+        if (sr >= den) {
+            sr -= den;
+            sq += 1ull;
+        }
+        return v;
     };
     StatAcc A;
     unsigned span_b32[ST_SPANS];  // per-span L = 32 bits (warp-uniform)
     if (cnt == ST_SPAN) {
         // full spans: two loaded ahead of the one being summarised
         float xa[4], xb[4], xc[4];
-        load_span4(it, vec, span0(0), cnt, xa);
-        if (S > 1) load_span4(it, vec, span0(1), cnt, xb);
+        load_span4(it, vec, next_span0(), cnt, xa);
+        if (S > 1) load_span4(it, vec, next_span0(), cnt, xb);
 #pragma unroll 1
         for (int j = 0; j < S; ++j) {
-            if (j + 2 < S) load_span4(it, vec, span0(j + 2), cnt, xc);
+            if (j + 2 < S) load_span4(it, vec, next_span0(), cnt, xc);
             span_b32[j] = stat_span<true>(xa, cnt, it, A);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
