@@ -206,7 +206,13 @@ __global__ void __launch_bounds__(256, 4) k_chunk_stats(const Item* items, unsig
         return v;
     };
     StatAcc A;
-    unsigned span_b32[ST_SPANS];  // per-span L = 32 bits (warp-uniform)
+    // sum over the spans of their L = 32 bits, and of its squares (warp-uniform;
+    // a span holds at most 128 x 25 bits, so both fit 32 bits over 16 spans)
+    unsigned span_b1 = 0u, span_b2 = 0u;
+    auto add_span = [&](unsigned b) {
+        span_b1 += b;
+        span_b2 += b * b;
+    };
     if (cnt == ST_SPAN) {
         // full spans: two loaded ahead of the one being summarised
         float xa[4], xb[4], xc[4];
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(256, 4) k_chunk_stats(const Item* items, unsig
 #pragma unroll 1
         for (int j = 0; j < S; ++j) {
             if (j + 2 < S) load_span4(it, vec, next_span0(), cnt, xc);
-            span_b32[j] = stat_span<true>(xa, cnt, it, A);
+            add_span(stat_span<true>(xa, cnt, it, A));
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 xa[k] = xb[k];
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(256, 4) k_chunk_stats(const Item* items, unsig
     } else {
         float xa[4];
         load_span4(it, vec, 0ull, cnt, xa);
-        span_b32[0] = stat_span<false>(xa, cnt, it, A);
+        add_span(stat_span<false>(xa, cnt, it, A));
     }
     const unsigned long long B16 = warp_sum_u64(A.b16), B32 = warp_sum_u64(A.b32);
     const unsigned long long B64 = warp_sum_u64(A.b64), B128 = warp_sum_u64(A.b128);
@@ -266,15 +272,11 @@ __global__ void __launch_bounds__(256, 4) k_chunk_stats(const Item* items, unsig
     f[10] = nd2 > 0.0f ? log2f(1.0f + __fdiv_rn((float)SAD2, nd2)) : 0.0f;
     f[11] = nd2 > 0.0f ? __fdiv_rn((float)NSC, nd2) : 0.0f;
     f[12] = __fdiv_rn(__fdiv_rn((float)HB, nheads), 24.0f);
-    float mean = 0.0f;
-    for (int j = 0; j < S; ++j) mean = __fadd_rn(mean, __fdiv_rn((float)span_b32[j], (float)cnt));
-    mean = __fdiv_rn(mean, (float)S);
-    float var = 0.0f;
-    for (int j = 0; j < S; ++j) {
-        const float e = __fsub_rn(__fdiv_rn((float)span_b32[j], (float)cnt), mean);
-        var = __fadd_rn(var, __fmul_rn(e, e));
-    }
-    f[13] = sqrtf(__fdiv_rn(var, (float)S));
+    // population spread of the spans' bits per element b_j / cnt, from exact
+    // integer moments: S^2 cnt^2 var = S sum b_j^2 - (sum b_j)^2
+    const long long dvar = (long long)S * (long long)span_b2 - (long long)span_b1 * (long long)span_b1;
+    const float sc2 = (float)S * (float)cnt;
+    f[13] = sqrtf(__fdiv_rn((float)dvar, __fmul_rn(sc2, sc2)));
     f[14] = it.x_dtype == ZC_F32 ? 1.0f : 0.5f;
     f[15] = __fdiv_rn(log2f(fn), 16.0f);
 #pragma unroll
