@@ -231,9 +231,9 @@ class Workload:
         self.packed = t.empty(self.pcap, dtype=t.uint8, device=device)
         self.seg = t.zeros(P_RING + 1, dtype=t.int64, device=device)
         # range, compress; width scan, decompress; scatter pack; batched compress
-        # (tile map, persistent kernel); selector (statistics, MLP, selection, tile
-        # map, batched compress); the ring adds its own
-        self.launches_per_step = 12
+        # (tile map, persistent kernel); selector (statistics, MLP, selection, the
+        # three grouping kernels, batched compress); the ring adds its own
+        self.launches_per_step = 14
 
     # the rows of one step, in step order: (name, input buffer index or None)
     ROWS = ("compress", "decompress", "ring_allreduce", "scatter_pack", "batched_compress",
