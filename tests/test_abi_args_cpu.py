@@ -127,7 +127,7 @@ def test_compress_variants_arguments(zc):
     assert h(FAKE, 10, 0, 0, 1e-3, 24, FAKE, 4096, FAKE, FAKE, BIG_WS, None) == zc.ERR_ARG
     assert h(FAKE, 10, 0, 7, 1e-3, 32, FAKE, 4096, FAKE, FAKE, BIG_WS, None) == zc.ERR_ARG
     na = zc.zc_compress_noalloc
-    assert na(FAKE, (1 << 24) + 1, 0, 0, 1e-3, 32, FAKE, 1 << 30, FAKE, FAKE, None) == zc.ERR_ARG
+    assert na(FAKE, zc.NOALLOC_MAX_N + 1, 0, 0, 1e-3, 32, FAKE, 1 << 30, FAKE, FAKE, None) == zc.ERR_ARG
     assert na(FAKE, 1000, 0, 0, 1e-3, 32, FAKE, 1 << 20, FAKE, None, None) == zc.ERR_ARG
     mm = zc.zc_minmax
     assert mm(FAKE, 10, 5, FAKE, FAKE, BIG_WS, None) == zc.ERR_ARG
