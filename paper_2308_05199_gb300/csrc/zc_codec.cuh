@@ -572,6 +572,24 @@ __device__ __forceinline__ void sts_u128_if(unsigned p, uint32_t v0, uint32_t v1
                  "@q st.shared.v4.u32 [%0], {%1, %2, %3, %4};\n\t}"
                  ::"r"(p), "r"(v0), "r"(v1), "r"(v2), "r"(v3), "r"(a), "r"(b) : "memory");
 }
+// Stores when m != 0 (a lane's bit of a mask); `p` is a shared-memory address.
+__device__ __forceinline__ void sts_u32_m(unsigned p, uint32_t v, uint32_t m)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.shared.u32 [%0], %1;\n\t}"
+                 ::"r"(p), "r"(v), "r"(m) : "memory");
+}
+__device__ __forceinline__ void sts_u8_m(unsigned p, uint32_t v, uint32_t m)
+{
+    asm volatile("{\n\t.reg .pred q;\n\t.reg .b16 h;\n\tcvt.u16.u32 h, %1;\n\t"
+                 "setp.ne.u32 q, %2, 0;\n\t@q st.shared.u8 [%0], h;\n\t}"
+                 ::"r"(p), "r"(v), "r"(m) : "memory");
+}
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
 // Predicated shared-memory stores of width bytes (`p` in shared memory).
 __device__ __forceinline__ void sts_if(uint8_t* p, uint4 v, bool c)
 {
@@ -679,7 +697,33 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
     // the group's width bytes, gathered in registers and stored once (GR * 32 / L bytes)
     uint32_t wacc[4] = {0u, 0u, 0u, 0u};
     uint32_t pk[GR / 2];  // L = 32: plane counts of the row pairs
-    if (!any_wide) {
+    // L = 32 and every value of the group within 8 planes (the common case at
+    // moderate bounds): four rows share a transpose.  Lane 8m + j then holds
+    // plane j of row m.  With M the ballot of nonzero planes, smearing every
+    // byte of M downwards gives F, whose byte m has the low np_m bits set:
+    // a lane stores its plane if its bit of F is set, at 4 popc(F & lanes
+    // below) bytes past the quad's start, and the quad takes 4 popc(F) bytes.
+    // The lane holding a row's top plane (j = np - 1), or lane j = 0 of a row
+    // without planes, writes the row's width byte, j, itself.
+    const bool quad = L == 32 && !any_wide && !__any_sync(FULL, (wide >> 8) != 0u);
+    if (quad) {
+        const uint32_t lt = lanemask_lt(), eq = 1u << lane;
+        const unsigned wrow = (unsigned)__cvta_generic_to_shared(wb) + (unsigned)(lane >> 3);
+#pragma unroll
+        for (int r = 0; r < GR; r += 4) {
+            const uint32_t w = __byte_perm(__byte_perm(u[r], u[r + 1], 0x0040),
+                                           __byte_perm(u[r + 2], u[r + 3], 0x0040), 0x5410);
+            const uint32_t t = tpose(w, tc);
+            const uint32_t M = __ballot_sync(FULL, t != 0u);
+            uint32_t F = M | ((M >> 1) & 0x7f7f7f7fu);
+            F |= (F >> 2) & 0x3f3f3f3fu;
+            F |= (F >> 4) & 0x0f0f0f0fu;
+            sts_u32_m(seg + lo + 4u * (unsigned)__popc(F & lt), t, F & eq);
+            const uint32_t top = (F & ~((F >> 1) & 0x7f7f7f7fu)) | (~F & 0x01010101u);
+            sts_u8_m(wrow + r, (uint32_t)(lane & 7), top & eq);
+            lo += 4 * __popc(F);
+        }
+    } else if (!any_wide) {
         // every value of the group fits 16 bits (the common case): paired (or
         // quadrupled) rows share a transpose, with no per-pair votes
 #pragma unroll
@@ -819,7 +863,7 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
     // one store of the group's width bytes (wb is 16-byte aligned per group
     // at L = 16, 8 at L = 32, 4 at L = 64, 2 at L = 128)
     if (L == 16) sts_if(wb, make_uint4(wacc[0], wacc[1], wacc[2], wacc[3]), lane == 0);
-    else if (L == 32) sts_if(wb, make_uint2(wacc[0], wacc[1]), lane == 0);
+    else if (L == 32) sts_if(wb, make_uint2(wacc[0], wacc[1]), lane == 0 && !quad);
     else if (L == 64) sts_if(wb, wacc[0], lane == 0);
     else sts_if(wb, (unsigned short)wacc[0], lane == 0);
     return lo;

@@ -123,6 +123,52 @@ def test_wide_and_narrow_blocks_mixed(zc, block):
     np.testing.assert_array_equal(np_of(sm), r_sum)
 
 
+def eight_plane_boundary_input(n_groups=400, tail=77, seed=23):
+    """Quantized values built group by group (8 rows of 32): every group's
+    largest sign-magnitude delta is drawn from one class: none, below 2^8
+    (at most 8 planes), exactly 2^8 - 1 or 2^8 (either side of the 8-plane
+    boundary), below 2^16, or wide.  Returns FP32 data whose quantization at
+    eb = 1e-3 gives exactly these values, and the class of every group."""
+    g = np.random.default_rng(seed)
+    eb_f, two = oracle.qparams(1e-3)
+    n = 256 * n_groups + tail
+    cls = g.integers(0, 6, n_groups + 1)
+    q = np.zeros(n, np.int64)
+    for k in range(n_groups + 1):
+        lo, hi = 256 * k, min(256 * (k + 1), n)
+        if lo >= n:
+            break
+        c = cls[k]
+        dmax = [0, 60, 127, 128, 30000, 100000][c]
+        d = g.integers(-dmax, dmax + 1, hi - lo) if dmax else np.zeros(hi - lo, np.int64)
+        if c in (2, 3):
+            d[g.integers(0, hi - lo)] = dmax * (1 if g.random() < 0.5 else -1)
+        # within every block of 32 the first value is a delta from 0
+        for b in range(lo, hi, 32):
+            e = min(b + 32, hi)
+            q[b:e] = np.cumsum(d[b - lo:e - lo])
+    x = (q.astype(np.float64) * np.float64(two)).astype(np.float32)
+    return x, cls[: (n + 255) // 256]
+
+
+def test_eight_plane_groups_at_l32(zc):
+    """L = 32 encodes a group whose values all fit 8 planes with four rows per
+    transpose, otherwise two rows (16 planes) or one: groups on both sides of
+    each boundary, a ragged tail, plain and heads-apart streams, decoding."""
+    x, cls = eight_plane_boundary_input()
+    n = x.size
+    s, st = gpu_compress(zc, torch.from_numpy(x), 1e-3, 32)
+    ref = oracle.compress(x, 1e-3, 5)
+    assert st[0] == 0 and s == ref
+    widths = np.frombuffer(ref[32:32 + (n + 31) // 32], np.uint8)
+    gmax = np.array([widths[i:i + 8].max() for i in range(0, widths.size, 8)])
+    assert (gmax <= 7).mean() > 0.2 and (gmax == 8).any() and (gmax > 16).any()
+    cmp = torch.frombuffer(bytearray(ref), dtype=torch.uint8).cuda()
+    np.testing.assert_array_equal(np_of(zc.decompress(cmp, n)), oracle.decompress(ref, n))
+    out, ob = zc.compress(torch.from_numpy(x).cuda(), 1e-3, 32, heads=True)
+    assert zc.stream_bytes(out, ob) == oracle.compress_heads(x, 1e-3, 5)
+
+
 @pytest.mark.parametrize("block", BLOCKS)
 def test_bf16_input(zc, block):
     x = (signal("tdist", 20011, 5) * 3).to(torch.bfloat16)
