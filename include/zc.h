@@ -500,11 +500,13 @@ void zc_set_wait_limit_ns(uint64_t ns);
 void zc_debug_withhold_tile(int64_t tile);
 
 /* Tile size of the next encoder launches and plans: chunks of 2048 elements
- * per CTA tile (4, 8 or 16; default 8).  Larger tiles shorten the chain of
- * offsets between tiles and stage more bytes per CTA in the workspace's tile
- * rings (so the same workspace runs fewer CTAs of them); small inputs keep
- * more CTAs busy with small tiles.  Returns ZC_ERR_ARG for other values.
- * Changes no stream byte. */
+ * per CTA tile (4, 8 or 16), or 0 (the default) to choose per launch: the
+ * largest of 16 and 8 that is no larger than the launch's mean item and
+ * still gives about 5/3 tiles per resident encoder CTA, else 4.  Larger
+ * tiles shorten the chain of offsets between tiles and stage more bytes per
+ * CTA in the workspace's tile rings (so the same workspace runs fewer CTAs
+ * of them); small inputs keep more CTAs busy with small tiles.  Returns
+ * ZC_ERR_ARG for other values.  Changes no stream byte. */
 int zc_set_tile_chunks(int chunks);
 
 /* Library version string. */

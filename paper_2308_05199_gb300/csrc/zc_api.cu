@@ -13,7 +13,7 @@ using namespace zc;
 
 namespace {
 
-int g_chunks = 8;  // sub-tiles of 2048 elements per encoder tile
+int g_chunks = 0;  // sub-tiles of 2048 elements per encoder tile; 0: chosen per launch
 unsigned long long g_wait_ns = 1000000000ull;
 long long g_withhold = -1;
 
@@ -137,9 +137,8 @@ int ws_view(void* ws, size_t bytes, WsView& v)
     return ZC_OK;
 }
 
-// Encoder CTAs for a launch that wants `want` (its tile count or a chosen
-// grid): at most one per ring and the resident CTAs of this GPU.
-uint64_t enc_grid(uint64_t want, int U, const WsView& w)
+// SM count of the current device (queried once per device).
+int sm_count()
 {
     static std::atomic<int> sms[64];  // SM count per device, 0 until queried
     int dev = 0;
@@ -151,6 +150,32 @@ uint64_t enc_grid(uint64_t want, int U, const WsView& w)
             sms[dev].store(c, std::memory_order_relaxed);
         if (c > 0) n_sm = c;
     }
+    return n_sm;
+}
+
+// Tile size of a launch over `total` elements in items of `per_item`
+// elements on average, unless zc_set_tile_chunks fixed one: the largest of 16
+// and 8 chunks that is no larger than the mean item and still gives about 5/3
+// tiles per resident encoder CTA, else 4.  Larger tiles cost fewer look-backs
+// and per-tile steps, smaller ones keep every CTA busy (compression of the
+// 512^3 field's first 2^20 .. 2^27 elements was fastest at 4 chunks up to
+// 2^23 elements, 8 at 2^24 and 16 from 2^25 on).
+int tile_chunks_for(uint64_t total, uint64_t per_item)
+{
+    if (g_chunks) return g_chunks;
+    const uint64_t want = (uint64_t)sm_count() * ENC_CTAS_PER_SM * 5 / 3;
+    for (int C = 16; C >= 8; C /= 2) {
+        const uint64_t te = (uint64_t)NWARPS * unit_rows(C) * 32;
+        if (te <= per_item && (total + te - 1) / te >= want) return C;
+    }
+    return 4;
+}
+
+// Encoder CTAs for a launch that wants `want` (its tile count or a chosen
+// grid): at most one per ring and the resident CTAs of this GPU.
+uint64_t enc_grid(uint64_t want, int U, const WsView& w)
+{
+    const int n_sm = sm_count();
     uint64_t g = want;
     const uint64_t rings = w.ring_bytes / ring_cta_bytes(U);
     const uint64_t resident = (uint64_t)n_sm * ENC_CTAS_PER_SM;
@@ -326,7 +351,7 @@ int compress_impl(const void* d_in, uint64_t n, int dtype, int eb_mode, double e
     WsView w;
     int st = ws_view(d_ws, ws_bytes, w);
     if (st) return st;
-    const int C = heads ? 8 : g_chunks;
+    const int C = heads ? 8 : tile_chunks_for(n, n);
     const uint64_t tiles = tiles_for(n, unit_rows(C));
     if (tiles > w.cap || tiles > 0x7fffffffull) return ZC_ERR_WORKSPACE;
     Launch P = base_launch(w);
@@ -441,7 +466,7 @@ int zc_reduce_step(const void* d_cmp_in, size_t cmp_in_cap, const float* d_local
     WsView w;
     int st = ws_view(d_ws, ws_bytes, w);
     if (st) return st;
-    const int C = g_chunks;
+    const int C = tile_chunks_for(n, n);
     const uint64_t tiles = tiles_for(n, unit_rows(C));
     const uint64_t chunks = chunks_for(tiles);
     if (tiles * NWARPS > w.cap || tiles > 0x7fffffffull) return ZC_ERR_WORKSPACE;
@@ -488,7 +513,9 @@ int zc_plan_reduce(zc_plan* plan, int P, const zc_reduce_item* h_items, double e
     float eb, two, inv;
     int st = qparams(eb_abs, &eb, &two, &inv);
     if (st) return st;
-    const int C = g_chunks;
+    uint64_t total_n = 0;
+    for (int r = 0; r < P; ++r) total_n += h_items[r].n;
+    const int C = tile_chunks_for(total_n, total_n / (uint64_t)P);
     std::vector<Item> items((size_t)P);
     uint64_t tile = 0, chunk = 0;
     int has_cin = 0;
@@ -585,7 +612,9 @@ int zc_scatter_pack(const void* d_in, int dtype, int P, const uint64_t* h_counts
     WsView w;
     int st = ws_view(d_ws, ws_bytes, w);
     if (st) return st;
-    const int C = g_chunks;
+    uint64_t all_n = 0;
+    for (int p = 0; p < P; ++p) all_n += h_counts[p];
+    const int C = tile_chunks_for(all_n, all_n / (uint64_t)P);
     thread_local static ScatterParams SP;  // host staging of the by-value parameter block
     uint64_t tile = 0, total_n = 0, min_cap = 0;
     std::vector<const void*> ptrs((size_t)P);
@@ -667,7 +696,9 @@ int zc_plan_compress_batch(zc_batch* plan, int n_msgs, const zc_message* h_msgs,
         !aligned(d_packed, 16) || d_msg_off == nullptr || !aligned(d_msg_off, 8) ||
         d_table == nullptr || !aligned(d_table, 16) || table_bytes < zc_batch_table_bytes(n_msgs))
         return ZC_ERR_ARG;
-    const int C = tile_chunks ? tile_chunks : g_chunks;
+    uint64_t all_n = 0;
+    for (int i = 0; i < n_msgs; ++i) all_n += h_msgs[i].n;
+    const int C = tile_chunks ? tile_chunks : tile_chunks_for(all_n, all_n / (uint64_t)n_msgs);
     if (C != 4 && C != 8 && C != 16) return ZC_ERR_ARG;
     std::vector<Item> items((size_t)n_msgs);
     uint64_t tile = 0, min_cap = 0;
@@ -909,7 +940,7 @@ void zc_debug_withhold_tile(int64_t tile) { g_withhold = tile; }
 
 int zc_set_tile_chunks(int chunks)
 {
-    if (chunks != 4 && chunks != 8 && chunks != 16) return ZC_ERR_ARG;
+    if (chunks != 0 && chunks != 4 && chunks != 8 && chunks != 16) return ZC_ERR_ARG;
     g_chunks = chunks;
     return ZC_OK;
 }

@@ -100,6 +100,29 @@ def test_tile_size_does_not_change_the_stream(zc, chunks):
         zc.zc_set_tile_chunks(8)
 
 
+def test_automatic_tile_size_streams(zc):
+    """With no tile size set the library picks one per launch (4 chunks for
+    2^20 elements, 8 for 2^24, 16 for 2^25 on 152 SMs): whole streams still
+    byte-equal to the oracle's, and the ring step and scatter pack at the
+    same sizes."""
+    try:
+        assert zc.zc_set_tile_chunks(0) == 0
+        for n in ((1 << 20) + 3, (1 << 24) + 5, (1 << 25) + 7):
+            x = signal("walk", n, n)
+            s, st = gpu_compress(zc, x, 1e-3, 32)
+            assert st[0] == 0 and s == oracle.compress(np_of(x), 1e-3, 5), n
+        n = (1 << 25) + 7
+        x = signal("walk", n, 5)
+        rb = oracle.compress(np_of(x), 1e-3, 5)
+        cmp = torch.frombuffer(bytearray(rb), dtype=torch.uint8).cuda()
+        out, ob, sm = zc.reduce_step(cmp, x.cuda(), 1e-3, 32, want_sum=True)
+        r_s, r_sum = oracle.reduce_step(rb, np_of(x), 1e-3, 5, want_sum=True)
+        assert zc.stream_bytes(out, ob) == r_s
+        np.testing.assert_array_equal(np_of(sm), r_sum)
+    finally:
+        zc.zc_set_tile_chunks(8)
+
+
 @pytest.mark.parametrize("block", BLOCKS)
 def test_wide_and_narrow_blocks_mixed(zc, block):
     """Heavy-tailed data at a tight bound: blocks above 16 planes (one row per

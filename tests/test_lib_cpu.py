@@ -97,6 +97,7 @@ def test_argument_errors_without_gpu(lib):
     lib.zc_set_tile_chunks.restype = ctypes.c_int
     assert lib.zc_set_tile_chunks(5) == 1
     assert lib.zc_set_tile_chunks(8) == 0
+    assert lib.zc_set_tile_chunks(0) == 0  # chosen per launch (the default)
 
 
 def test_batch_plan_argument_errors_without_gpu():
