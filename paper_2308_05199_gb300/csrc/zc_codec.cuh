@@ -697,31 +697,52 @@ __device__ __forceinline__ int encode_group(const float acc[GR], int nrem, float
     // the group's width bytes, gathered in registers and stored once (GR * 32 / L bytes)
     uint32_t wacc[4] = {0u, 0u, 0u, 0u};
     uint32_t pk[GR / 2];  // L = 32: plane counts of the row pairs
-    // L = 32 and every value of the group within 8 planes (the common case at
-    // moderate bounds): four rows share a transpose.  Lane 8m + j then holds
-    // plane j of row m.  With M the ballot of nonzero planes, smearing every
-    // byte of M downwards gives F, whose byte m has the low np_m bits set:
-    // a lane stores its plane if its bit of F is set, at 4 popc(F & lanes
-    // below) bytes past the quad's start, and the quad takes 4 popc(F) bytes.
-    // The lane holding a row's top plane (j = np - 1), or lane j = 0 of a row
-    // without planes, writes the row's width byte, j, itself.
-    const bool quad = L == 32 && !any_wide && !__any_sync(FULL, (wide >> 8) != 0u);
+    // Every value of the group within 8 planes (the common case at moderate
+    // bounds; L >= 32): four rows share a transpose, and lane 8m + j then
+    // holds plane j of row m.  M is the ballot of nonzero planes.
+    //   L = 32 (a block per row): smearing every byte of M downwards gives F,
+    //   whose byte m has the low np_m bits set; a lane stores its plane if
+    //   its bit of F is set, at 4 popc(F & lanes below) bytes past the quad's
+    //   start, and the quad takes 4 popc(F) bytes.  The lane at a row's top
+    //   plane (j = np - 1), or lane j = 0 of a row without planes, writes the
+    //   row's width byte, j, itself.
+    //   L = 64 (rows 0-1 and 2-3 are blocks): the block masks are bytes 0 | 1
+    //   and 2 | 3 of M; plane j of a block is 8 bytes, its two rows' words.
+    //   L = 128 (one block): the block mask is the OR of M's bytes; plane j
+    //   is 16 bytes, the four rows' words.
+    const bool quad = L >= 32 && !any_wide && !__any_sync(FULL, (wide >> 8) != 0u);
     if (quad) {
+        const int j = lane & 7, m4 = lane >> 3;
         const uint32_t lt = lanemask_lt(), eq = 1u << lane;
-        const unsigned wrow = (unsigned)__cvta_generic_to_shared(wb) + (unsigned)(lane >> 3);
+        const unsigned wrow = (unsigned)__cvta_generic_to_shared(wb) + (unsigned)m4;
 #pragma unroll
         for (int r = 0; r < GR; r += 4) {
             const uint32_t w = __byte_perm(__byte_perm(u[r], u[r + 1], 0x0040),
                                            __byte_perm(u[r + 2], u[r + 3], 0x0040), 0x5410);
             const uint32_t t = tpose(w, tc);
             const uint32_t M = __ballot_sync(FULL, t != 0u);
-            uint32_t F = M | ((M >> 1) & 0x7f7f7f7fu);
-            F |= (F >> 2) & 0x3f3f3f3fu;
-            F |= (F >> 4) & 0x0f0f0f0fu;
-            sts_u32_m(seg + lo + 4u * (unsigned)__popc(F & lt), t, F & eq);
-            const uint32_t top = (F & ~((F >> 1) & 0x7f7f7f7fu)) | (~F & 0x01010101u);
-            sts_u8_m(wrow + r, (uint32_t)(lane & 7), top & eq);
-            lo += 4 * __popc(F);
+            if (L == 32) {
+                uint32_t F = M | ((M >> 1) & 0x7f7f7f7fu);
+                F |= (F >> 2) & 0x3f3f3f3fu;
+                F |= (F >> 4) & 0x0f0f0f0fu;
+                sts_u32_m(seg + lo + 4u * (unsigned)__popc(F & lt), t, F & eq);
+                const uint32_t top = (F & ~((F >> 1) & 0x7f7f7f7fu)) | (~F & 0x01010101u);
+                sts_u8_m(wrow + r, (uint32_t)j, top & eq);
+                lo += 4 * __popc(F);
+            } else if (L == 64) {
+                const uint32_t X = M | (M >> 8);
+                const int npA = 32 - __clz(X & 0xffu), npB = 32 - __clz((X >> 16) & 0xffu);
+                sts_u32_if(seg + lo + 8 * j + 4 * (m4 & 1) + (hmask & (8 * npA)), t, j,
+                           hi ? npB : npA);
+                wacc[0] |= ((uint32_t)width_byte(npA) | ((uint32_t)width_byte(npB) << 8)) << (8 * (r / 2));
+                lo += 8 * (npA + npB);
+            } else {
+                const uint32_t X = M | (M >> 16);
+                const int np = 32 - __clz((X | (X >> 8)) & 0xffu);
+                sts_u32_if(seg + lo + 16 * j + 4 * m4, t, j, np);
+                wacc[0] |= (uint32_t)width_byte(np) << (8 * (r / 4));
+                lo += 16 * np;
+            }
         }
     } else if (!any_wide) {
         // every value of the group fits 16 bits (the common case): paired (or

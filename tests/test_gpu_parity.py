@@ -146,7 +146,7 @@ def test_wide_and_narrow_blocks_mixed(zc, block):
     np.testing.assert_array_equal(np_of(sm), r_sum)
 
 
-def eight_plane_boundary_input(n_groups=400, tail=77, seed=23):
+def eight_plane_boundary_input(block=32, n_groups=400, tail=77, seed=23):
     """Quantized values built group by group (8 rows of 32): every group's
     largest sign-magnitude delta is drawn from one class: none, below 2^8
     (at most 8 planes), exactly 2^8 - 1 or 2^8 (either side of the 8-plane
@@ -166,30 +166,38 @@ def eight_plane_boundary_input(n_groups=400, tail=77, seed=23):
         d = g.integers(-dmax, dmax + 1, hi - lo) if dmax else np.zeros(hi - lo, np.int64)
         if c in (2, 3):
             d[g.integers(0, hi - lo)] = dmax * (1 if g.random() < 0.5 else -1)
-        # within every block of 32 the first value is a delta from 0
-        for b in range(lo, hi, 32):
-            e = min(b + 32, hi)
+        # within every block the first value is a delta from 0
+        for b in range(lo, hi, block):
+            e = min(b + block, hi)
             q[b:e] = np.cumsum(d[b - lo:e - lo])
     x = (q.astype(np.float64) * np.float64(two)).astype(np.float32)
     return x, cls[: (n + 255) // 256]
 
 
-def test_eight_plane_groups_at_l32(zc):
-    """L = 32 encodes a group whose values all fit 8 planes with four rows per
-    transpose, otherwise two rows (16 planes) or one: groups on both sides of
-    each boundary, a ragged tail, plain and heads-apart streams, decoding."""
-    x, cls = eight_plane_boundary_input()
+@pytest.mark.parametrize("block", [32, 64, 128])
+def test_eight_plane_groups(zc, block):
+    """At L >= 32 a group whose values all fit 8 planes is encoded with four
+    rows per transpose, otherwise two rows (16 planes) or one: groups on both
+    sides of each boundary, a ragged tail, plain and heads-apart streams,
+    decoding."""
+    lg = int(math.log2(block))
+    x, cls = eight_plane_boundary_input(block)
     n = x.size
-    s, st = gpu_compress(zc, torch.from_numpy(x), 1e-3, 32)
-    ref = oracle.compress(x, 1e-3, 5)
+    s, st = gpu_compress(zc, torch.from_numpy(x), 1e-3, block)
+    ref = oracle.compress(x, 1e-3, lg)
     assert st[0] == 0 and s == ref
-    widths = np.frombuffer(ref[32:32 + (n + 31) // 32], np.uint8)
-    gmax = np.array([widths[i:i + 8].max() for i in range(0, widths.size, 8)])
+    widths = np.frombuffer(ref[32:32 + (n + block - 1) // block], np.uint8)
+    per = 256 // block  # blocks of a group of 8 rows
+    gmax = np.array([widths[i:i + per].max() for i in range(0, widths.size, per)])
     assert (gmax <= 7).mean() > 0.2 and (gmax == 8).any() and (gmax > 16).any()
     cmp = torch.frombuffer(bytearray(ref), dtype=torch.uint8).cuda()
     np.testing.assert_array_equal(np_of(zc.decompress(cmp, n)), oracle.decompress(ref, n))
-    out, ob = zc.compress(torch.from_numpy(x).cuda(), 1e-3, 32, heads=True)
-    assert zc.stream_bytes(out, ob) == oracle.compress_heads(x, 1e-3, 5)
+    out, ob = zc.compress(torch.from_numpy(x).cuda(), 1e-3, block, heads=True)
+    assert zc.stream_bytes(out, ob) == oracle.compress_heads(x, 1e-3, lg)
+    out, ob, sm = zc.reduce_step(cmp, torch.from_numpy(x).cuda(), 1e-3, block, want_sum=True)
+    r_s, r_sum = oracle.reduce_step(ref, x, 1e-3, lg, want_sum=True)
+    assert zc.stream_bytes(out, ob) == r_s
+    np.testing.assert_array_equal(np_of(sm), r_sum)
 
 
 @pytest.mark.parametrize("block", BLOCKS)
