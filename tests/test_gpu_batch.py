@@ -78,6 +78,22 @@ def test_batch_streams_match_oracle(zc, chunks, grid):
     check_against_oracle(b, xs, blocks, ebs)
 
 
+@pytest.mark.parametrize("sizes", [[1 << 20] * 36 + [70001, 3],  # mean >= 2^15: 16-chunk tiles
+                                   SIZES_MIX[:8] * 60])             # mean 6527: 4-chunk tiles
+def test_batch_automatic_tile_size(zc, sizes):
+    """With no tile size set, a batch plan takes the largest tile no larger
+    than its mean message that keeps about 5/3 tiles per resident CTA: every
+    stream still byte-equal to the oracle's."""
+    try:
+        assert zc.zc_set_tile_chunks(0) == 0
+        xs, blocks, ebs = mixed_messages(77, sizes)
+        b = zc.BatchCompress([x.cuda() for x in xs], blocks, ebs)
+        b.run()
+        check_against_oracle(b, xs, blocks, ebs)
+    finally:
+        zc.zc_set_tile_chunks(8)
+
+
 def test_batch_single_message_equals_plain_compress(zc):
     x = W.student_t3(250001, 0.01, 7).cuda()
     b = zc.BatchCompress([x], [32], [1e-5])

@@ -119,6 +119,14 @@ def test_automatic_tile_size_streams(zc):
         r_s, r_sum = oracle.reduce_step(rb, np_of(x), 1e-3, 5, want_sum=True)
         assert zc.stream_bytes(out, ob) == r_s
         np.testing.assert_array_equal(np_of(sm), r_sum)
+        # scatter pack: 8 segments of about 2^22 elements (16-chunk tiles)
+        counts = [(1 << 22) - 3 * k for k in range(8)]
+        displs = list(np.cumsum([0] + counts[:-1]))
+        packed, seg = zc.scatter_pack(x.cuda(), counts, displs, 1e-3, 32)
+        ref, ref_seg = oracle.scatter_pack(np_of(x), counts, displs, 1e-3, 5)
+        seg_h = seg.cpu().numpy().astype(np.uint64)
+        np.testing.assert_array_equal(seg_h, ref_seg)
+        assert packed[: int(seg_h[-1])].cpu().numpy().tobytes() == ref
     finally:
         zc.zc_set_tile_chunks(8)
 
