@@ -17,10 +17,12 @@ resident in HBM:
                      persistent launch (autotuned block size, tile and grid)
                      from a CUDA graph
   selector path      a held-out mixed workload (about 4 GiB of the four
-                     workload kinds) cut into 64 KiB chunks: statistics, MLP,
-                     selection of block size or raw, batched compression, all
-                     from one CUDA graph (network trained at set-up on 10^5
-                     chunks by the library's own gradient and SGD kernels)
+                     workload kinds) cut into 64 KiB chunks: statistics, the
+                     bits and time networks, selection of block size or raw,
+                     batched compression, all from one CUDA graph (networks
+                     trained at set-up on 10^5 chunks by the library's own
+                     gradient and SGD kernels; time labels from the codec
+                     timed on groups of similar training chunks)
 
 ``value`` is the algorithmic bytes of one step (every kernel's input read
 plus output written, the extra input read of the relative bound included)
@@ -489,6 +491,7 @@ class SelectorRow:
     LINK_GBS = 12.5  # the paper's 100 Gb/s network, as a model parameter
 
     def __init__(self, torch, zc, stream, device, train_chunks, heldout_bytes, epochs):
+        import numpy as np
         from paper_2308_05199_gb300 import selector as S
         self.torch, self.zc, self.S, self.stream = torch, zc, S, stream
         t0 = time.perf_counter()
@@ -499,17 +502,24 @@ class SelectorRow:
         for link in (self.LINK_GBS, 100.0):
             self.cfg[link] = tr.cost_model(link_gbs=link)
         self.uniform_ns = [round(v, 6) for v in tr.uniform_ns_per_byte]
-        X, T, keep, _ = S.dataset(tr)
+        X, T, keep, bits = S.dataset(tr)
+        # time labels: the codec timed on groups of similar training chunks
+        rates, _ = S.time_labels(tv, te, bits, groups=16, stream=stream)
+        TT = torch.from_numpy(np.log2(rates[keep]).astype(np.float32)).to(device)
         self.mlp = S.Mlp(seed=0)
         self.mlp.set_norm(X)
+        self.tmlp = S.Mlp(seed=1)
+        self.tmlp.set_norm(X)
         t1 = time.perf_counter()
         self.hist = self.mlp.fit(X, T, epochs=epochs, batch=256, lr=0.02, momentum=0.9, seed=0,
                                  stream=stream)
+        self.thist = self.tmlp.fit(X, TT, epochs=epochs, batch=256, lr=0.02, momentum=0.9,
+                                   seed=1, stream=stream)
         stream.synchronize()
         self.train_s = time.perf_counter() - t1
         self.n_train = int(keep.sum())
         self.setup_s = t1 - t0
-        del tr, tv, te, X, T
+        del tr, tv, te, X, T, TT
         torch.cuda.empty_cache()
         with torch.cuda.stream(stream):
             xs, ebs, kinds = S.mixed_messages(heldout_bytes, seed=7, device=device)
@@ -517,13 +527,14 @@ class SelectorRow:
         stream.synchronize()
         self.xs, self.ebs = xs, ebs
         hv, he = S.split_chunks(xs, ebs)
+        self.heldout_ebs = he
         self.cb = S.ChunkBatch(hv, he, stream=stream)
         cfg = self.cfg[self.LINK_GBS]
-        self.cb.run_selected(cfg, self.mlp)
+        self.cb.run_selected(cfg, self.mlp, self.tmlp)
         stream.synchronize()
         self.graph = zc.Graph(stream)
         with self.graph.capture():
-            self.cb.run_selected(cfg, self.mlp)
+            self.cb.run_selected(cfg, self.mlp, self.tmlp)
 
     def step_bytes(self):
         # sampled statistics read + codec read + packed write (the network and
@@ -537,7 +548,9 @@ class SelectorRow:
         torch, zc, st, cb = self.torch, self.zc, self.stream, self.cb
         parts = [("stats", cb.stats),
                  ("mlp_forward", lambda: self.mlp.forward(cb.feat, out=cb.pred, stream=st)),
-                 ("select", lambda: cb.select(cfg, cb.pred)),
+                 ("mlp_forward_time", lambda: self.tmlp.forward(cb.feat, out=cb.pred_time,
+                                                                stream=st)),
+                 ("select", lambda: cb.select(cfg, cb.pred, cb.pred_time)),
                  ("compress", lambda: cb.batch.run(st)),
                  ("decompress", lambda: cb.dec.run(st))]
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)]
@@ -554,13 +567,30 @@ class SelectorRow:
 
     def report(self, reps=3):
         """Mispredicts and modelled end-to-end GB/s of the plain per-message
-        form, the batched heuristic and the batched learned selector."""
+        form, the batched heuristic and the batched learned selector (bits
+        network alone, and with the time network)."""
+        import numpy as np
         torch, zc, S, st = self.torch, self.zc, self.S, self.stream
         cb = self.cb
         bits = cb.true_bits()
+        # the held-out chunks' own codec rates, measured like the training labels
+        hrates, _ = S.time_labels(cb.views, [float(e) for e in self.heldout_ebs], bits,
+                                  groups=16, stream=st)
+        cb.stats()
+        pt = self.tmlp.forward(cb.feat, out=cb.pred_time, stream=st)
+        cb.sync()
+        okr = torch.isfinite(cb.feat).all(1).cpu().numpy()
+        lt = np.log2(hrates[okr])
+        uni = np.log2(np.array(self.uniform_ns))[None, :]
         ev = lambda: torch.cuda.Event(enable_timing=True)
         out = {"train_chunks": self.n_train, "epochs": len(self.hist),
                "loss_first": round(self.hist[0], 5), "loss_last": round(self.hist[-1], 5),
+               "time_loss_first": round(self.thist[0], 5),
+               "time_loss_last": round(self.thist[-1], 5),
+               "time_rmse_log2": {
+                   "network": round(float(np.sqrt(np.mean(
+                       (pt.cpu().numpy().astype(np.float64)[okr] - lt) ** 2))), 4),
+                   "batch_wide_rate": round(float(np.sqrt(np.mean((uni - lt) ** 2))), 4)},
                "train_s": round(self.train_s, 2), "heldout_chunks": cb.M,
                "heldout_bytes": cb.raw_bytes, "messages": len(self.xs), "links": {}}
         # plain per-message form: one zc_compress + one zc_decompress per whole message, L = 32
@@ -598,16 +628,21 @@ class SelectorRow:
             rec = {"plain_per_message": {
                 "device_ms": round(plain_ms, 3), "bytes": plain_bytes,
                 "e2e_gbs": round(raw / (plain_ms * 1e6 + plain_bytes / link), 3)}}
-            for name, mlp in (("batched_heuristic", None), ("batched_learned", self.mlp)):
-                ms = timed(lambda: (cb.run_selected(cfg, mlp), cb.dec.run(st)))
+            for name, mlp, tmlp in (("batched_heuristic", None, None),
+                                    ("batched_learned_bits_only", self.mlp, None),
+                                    ("batched_learned", self.mlp, self.tmlp)):
+                ms = timed(lambda: (cb.run_selected(cfg, mlp, tmlp), cb.dec.run(st)))
                 choice = cb.choice.cpu().numpy().copy()
                 counts = cb.counts.cpu().numpy()
                 ev_ = S.evaluate(choice, cb.n, cb.es, bits, cfg)
+                evr = S.evaluate(choice, cb.n, cb.es, bits, cfg, rates=hrates)
                 packed = int(cb.batch.msg_off[-1].item())
                 rec[name] = {"device_ms": round(ms, 3), "bytes": packed,
                              "e2e_gbs": round(raw / (ms * 1e6 + packed / link), 3),
                              "mispredict": round(ev_["mispredict"], 4),
                              "regret": round(ev_["regret"], 5),
+                             "mispredict_measured_rates": round(evr["mispredict"], 4),
+                             "regret_measured_rates": round(evr["regret"], 5),
                              "raw_frac": round(ev_["raw_frac"], 4),
                              "fallbacks": int(counts[0]) if mlp is not None else None,
                              "blocks": {str(b): int((choice == b).sum())
@@ -618,7 +653,7 @@ class SelectorRow:
             out["links"][str(link)] = rec
         out["breakdown_ms"] = self.breakdown(self.cfg[self.LINK_GBS])
         # leave the plan as the graph expects it
-        cb.run_selected(self.cfg[self.LINK_GBS], self.mlp)
+        cb.run_selected(self.cfg[self.LINK_GBS], self.mlp, self.tmlp)
         st.synchronize()
         del outs, decs
         return out

@@ -396,7 +396,9 @@ int zc_batch_chunk_stats(const zc_batch* plan, float* d_feat, zc_stream_t s);
 
 /* MLP forward: y[b] = W3 relu(W2 relu(W1 x'[b] + b1) + b2) + b3 with
  * x' = (x - mu) * inv_sd, d_norm = {mu[16], inv_sd[16]}; d_x[B][16] ->
- * d_y[B][4] (predicted log2 bits per element at L = 16 .. 128). */
+ * d_y[B][4] (the four outputs: predicted log2 bits per element at L = 16 ..
+ * 128 for the bits network, predicted log2 codec ns per input byte at L = 16
+ * .. 128 for a time network of the same shape; the kernel is the same). */
 int zc_mlp_forward(const float* d_params, const float* d_norm, const float* d_x, int B,
                    float* d_y, zc_stream_t s);
 
@@ -420,12 +422,15 @@ int zc_mlp_sgd(float* d_params, float* d_vel, const float* d_grad, float lr, flo
  * coded at L_k with b bits per element, n s ns_per_byte[k] + (n b / 8) /
  * link_gbs ns, and raw, n s raw_ns_per_byte + (32 + n s) / link_gbs ns
  * (ns_per_byte: measured codec time, compression plus decompression, per
- * input byte; link_gbs in GB/s = bytes per ns). */
+ * input byte; link_gbs in GB/s = bytes per ns).  With a time prediction
+ * (zc_batch_select_timed) the message's own predicted ns per input byte
+ * takes the place of ns_per_byte[k]. */
 typedef struct {
     float link_gbs;
     float ns_per_byte[4];
     float raw_ns_per_byte;
     float judge_log2;        /* largest accepted |prediction - log2 estimate| */
+    float judge_time_log2;   /* largest accepted |time prediction - log2 ns_per_byte[k]| */
 } zc_select_cfg;
 
 /* Choose every message's storage and write it into the plan's table (the
@@ -440,6 +445,22 @@ typedef struct {
  * messages. */
 int zc_batch_select(const zc_batch* plan, const float* d_feat, const float* d_pred,
                     const zc_select_cfg* cfg, int* d_choice, unsigned* d_counts, zc_stream_t s);
+
+/* zc_batch_select with a second network's output as well: d_pred_time
+ * [n_msgs][4] (zc_mlp_forward of a network trained on the codec's measured
+ * times) holds the predicted log2 of the codec's ns per input byte
+ * (compression plus decompression) of each message at L = 16 .. 128.  A
+ * message's coded cost at L_k then uses 2^pred_time[k] in place of
+ * cfg->ns_per_byte[k] -- unless that prediction is not finite or lies more
+ * than cfg->judge_time_log2 from log2 ns_per_byte[k] (the measured batch-wide
+ * rate judges it), where the batch-wide rate is kept.  The raw cost and the
+ * bits side are as in zc_batch_select; d_pred_time == NULL is exactly
+ * zc_batch_select.  The paper picks no per-chunk configuration (Sec. 3.2.2
+ * measures that the codec's time depends on the message; Sec. 3.3.3 weighs
+ * it against link time); this prediction is an addition to its method. */
+int zc_batch_select_timed(const zc_batch* plan, const float* d_feat, const float* d_pred,
+                          const float* d_pred_time, const zc_select_cfg* cfg, int* d_choice,
+                          unsigned* d_counts, zc_stream_t s);
 
 /* ---- CUDA graphs of zc calls ----------------------------------------------
  * Every zc launch function is asynchronous and reads nothing back, so a

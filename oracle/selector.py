@@ -12,11 +12,15 @@ compression step costs depends on the message, and Sec. 3.3.3 weighs the
 compression cost of a collective against what it saves on the link.  The
 selector makes that trade per 64 KiB chunk: 16 cheap statistics of a sample
 of the chunk feed a 16-64-64-4 MLP that predicts, for each block size
-L in {16, 32, 64, 128}, the log2 of the stream's bits per element; a cost
-model turns predictions into a choice of L or of sending the chunk raw.  The
+L in {16, 32, 64, 128}, the log2 of the stream's bits per element, and a
+second network of the same shape (a time network) may predict the log2 of
+the codec's ns per input byte at each L; a cost model turns predictions into
+a choice of L or of sending the chunk raw.  The
 fixed heuristic (L = 32, raw when the sampled estimate does not pay) is the
 fallback, and it judges the network: a prediction too far from the sampled
-estimate of the chosen L is discarded in favour of the heuristic.
+estimate of the chosen L is discarded in favour of the heuristic.  The
+measured batch-wide codec rate judges the time network the same way: a
+predicted rate too far from it is replaced by it.
 
 Definitions (the CUDA kernels implement the same ones):
 
@@ -220,16 +224,32 @@ def sgd_step(p, v, g, lr: float, momentum: float):
 
 # ---- selection ---------------------------------------------------------------------
 
-def chunk_costs(n: int, es: int, bits, cfg: dict):
+def chunk_costs(n: int, es: int, bits, cfg: dict, rates=None):
     """Modelled end-to-end cost in ns of sending an n-element chunk coded at
     each L with `bits` bits per element, and raw: codec time (measured ns per
-    input byte, compression plus decompression) plus the bytes over a link of
+    input byte, compression plus decompression: cfg['ns_per_byte'][k], or
+    this chunk's own rates[k] when given) plus the bytes over a link of
     cfg['link_gbs'] GB/s (bytes per ns)."""
     bytes_in = n * es
     link = cfg["link_gbs"]
-    coded = [bytes_in * cfg["ns_per_byte"][k] + n * bits[k] / 8.0 / link for k in range(4)]
+    rate = cfg["ns_per_byte"] if rates is None else rates
+    coded = [bytes_in * rate[k] + n * bits[k] / 8.0 / link for k in range(4)]
     raw = bytes_in * cfg["raw_ns_per_byte"] + (32.0 + bytes_in) / link
     return coded, raw
+
+
+def judged_rates(yt, cfg: dict):
+    """The codec rates a time prediction yt (log2 ns per input byte at each L)
+    stands for: 2^yt[k] where yt[k] is finite and within
+    cfg['judge_time_log2'] of log2 cfg['ns_per_byte'][k], else the measured
+    batch-wide rate cfg['ns_per_byte'][k] (the judge of the time network)."""
+    out = []
+    for k in range(4):
+        c = cfg["ns_per_byte"][k]
+        t = float(yt[k])
+        ok = math.isfinite(t) and abs(t - math.log2(c)) <= cfg["judge_time_log2"]
+        out.append(2.0 ** t if ok else c)
+    return out
 
 
 def heuristic_choice(n: int, es: int, f: np.ndarray, cfg: dict) -> int:
@@ -240,15 +260,17 @@ def heuristic_choice(n: int, es: int, f: np.ndarray, cfg: dict) -> int:
     return 32 if coded[1] < raw else 0
 
 
-def mlp_choice(n: int, es: int, f: np.ndarray, y: np.ndarray, cfg: dict):
+def mlp_choice(n: int, es: int, f: np.ndarray, y: np.ndarray, cfg: dict, yt=None):
     """(choice, fell_back): the L minimising the modelled cost with bits
     2^y_k, raw (0) when that is cheaper, or the heuristic's choice when a
     prediction is not finite or the chosen L's prediction is more than
-    cfg['judge_log2'] away from log2 of the sampled estimate."""
+    cfg['judge_log2'] away from log2 of the sampled estimate.  With a time
+    prediction yt the codec rates are judged_rates(yt, cfg)."""
     if not (np.all(np.isfinite(y)) and np.all(np.isfinite(f[:4]))):
         return heuristic_choice(n, es, f, cfg), True
     bits = [2.0 ** float(v) for v in y]
-    coded, raw = chunk_costs(n, es, bits, cfg)
+    rates = None if yt is None else judged_rates(yt, cfg)
+    coded, raw = chunk_costs(n, es, bits, cfg, rates)
     k = int(np.argmin(coded))
     if abs(float(y[k]) - math.log2(f[k])) > cfg["judge_log2"]:
         return heuristic_choice(n, es, f, cfg), True

@@ -25,27 +25,44 @@ __device__ __forceinline__ void acc_one(Acc& a, float v)
 }
 
 template <typename TX>
+__device__ __forceinline__ void acc_vec(Acc& a, const uint4 v)
+{
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (sizeof(TX) == 4) {
+            acc_one(a, __uint_as_float(w[k]));
+        } else {
+            acc_one(a, __uint_as_float(w[k] << 16));
+            acc_one(a, __uint_as_float(w[k] & 0xffff0000u));
+        }
+    }
+}
+
+// A thread's grid-strided share of one segment: four independent 16-byte
+// loads in flight per thread (the read-only pass is bound by the bytes in
+// flight per SM), then the scalar tail.  The pass runs from the end of the
+// segment to its start, so the compressor, which reads it from the start
+// next, finds its first lines still in L2.
+template <typename TX>
 __device__ __forceinline__ void range_seg(Acc& a, const void* p, unsigned long long n,
                                           unsigned long long gtid, unsigned long long gstride)
 {
     constexpr int VEC = 16 / sizeof(TX);
+    constexpr int UNR = 4;
     unsigned long long nvec = 0;
     if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
         nvec = n / VEC;
-        const uint4* v4 = (const uint4*)p;
-        for (unsigned long long i = gtid; i < nvec; i += gstride) {
-            const uint4 v = __ldg(v4 + i);
-            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        const uint4* top = (const uint4*)p + (nvec ? nvec - 1 : 0);  // vector i is top[-i]
+        unsigned long long i = gtid;
+        for (; i + (UNR - 1) * gstride < nvec; i += UNR * gstride) {
+            uint4 v[UNR];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (sizeof(TX) == 4) {
-                    acc_one(a, __uint_as_float(w[k]));
-                } else {
-                    acc_one(a, __uint_as_float(w[k] << 16));
-                    acc_one(a, __uint_as_float(w[k] & 0xffff0000u));
-                }
-            }
+            for (int u = 0; u < UNR; ++u) v[u] = __ldg(top - (long long)(i + u * gstride));
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) acc_vec<TX>(a, v[u]);
         }
+        for (; i < nvec; i += gstride) acc_vec<TX>(a, __ldg(top - (long long)i));
     }
     for (unsigned long long i = nvec * VEC + gtid; i < n; i += gstride) {
         const float v = sizeof(TX) == 4 ? __ldg((const float*)p + i)
@@ -171,7 +188,8 @@ __global__ void __launch_bounds__(256) k_range_multi(const RangeLaunch P, const 
     Acc a{FLT_MAX, -FLT_MAX, false};
     const unsigned long long gtid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long gstride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned k = 0; k < P.n_segs; ++k) range_seg<TX>(a, S.ptr[k], S.cnt[k], gtid, gstride);
+    // last segment first, each from its end: the first segment's start is read last
+    for (unsigned k = P.n_segs; k-- > 0;) range_seg<TX>(a, S.ptr[k], S.cnt[k], gtid, gstride);
     range_finish(P, a);
 }
 

@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(256, 4) k_chunk_stats(const Item* items, unsig
 // ---- MLP ------------------------------------------------------------------------------
 // Shared memory of an MLP CTA (floats): the parameters with padded row
 // strides (no bank conflicts), the normalised inputs, both layers'
-// pre-activations, one 64 x 64 gradient buffer and the outputs.
+// activations (after the ReLU), one 64 x 64 gradient buffer and the outputs.
 struct MlpSmem {
     float W1[NH][NI + 1], b1[NH];
     float W2[NH][NH + 1], b2[NH];
@@ -301,9 +301,8 @@ struct MlpSmem {
 
 __device__ __forceinline__ float relu(float v) { return v > 0.0f ? v : 0.0f; }
 
-// Loads the parameters and the tile's rows (normalised); rows past B are zero.
-__device__ __forceinline__ void mlp_load(MlpSmem& sm, const float* P, const float* norm,
-                                         const float* X, const int* idx, int B, int row0)
+// Loads the parameters into shared memory (no barrier).
+__device__ __forceinline__ void mlp_load_params(MlpSmem& sm, const float* P)
 {
     const int t = threadIdx.x;
     for (int p = t; p < NH * NI; p += MT) sm.W1[p / NI][p % NI] = P[p];
@@ -314,6 +313,14 @@ __device__ __forceinline__ void mlp_load(MlpSmem& sm, const float* P, const floa
         sm.b2[t] = P[OFF_B2 + t];
     }
     if (t < NO) sm.b3[t] = P[OFF_B3 + t];
+}
+
+// Loads the tile's rows (normalised) into shared memory; rows past B are
+// zero (no barrier).
+__device__ __forceinline__ void mlp_load_rows(MlpSmem& sm, const float* norm, const float* X,
+                                              const int* idx, int B, int row0)
+{
+    const int t = threadIdx.x;
     for (int p = t; p < TB * NI; p += MT) {
         const int s = p / NI, k = p % NI, r = row0 + s;
         float v = 0.0f;
@@ -323,10 +330,21 @@ __device__ __forceinline__ void mlp_load(MlpSmem& sm, const float* P, const floa
         }
         sm.X[s][k] = v;
     }
+}
+
+// Loads the parameters and the tile's rows.
+__device__ __forceinline__ void mlp_load(MlpSmem& sm, const float* P, const float* norm,
+                                         const float* X, const int* idx, int B, int row0)
+{
+    mlp_load_params(sm, P);
+    mlp_load_rows(sm, norm, X, idx, B, row0);
     __syncthreads();
 }
 
-// A1 = X W1^T + b1, A2 = relu(A1) W2^T + b2, Y = relu(A2) W3^T + b3.
+// H1 = relu(X W1^T + b1), H2 = relu(H1 W2^T + b2), Y = H2 W3^T + b3, each
+// sum accumulated by FMAs in input order.  sm.A1 and sm.A2 hold the
+// activations after the ReLU: the gradient's ReLU derivative only asks
+// whether the pre-activation was positive, which H > 0 answers alike.
 __device__ __forceinline__ void mlp_forward_tile(MlpSmem& sm)
 {
     const int t = threadIdx.x, j = t & (NH - 1), g = t >> 6;
@@ -338,8 +356,8 @@ __device__ __forceinline__ void mlp_forward_tile(MlpSmem& sm)
             const int s = g * (TB / 4) + i;
             float a = sm.b1[j];
 #pragma unroll
-            for (int k = 0; k < NI; ++k) a = __fadd_rn(a, __fmul_rn(w[k], sm.X[s][k]));
-            sm.A1[s][j] = a;
+            for (int k = 0; k < NI; ++k) a = __fmaf_rn(w[k], sm.X[s][k], a);
+            sm.A1[s][j] = relu(a);
         }
     }
     __syncthreads();
@@ -347,35 +365,45 @@ __device__ __forceinline__ void mlp_forward_tile(MlpSmem& sm)
         float acc[TB / 4];
 #pragma unroll
         for (int i = 0; i < TB / 4; ++i) acc[i] = sm.b2[j];
+#pragma unroll 4
         for (int k = 0; k < NH; ++k) {
             const float w = sm.W2[j][k];
 #pragma unroll
             for (int i = 0; i < TB / 4; ++i)
-                acc[i] = __fadd_rn(acc[i], __fmul_rn(w, relu(sm.A1[g * (TB / 4) + i][k])));
+                acc[i] = __fmaf_rn(w, sm.A1[g * (TB / 4) + i][k], acc[i]);
         }
 #pragma unroll
-        for (int i = 0; i < TB / 4; ++i) sm.A2[g * (TB / 4) + i][j] = acc[i];
+        for (int i = 0; i < TB / 4; ++i) sm.A2[g * (TB / 4) + i][j] = relu(acc[i]);
     }
     __syncthreads();
     {
         const int s = t >> 2, o = t & 3;
         float y = sm.b3[o];
-        for (int k = 0; k < NH; ++k) y = __fadd_rn(y, __fmul_rn(sm.W3[o][k], relu(sm.A2[s][k])));
+#pragma unroll 8
+        for (int k = 0; k < NH; ++k) y = __fmaf_rn(sm.W3[o][k], sm.A2[s][k], y);
         sm.Y[s][o] = y;
     }
     __syncthreads();
 }
 
+// Persistent over row tiles: the parameters are loaded once per CTA, then
+// the CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ... (every row's
+// arithmetic is the same as with one tile per CTA).
 __global__ void __launch_bounds__(MT) k_mlp_forward(const float* P, const float* norm,
                                                     const float* X, int B, float* Yout)
 {
     extern __shared__ __align__(16) uint8_t raw[];
     MlpSmem& sm = *reinterpret_cast<MlpSmem*>(raw);
-    const int row0 = blockIdx.x * TB;
-    mlp_load(sm, P, norm, X, nullptr, B, row0);
-    mlp_forward_tile(sm);
-    const int t = threadIdx.x, s = t >> 2, o = t & 3;
-    if (row0 + s < B) Yout[(long long)(row0 + s) * NO + o] = sm.Y[s][o];
+    const int ntiles = (B + TB - 1) / TB;
+    mlp_load_params(sm, P);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int row0 = tile * TB;
+        mlp_load_rows(sm, norm, X, nullptr, B, row0);
+        __syncthreads();
+        mlp_forward_tile(sm);  // ends with a barrier: sm.Y is complete
+        const int t = threadIdx.x, s = t >> 2, o = t & 3;
+        if (row0 + s < B) Yout[(long long)(row0 + s) * NO + o] = sm.Y[s][o];
+    }
 }
 
 // Per-CTA partial gradient of sum((Y - T)^2) / (B * NO) over its rows, and
@@ -414,11 +442,11 @@ __global__ void __launch_bounds__(MT) k_mlp_grad(const float* P, const float* no
         for (int w = 0; w < MT / 32; ++w) l = __fadd_rn(l, sm.red[w]);
         G[NPARAM] = l;
     }
-    // dW3[o][k] = sum_s dY[s][o] relu(A2[s][k]); db3
+    // dW3[o][k] = sum_s dY[s][o] H2[s][k]; db3
     {
         const int o = t >> 6, k = t & 63;
         float acc = 0.0f;
-        for (int s = 0; s < TB; ++s) acc = __fadd_rn(acc, __fmul_rn(sm.Y[s][o], relu(sm.A2[s][k])));
+        for (int s = 0; s < TB; ++s) acc = __fadd_rn(acc, __fmul_rn(sm.Y[s][o], sm.A2[s][k]));
         G[OFF_W3 + o * NH + k] = acc;
         if (t < NO) {
             float b = 0.0f;
@@ -426,7 +454,7 @@ __global__ void __launch_bounds__(MT) k_mlp_grad(const float* P, const float* no
             G[OFF_B3 + t] = b;
         }
     }
-    // dA2[s][j] = (sum_o dY[s][o] W3[o][j]) [A2 > 0]
+    // dA2[s][j] = (sum_o dY[s][o] W3[o][j]) [H2 > 0]
     for (int i = 0; i < TB / 4; ++i) {
         const int s = g * (TB / 4) + i;
         float a = 0.0f;
@@ -435,7 +463,7 @@ __global__ void __launch_bounds__(MT) k_mlp_grad(const float* P, const float* no
         sm.D[s][j] = sm.A2[s][j] > 0.0f ? a : 0.0f;
     }
     __syncthreads();
-    // dW2[j][k] = sum_s dA2[s][j] relu(A1[s][k]) for k in this thread's 16; db2
+    // dW2[j][k] = sum_s dA2[s][j] H1[s][k] for k in this thread's 16; db2
     {
         float acc[NH / 4];
 #pragma unroll
@@ -446,13 +474,13 @@ __global__ void __launch_bounds__(MT) k_mlp_grad(const float* P, const float* no
             b = __fadd_rn(b, a);
 #pragma unroll
             for (int kk = 0; kk < NH / 4; ++kk)
-                acc[kk] = __fadd_rn(acc[kk], __fmul_rn(a, relu(sm.A1[s][g * (NH / 4) + kk])));
+                acc[kk] = __fadd_rn(acc[kk], __fmul_rn(a, sm.A1[s][g * (NH / 4) + kk]));
         }
 #pragma unroll
         for (int kk = 0; kk < NH / 4; ++kk) G[OFF_W2 + j * NH + g * (NH / 4) + kk] = acc[kk];
         if (g == 0) G[OFF_B2 + j] = b;
     }
-    // dA1[s][k] = (sum_j dA2[s][j] W2[j][k]) [A1 > 0], into A2's storage (k = this thread's j)
+    // dA1[s][k] = (sum_j dA2[s][j] W2[j][k]) [H1 > 0], into A2's storage (k = this thread's j)
     {
         float acc[TB / 4];
 #pragma unroll
@@ -513,11 +541,14 @@ __global__ void k_mlp_sgd(float* P, float* V, const float* G, float lr, float mo
 
 // ---- selection: one thread per item -------------------------------------------------
 struct SelectArgs {
-    float link, c[4], c_raw, judge;
+    float link, c[4], c_raw, judge, judge_time;
 };
 
+// With `pred_time`, a message's coded cost at L_k takes its own predicted ns
+// per input byte, 2^pred_time[k], where that prediction is finite and within
+// judge_time (log2) of the batch-wide rate c[k]; elsewhere c[k] stays.
 __global__ void k_select(Item* items, unsigned n_items, const float* feat, const float* pred,
-                         SelectArgs a, int* choice, unsigned* counts)
+                         const float* pred_time, SelectArgs a, int* choice, unsigned* counts)
 {
     const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_items) return;
@@ -544,7 +575,13 @@ __global__ void k_select(Item* items, unsigned n_items, const float* feat, const
             float best = 0.0f;
             for (int k = 0; k < 4; ++k) {
                 const float bits = exp2f(y[k]);
-                const float ck = __fadd_rn(__fmul_rn(bytes_in, a.c[k]),
+                float rate = a.c[k];
+                if (pred_time != nullptr) {
+                    const float t = pred_time[(size_t)i * NO + k];
+                    if (isfinite(t) && fabsf(__fsub_rn(t, log2f(a.c[k]))) <= a.judge_time)
+                        rate = exp2f(t);
+                }
+                const float ck = __fadd_rn(__fmul_rn(bytes_in, rate),
                                            __fdiv_rn(__fdiv_rn(__fmul_rn(nf, bits), 8.0f), a.link));
                 if (k == 0 || ck < best) {
                     best = ck;
@@ -596,8 +633,14 @@ int zc_mlp_forward(const float* d_params, const float* d_norm, const float* d_x,
         return ZC_ERR_ARG;
     if (B == 0) return ZC_OK;
     if (mlp_prepare() != cudaSuccess) return ZC_ERR_CUDA;
-    k_mlp_forward<<<(B + TB - 1) / TB, MT, sizeof(MlpSmem), (cudaStream_t)s>>>(d_params, d_norm,
-                                                                               d_x, B, d_y);
+    // two CTAs per SM fit (shared memory), each looping over row tiles
+    int dev = 0, n_sm = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return ZC_ERR_CUDA;
+    const int ntiles = (B + TB - 1) / TB;
+    const int grid = ntiles < 2 * n_sm ? ntiles : 2 * n_sm;
+    k_mlp_forward<<<grid, MT, sizeof(MlpSmem), (cudaStream_t)s>>>(d_params, d_norm, d_x, B, d_y);
     return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
 }
 
@@ -634,24 +677,34 @@ int zc_mlp_sgd(float* d_params, float* d_vel, const float* d_grad, float lr, flo
     return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
 }
 
-int zc_batch_select(const zc_batch* plan, const float* d_feat, const float* d_pred,
-                    const zc_select_cfg* cfg, int* d_choice, unsigned* d_counts, zc_stream_t s)
+int zc_batch_select_timed(const zc_batch* plan, const float* d_feat, const float* d_pred,
+                          const float* d_pred_time, const zc_select_cfg* cfg, int* d_choice,
+                          unsigned* d_counts, zc_stream_t s)
 {
     if (plan == nullptr || plan->d_table == nullptr || plan->n_msgs < 1 || plan->decompress != 0 ||
         d_feat == nullptr || cfg == nullptr || !(cfg->link_gbs > 0.0f) || !(cfg->judge_log2 >= 0.0f))
+        return ZC_ERR_ARG;
+    if (d_pred_time != nullptr && (d_pred == nullptr || !(cfg->judge_time_log2 >= 0.0f)))
         return ZC_ERR_ARG;
     SelectArgs a;
     a.link = cfg->link_gbs;
     for (int k = 0; k < 4; ++k) a.c[k] = cfg->ns_per_byte[k];
     a.c_raw = cfg->raw_ns_per_byte;
     a.judge = cfg->judge_log2;
+    a.judge_time = d_pred_time != nullptr ? cfg->judge_time_log2 : 0.0f;
     if (d_counts != nullptr &&
         cudaMemsetAsync(d_counts, 0, 2 * sizeof(unsigned), (cudaStream_t)s) != cudaSuccess)
         return ZC_ERR_CUDA;
     const unsigned n = (unsigned)plan->n_msgs;
     k_select<<<(n + 255) / 256, 256, 0, (cudaStream_t)s>>>((Item*)plan->d_table, n, d_feat, d_pred,
-                                                           a, d_choice, d_counts);
+                                                           d_pred_time, a, d_choice, d_counts);
     return cudaGetLastError() == cudaSuccess ? ZC_OK : ZC_ERR_CUDA;
+}
+
+int zc_batch_select(const zc_batch* plan, const float* d_feat, const float* d_pred,
+                    const zc_select_cfg* cfg, int* d_choice, unsigned* d_counts, zc_stream_t s)
+{
+    return zc_batch_select_timed(plan, d_feat, d_pred, nullptr, cfg, d_choice, d_counts, s);
 }
 
 }  // extern "C"

@@ -10,7 +10,12 @@ block size L in {16, 32, 64, 128} or raw storage.  Its network predicts the
 log2 bits per element of each L from 16 sampled statistics; the fixed
 heuristic (L = 32, raw when the sampled estimate says coding does not pay) is
 both its fallback and its judge.  Labels come from the codec itself: every
-training chunk is compressed at every L and its stream lengths are read.
+training chunk is compressed at every L and its stream lengths are read.  A
+second network of the same shape predicts the codec's time: the log2 of its
+ns per input byte (compression plus decompression) at each L, labelled by
+timing the codec on groups of similar training chunks (one input type, close
+stream sizes), each group as one batch at every L; the measured batch-wide
+rate judges it.
 """
 from __future__ import annotations
 
@@ -135,6 +140,7 @@ class ChunkBatch:
                                       stream=stream, grouped=True)
         self.feat = torch.empty((self.M, zc.N_STATS), dtype=torch.float32, device=dev)
         self.pred = torch.empty((self.M, 4), dtype=torch.float32, device=dev)
+        self.pred_time = torch.empty((self.M, 4), dtype=torch.float32, device=dev)
         self.choice = torch.zeros(self.M, dtype=torch.int32, device=dev)
         self.counts = torch.zeros(2, dtype=torch.int32, device=dev)
 
@@ -202,7 +208,8 @@ class ChunkBatch:
         ts = ts[1:]
         return (float(np.median([t[0] for t in ts])), float(np.median([t[1] for t in ts])))
 
-    def cost_model(self, link_gbs: float, judge_log2: float = 1.0, reps: int = 5):
+    def cost_model(self, link_gbs: float, judge_log2: float = 1.0, reps: int = 5,
+                   judge_time_log2: float = 2.0):
         """The codec's time per input byte at each choice, measured on this
         batch (compression + decompression, CUDA events), as a zc_select_cfg:
         every block size timed on a plan that uses it throughout, raw storage
@@ -213,6 +220,7 @@ class ChunkBatch:
         cfg = zc.ZcSelectCfg()
         cfg.link_gbs = link_gbs
         cfg.judge_log2 = judge_log2
+        cfg.judge_time_log2 = judge_time_log2
         self.uniform_ns_per_byte = []
         for k, L in enumerate(BLOCKS):
             self.set_all(L)
@@ -230,22 +238,84 @@ class ChunkBatch:
         self.set_all(32)
         return cfg
 
-    def run_selected(self, cfg, mlp: "Mlp | None"):
-        """The selector path: statistics, (network,) selection into the
-        plan, batched compression -- all launches on the plan's stream."""
+    def run_selected(self, cfg, mlp: "Mlp | None", tmlp: "Mlp | None" = None):
+        """The selector path: statistics, (networks,) selection into the
+        plan, batched compression -- all launches on the plan's stream.
+        tmlp: the time network (used only with the bits network mlp)."""
         self.stats()
-        pred = None
+        pred = pred_time = None
         if mlp is not None:
             pred = mlp.forward(self.feat, out=self.pred, stream=self.stream)
-        self.select(cfg, pred)
+            if tmlp is not None:
+                pred_time = tmlp.forward(self.feat, out=self.pred_time, stream=self.stream)
+        self.select(cfg, pred, pred_time)
         self.batch.run(self.stream)
 
-    def select(self, cfg, pred: torch.Tensor | None):
-        zc._check(zc.zc_batch_select(self.batch.plan, self.feat.data_ptr(),
-                                     None if pred is None else pred.data_ptr(), cfg,
-                                     self.choice.data_ptr(), self.counts.data_ptr(),
-                                     zc._stream(self.stream)), "zc_batch_select")
+    def select(self, cfg, pred: torch.Tensor | None, pred_time: torch.Tensor | None = None):
+        zc._check(zc.zc_batch_select_timed(self.batch.plan, self.feat.data_ptr(),
+                                           None if pred is None else pred.data_ptr(),
+                                           None if pred_time is None else pred_time.data_ptr(),
+                                           cfg, self.choice.data_ptr(), self.counts.data_ptr(),
+                                           zc._stream(self.stream)), "zc_batch_select_timed")
         return self.choice
+
+
+def _copies(views, stream=None, align: int = 64):
+    """Copies of the views in one fresh buffer, each starting at a multiple
+    of `align` elements (the originals' dtype)."""
+    offs, tot = [], 0
+    for v in views:
+        offs.append(tot)
+        tot += (v.numel() + align - 1) // align * align
+    buf = torch.empty(max(tot, 1), dtype=views[0].dtype, device=views[0].device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    s.wait_stream(torch.cuda.current_stream())
+    out = []
+    with torch.cuda.stream(s):
+        for v, o in zip(views, offs):
+            d = buf[o:o + v.numel()]
+            d.copy_(v.reshape(-1))
+            out.append(d)
+    return out
+
+
+def time_labels(views, ebs, true_bits, groups: int = 16, reps: int = 3, stream=None,
+                min_group: int = 8, min_bytes: int = 256 << 20):
+    """[M, 4] measured codec ns per input byte (compression plus
+    decompression) of every chunk at L = 16 .. 128, and the groups.  The
+    chunks of each input type are sorted by their true bits per element at
+    L = 32 and cut into `groups` runs of about equal count (at least
+    min_group chunks each); every run is compressed and decompressed as one
+    grouped batch at each L (CUDA events, median of reps) and its chunks take
+    the run's rate.  A run is timed repeated until the batch holds at least
+    min_bytes of input, so that every rate is the codec's rate on a full GPU
+    (a small batch would charge its launch and its last partial wave to its
+    few bytes); the copies are distinct memory (no copy is read from L2
+    because an earlier one was).  Returns (rates, group index of every
+    chunk)."""
+    M = len(views)
+    es = np.array([v.element_size() for v in views])
+    rates = np.zeros((M, 4))
+    gid = np.full(M, -1, np.int64)
+    g = 0
+    for e in sorted(set(es.tolist())):
+        idx = np.nonzero(es == e)[0]
+        idx = idx[np.argsort(true_bits[idx, 1], kind="stable")]
+        k = max(1, min(groups, len(idx) // min_group))
+        for part in np.array_split(idx, k):
+            nbytes = int(sum(views[i].numel() for i in part)) * int(e)
+            rep = max(1, -(-min_bytes // max(nbytes, 1)))
+            sel = np.tile(part, rep)
+            gv = _copies([views[i] for i in sel], stream)
+            cb = ChunkBatch(gv, [ebs[i] for i in sel], stream=stream)
+            for j, L in enumerate(BLOCKS):
+                cb.set_all(L)
+                c, d = cb.time_ms(reps)
+                rates[part, j] = (c + d) * 1e6 / cb.raw_bytes
+            gid[part] = g
+            g += 1
+            del cb
+    return rates, gid
 
 
 # ---- the network -----------------------------------------------------------------------
@@ -330,21 +400,24 @@ class Mlp:
 
 # ---- evaluation ----------------------------------------------------------------------
 
-def costs(n, es, bits, cfg):
+def costs(n, es, bits, cfg, rates=None):
     """Modelled ns per chunk: coded at each L with the given bits per element
-    ([M, 4]) and raw ([M])."""
+    ([M, 4]) and raw ([M]); codec time at the batch-wide rates of cfg, or at
+    every chunk's own measured rates ([M, 4] ns per input byte)."""
     bytes_in = n * es
-    c = np.array([cfg.ns_per_byte[k] for k in range(4)])
-    coded = bytes_in[:, None] * c[None, :] + n[:, None] * bits / 8.0 / cfg.link_gbs
+    if rates is None:
+        rates = np.array([cfg.ns_per_byte[k] for k in range(4)])[None, :]
+    coded = bytes_in[:, None] * rates + n[:, None] * bits / 8.0 / cfg.link_gbs
     raw = bytes_in * cfg.raw_ns_per_byte + (32.0 + bytes_in) / cfg.link_gbs
     return coded, raw
 
 
-def evaluate(choice: np.ndarray, n, es, true_bits, cfg) -> dict:
-    """Modelled cost of the choices with the measured sizes, against the best
-    choice per chunk: total ns, regret (total / best total - 1), mispredict
-    rate (chunks whose choice costs more than 0.1 % above their best)."""
-    coded, raw = costs(n, es, true_bits, cfg)
+def evaluate(choice: np.ndarray, n, es, true_bits, cfg, rates=None) -> dict:
+    """Modelled cost of the choices with the measured sizes (and, given,
+    every chunk's measured codec rates), against the best choice per chunk:
+    total ns, regret (total / best total - 1), mispredict rate (chunks whose
+    choice costs more than 0.1 % above their best)."""
+    coded, raw = costs(n, es, true_bits, cfg, rates)
     allc = np.concatenate([coded, raw[:, None]], 1)
     col = np.array([{16: 0, 32: 1, 64: 2, 128: 3, 0: 4}[int(c)] for c in choice])
     got = allc[np.arange(len(col)), col]

@@ -76,7 +76,8 @@ class ZcTunePoint(ctypes.Structure):
 
 class ZcSelectCfg(ctypes.Structure):
     _fields_ = [("link_gbs", ctypes.c_float), ("ns_per_byte", ctypes.c_float * 4),
-                ("raw_ns_per_byte", ctypes.c_float), ("judge_log2", ctypes.c_float)]
+                ("raw_ns_per_byte", ctypes.c_float), ("judge_log2", ctypes.c_float),
+                ("judge_time_log2", ctypes.c_float)]
 
 
 N_STATS = 16
@@ -145,6 +146,8 @@ def _declare(L):
         "zc_mlp_sgd": (i32, [vp, vp, vp, c.c_float, c.c_float, vp]),
         "zc_batch_select": (i32, [c.POINTER(ZcBatch), vp, vp, c.POINTER(ZcSelectCfg), vp, vp,
                                   vp]),
+        "zc_batch_select_timed": (i32, [c.POINTER(ZcBatch), vp, vp, vp, c.POINTER(ZcSelectCfg),
+                                        vp, vp, vp]),
         "zc_graph_begin": (i32, [vp]),
         "zc_graph_end": (i32, [vp, c.POINTER(vp)]),
         "zc_graph_launch": (i32, [vp, vp]),
@@ -172,6 +175,7 @@ def exported_names():
             "zc_decompress_batch", "zc_batch_set_grouped", "zc_plan_decompress_streams",
             "zc_autotune_batch", "zc_batch_chunk_stats", "zc_mlp_forward",
             "zc_mlp_scratch_bytes", "zc_mlp_grad", "zc_mlp_sgd", "zc_batch_select",
+            "zc_batch_select_timed",
             "zc_graph_begin", "zc_graph_end",
             "zc_graph_launch", "zc_graph_destroy",
             "zc_get_device_status", "zc_clear_device_status", "zc_set_wait_limit_ns",
@@ -347,6 +351,12 @@ def zc_mlp_sgd(d_params, d_vel, d_grad, lr, momentum, stream) -> int:
 def zc_batch_select(plan, d_feat, d_pred, cfg, d_choice, d_counts, stream) -> int:
     return lib().zc_batch_select(ctypes.byref(plan), d_feat, d_pred, ctypes.byref(cfg), d_choice,
                                  d_counts, stream)
+
+
+def zc_batch_select_timed(plan, d_feat, d_pred, d_pred_time, cfg, d_choice, d_counts,
+                          stream) -> int:
+    return lib().zc_batch_select_timed(ctypes.byref(plan), d_feat, d_pred, d_pred_time,
+                                       ctypes.byref(cfg), d_choice, d_counts, stream)
 
 
 def zc_graph_begin(stream) -> int:

@@ -151,6 +151,15 @@ def test_selector_and_status_arguments(zc):
     cfg = zc.ZcSelectCfg()
     cfg.link_gbs, cfg.judge_log2 = 12.5, 1.0
     assert zc.zc_batch_select(empty, FAKE, FAKE, cfg, FAKE, None, None) == zc.ERR_ARG
+    assert zc.zc_batch_select_timed(empty, FAKE, FAKE, FAKE, cfg, FAKE, None, None) == zc.ERR_ARG
+    fake_plan = zc.ZcBatch()
+    fake_plan.n_msgs, fake_plan.d_table = 1, FAKE
+    # a time prediction needs a bits prediction and a judge of its own
+    assert zc.zc_batch_select_timed(fake_plan, FAKE, None, FAKE, cfg, FAKE, None,
+                                    None) == zc.ERR_ARG
+    cfg.judge_time_log2 = -1.0
+    assert zc.zc_batch_select_timed(fake_plan, FAKE, FAKE, FAKE, cfg, FAKE, None,
+                                    None) == zc.ERR_ARG
     assert zc.zc_decompress_batch(empty, FAKE, BIG_WS, None) == zc.ERR_ARG
     assert zc.zc_compress_batch(empty, FAKE, BIG_WS, None) == zc.ERR_ARG
     assert zc.zc_graph_launch(None, None) == zc.ERR_ARG

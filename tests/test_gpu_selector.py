@@ -88,7 +88,7 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("B", [1, 63, 64, 200])
+@pytest.mark.parametrize("B", [1, 63, 64, 200, 50001])  # 50001: CTAs loop over row tiles
 def test_mlp_forward_matches_oracle(zc, B):
     p, norm, X, T = _mlp_problem(B, B)
     y = torch.empty((B, 4), device="cuda")
@@ -190,6 +190,87 @@ def test_selection_matches_oracle(zc):
             assert h["flags"] == 1
         else:
             assert h["flags"] == 0 and 1 << h["log2L"] == got[i]
+
+
+def test_timed_selection_matches_oracle(zc):
+    """zc_batch_select_timed against the oracle's choice with a time
+    prediction: per-chunk rates judged against the batch-wide ones."""
+    r = np.random.default_rng(13)
+    M = 3000
+    sizes = r.integers(1, 16385, M)
+    xs = [torch.zeros(int(n), dtype=torch.float32 if i % 3 else torch.bfloat16, device="cuda")
+          for i, n in enumerate(sizes)]
+    b = zc.BatchCompress(xs, [32] * M, [1e-3] * M)
+    f = np.abs(r.normal(8, 6, (M, 16))).astype(np.float32) + 0.5
+    y = (np.log2(f[:, :4]) + r.normal(0, 0.3, (M, 4))).astype(np.float32)
+    rates = [0.03, 0.02, 0.018, 0.017]
+    judge_t = 1.5
+    yt = (np.log2(rates)[None, :] + r.normal(0, 1.2, (M, 4))).astype(np.float32)
+    # keep every time prediction clear of the judge's threshold (FP32 vs FP64)
+    edge = np.abs(np.abs(yt.astype(np.float64) - np.log2(rates)[None, :]) - judge_t) < 1e-3
+    yt[edge] += np.float32(0.01)
+    yt[r.random(M) < 0.01, 1] = np.nan
+    cfg = zc.ZcSelectCfg()
+    cfg.link_gbs, cfg.raw_ns_per_byte, cfg.judge_log2, cfg.judge_time_log2 = 100.0, 0.004, 1.0, judge_t
+    for k, c in enumerate(rates):
+        cfg.ns_per_byte[k] = c
+    ocfg = {"link_gbs": 100.0, "ns_per_byte": rates, "raw_ns_per_byte": 0.004,
+            "judge_log2": 1.0, "judge_time_log2": judge_t}
+    dF, dY, dT = _dev(f), _dev(y), _dev(yt)
+    choice = torch.zeros(M, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+    assert zc.zc_batch_select_timed(b.plan, dF.data_ptr(), dY.data_ptr(), dT.data_ptr(), cfg,
+                                    choice.data_ptr(), None, s) == 0
+    got = choice.cpu().numpy()
+    changed = 0
+    for i in range(M):
+        n, es = int(sizes[i]), (4 if i % 3 else 2)
+        want, _ = OS.mlp_choice(n, es, f[i].astype(np.float64), y[i].astype(np.float64), ocfg,
+                                yt[i].astype(np.float64))
+        plain, _ = OS.mlp_choice(n, es, f[i].astype(np.float64), y[i].astype(np.float64), ocfg)
+        changed += want != plain
+        if got[i] != want:
+            coded, raw = OS.chunk_costs(n, es, [2.0 ** float(v) for v in y[i]], ocfg,
+                                        OS.judged_rates(yt[i].astype(np.float64), ocfg))
+            allc = dict(zip((16, 32, 64, 128, 0), coded + [raw]))
+            assert abs(allc[int(got[i])] - allc[want]) <= 1e-5 * allc[want], (i, got[i], want)
+    assert changed > M // 10  # the time prediction really moves choices
+    # no time prediction: exactly zc_batch_select
+    c2 = torch.zeros_like(choice)
+    assert zc.zc_batch_select_timed(b.plan, dF.data_ptr(), dY.data_ptr(), None, cfg,
+                                    c2.data_ptr(), None, s) == 0
+    assert zc.zc_batch_select(b.plan, dF.data_ptr(), dY.data_ptr(), cfg, choice.data_ptr(),
+                              None, s) == 0
+    assert torch.equal(choice, c2)
+
+
+def test_time_network_predicts_the_codec_rate_on_held_out_chunks(zc):
+    """The time network, trained on rates the codec measured on groups of
+    training chunks, predicts held-out groups' measured rates better than
+    the batch-wide rate at each L does."""
+    from paper_2308_05199_gb300 import selector as S
+    train_v, train_e, _ = S.mixed_chunks(3000, seed=1, scale=64)
+    test_v, test_e, _ = S.mixed_chunks(1600, seed=2, scale=64)
+    tr = S.ChunkBatch(train_v, train_e)
+    te = S.ChunkBatch(test_v, test_e)
+    cfg = tr.cost_model(link_gbs=100.0)
+    X, _, keep, bits = S.dataset(tr)
+    rates, _ = S.time_labels(train_v, train_e, bits, groups=8)
+    T = torch.from_numpy(np.log2(rates[keep]).astype(np.float32)).cuda()
+    tm = S.Mlp(seed=1)
+    tm.set_norm(X)
+    hist = tm.fit(X, T, epochs=40, batch=256, lr=0.02, momentum=0.9, seed=0)
+    assert hist[-1] < 0.5 * hist[0]
+    feat = te.stats().clone()
+    tbits = te.true_bits()
+    trates, _ = S.time_labels(test_v, test_e, tbits, groups=8)
+    ok = torch.isfinite(feat).all(1).cpu().numpy()
+    pt = tm.forward(feat).cpu().numpy().astype(np.float64)
+    want = np.log2(trates)
+    uni = np.log2(np.array([cfg.ns_per_byte[k] for k in range(4)]))[None, :]
+    err_net = np.sqrt(np.mean((pt[ok] - want[ok]) ** 2))
+    err_uni = np.sqrt(np.mean((uni - want[ok]) ** 2))
+    assert err_net < 0.7 * err_uni, (err_net, err_uni)
 
 
 def test_training_beats_the_heuristic_on_held_out_chunks(zc):

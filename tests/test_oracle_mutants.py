@@ -295,6 +295,15 @@ SEL_MUTANTS = {
     # statistics: the level range without its +1
     "range_without_one": [("    f[4] = math.log2(1 + int(allq.max()) - int(allq.min()))",
                            "    f[4] = math.log2(max(int(allq.max()) - int(allq.min()), 1))")],
+    # the time network's rates never judged against the measured ones
+    "time_judge_ignored": [('        ok = math.isfinite(t) and abs(t - math.log2(c)) <= cfg["judge_time_log2"]',
+                            "        ok = math.isfinite(t)")],
+    # a time prediction read as ns per byte instead of its log2
+    "time_not_exponentiated": [("        out.append(2.0 ** t if ok else c)",
+                                "        out.append(t if ok else c)")],
+    # the predicted rates charged to raw storage instead of the coded options
+    "time_rates_ignored": [('    rate = cfg["ns_per_byte"] if rates is None else rates',
+                            '    rate = cfg["ns_per_byte"]')],
     # a raw chunk's header not charged on the link
     "raw_header_free": [('    raw = bytes_in * cfg["raw_ns_per_byte"] + (32.0 + bytes_in) / link',
                          '    raw = bytes_in * cfg["raw_ns_per_byte"] + bytes_in / link')],

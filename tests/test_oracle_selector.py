@@ -222,3 +222,48 @@ def test_best_choice():
     assert coded[1] == pytest.approx(65536 * 0.015 + 16384 * 8 / 8 / 12.5)
     assert raw == pytest.approx(65536 * 0.002 + 65568 / 12.5)
     assert S.best_choice(16384, 4, [40.0] * 4, CFG)[0] == 0
+
+
+# ---- the time network's rates --------------------------------------------------------
+
+TCFG = dict(CFG, judge_time_log2=1.5)
+
+
+def test_timed_choice_with_the_measured_rates_is_the_untimed_choice():
+    r = np.random.default_rng(11)
+    for _ in range(200):
+        f = np.abs(r.normal(8, 5, 16)) + 0.5
+        y = np.log2(f[:4]) + r.normal(0, 0.4, 4)
+        n, es = int(r.integers(1, 16385)), int(r.choice([2, 4]))
+        yt = np.log2(TCFG["ns_per_byte"])
+        assert S.mlp_choice(n, es, f, y, TCFG, yt) == S.mlp_choice(n, es, f, y, TCFG)
+
+
+def test_timed_choice_by_hand():
+    f = np.array([6.0, 5.5, 5.0, 6.0] + [0.0] * 12)
+    y = np.log2([6.2, 5.4, 4.1, 6.5])
+    # link ns: 16384 * bits / 8 / 12.5 = [1015.8, 884.7, 671.7, 1065.0]
+    # rates [0.02, 0.015, 0.028, 0.0065] ns/B on 65536 B: [1310.7, 983.0, 1835.0, 426.0]
+    # totals [2326.5, 1867.8, 2506.7, 1491.0] -> L = 128 (untimed: L = 64)
+    yt = np.log2([0.02, 0.015, 0.028, 0.0065])
+    assert S.mlp_choice(16384, 4, f, y, TCFG, yt) == (128, False)
+    assert S.judged_rates(yt, TCFG) == pytest.approx([0.02, 0.015, 0.028, 0.0065])
+    # a judge of 0.5 (log2) rejects both changed rates: the measured ones stand
+    tight = dict(TCFG, judge_time_log2=0.5)
+    assert S.judged_rates(yt, tight) == pytest.approx(CFG["ns_per_byte"])
+    assert S.mlp_choice(16384, 4, f, y, tight, yt) == (64, False)
+    # a rate that is not finite is replaced by the measured one (L = 128 alone)
+    yt2 = yt.copy()
+    yt2[3] = np.nan
+    assert S.judged_rates(yt2, TCFG)[3] == CFG["ns_per_byte"][3]
+    assert S.mlp_choice(16384, 4, f, y, TCFG, yt2) == (32, False)  # 1867.8 < 2326.5, 2506.7, 1917.0
+
+
+def test_timed_choice_sends_raw_when_the_codec_is_slow():
+    f = np.array([6.0, 5.5, 5.0, 6.0] + [0.0] * 12)
+    y = np.log2([6.2, 5.4, 4.1, 6.5])
+    # every rate 8x the measured one: the cheapest coded cost is L = 64,
+    # 65536 * 0.112 + 671.7 = 8011.8 ns, against raw 131.1 + 5245.4 = 5376.5 ns
+    yt = np.log2(np.array(CFG["ns_per_byte"]) * 8)
+    assert S.mlp_choice(16384, 4, f, y, dict(CFG, judge_time_log2=3.5), yt) == (0, False)
+    assert S.mlp_choice(16384, 4, f, y, dict(CFG, judge_time_log2=2.5), yt) == (64, False)
