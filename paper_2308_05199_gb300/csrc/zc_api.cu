@@ -582,8 +582,16 @@ int zc_reduce_step_batch(const zc_plan* plan, void* d_ws, size_t ws_bytes, zc_st
     P.urows = unit_rows(C);
     if (plan->has_input) {
         P.total_tiles = (unsigned)plan->total_chunks;
+        if (plan->n_items > 1) {
+            // chunk -> item map for the width scan (the tile map below reuses its space)
+            if (launch_tile_map(P.items, P.n_items, P.total_tiles, w.tile_map, (cudaStream_t)s,
+                                true) != cudaSuccess)
+                return ZC_ERR_CUDA;
+            P.tile_map = w.tile_map;
+        }
         if (launch_wscan(P, (unsigned)plan->total_chunks, (cudaStream_t)s) != cudaSuccess)
             return ZC_ERR_CUDA;
+        P.tile_map = nullptr;
     }
     P.total_tiles = (unsigned)plan->total_tiles;
     if (plan->n_items > 1) {
@@ -896,8 +904,16 @@ int zc_decompress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_st
     P.in_cap = plan->packed_cap;
     P.grouped = plan->grouped;
     P.total_tiles = (unsigned)plan->total_chunks;
+    if (plan->n_msgs > 1) {
+        // chunk -> item map for the width scan (the tile map below reuses its space)
+        if (launch_tile_map(P.items, P.n_items, P.total_tiles, w.tile_map, (cudaStream_t)s,
+                            true) != cudaSuccess)
+            return ZC_ERR_CUDA;
+        P.tile_map = w.tile_map;
+    }
     if (launch_wscan(P, (unsigned)plan->total_chunks, (cudaStream_t)s) != cudaSuccess)
         return ZC_ERR_CUDA;
+    P.tile_map = nullptr;
     P.total_tiles = (unsigned)plan->total_tiles;
     if (plan->n_msgs > 1) {
         if (launch_tile_map(P.items, P.n_items, P.total_tiles, w.tile_map, (cudaStream_t)s) !=

@@ -1676,17 +1676,20 @@ __device__ __forceinline__ void resolve_packed(const Launch& P, Item& it, unsign
 
 #ifdef ZC_DECODE_KERNELS  // defined by the one translation unit that launches them
 
-// Item of every encoder tile of a multi-item launch, so that a CTA finds its
-// tile's item with one load instead of a binary search of dependent loads.
+// Item of every encoder tile (by_chunk: of every width-scan chunk) of a
+// multi-item launch, so that a CTA finds its ticket's item with one load
+// instead of a binary search of dependent loads.
 __global__ void __launch_bounds__(NTHREADS) k_tile_map(const Item* items, unsigned n_items,
-                                                      unsigned total_tiles, unsigned* map)
+                                                      unsigned total_tiles, unsigned* map,
+                                                      int by_chunk)
 {
     const unsigned g = blockIdx.x * NTHREADS + threadIdx.x;
     if (g >= total_tiles) return;
     unsigned lo = 0, hi = n_items;
     while (hi - lo > 1) {
         const unsigned mid = (lo + hi) >> 1;
-        if (__ldg(&items[mid].tile_begin) <= g) lo = mid;
+        const unsigned b = by_chunk ? __ldg(&items[mid].chunk_begin) : __ldg(&items[mid].tile_begin);
+        if (b <= g) lo = mid;
         else hi = mid;
     }
     map[g] = lo;
@@ -1814,7 +1817,8 @@ __global__ void __launch_bounds__(GROUP_T) k_group_place(Item* items, unsigned n
 // One CTA per chunk of WSCAN warp units of one item; thread i sums the plane
 // bytes of unit i from its width bytes; a CTA scan and a look-back over the
 // item's chunks give every unit's payload offset (global decode slot = item
-// tile slot * NWARPS + unit in tile).
+// tile slot * NWARPS + unit in tile).  A multi-item launch finds a chunk's
+// item in P.tile_map, here the chunk -> item map (k_tile_map by chunk).
 __global__ void __launch_bounds__(NTHREADS) k_wscan(const Launch P)
 {
     __shared__ Smem sm;
@@ -1834,13 +1838,17 @@ __global__ void __launch_bounds__(NTHREADS) k_wscan(const Launch P)
             sm.ticket = atomicInc(&P.ctl->ticket, modulus);
             unsigned it = 0;
             if (P.items != nullptr && sm.ticket < P.total_tiles) {
-                unsigned lo = 0, hi = P.n_items;
-                while (hi - lo > 1) {
-                    const unsigned mid = (lo + hi) >> 1;
-                    if (P.items[mid].chunk_begin <= sm.ticket) lo = mid;
-                    else hi = mid;
+                if (P.tile_map != nullptr) {
+                    it = P.tile_map[sm.ticket];  // the chunk map of this launch
+                } else {
+                    unsigned lo = 0, hi = P.n_items;
+                    while (hi - lo > 1) {
+                        const unsigned mid = (lo + hi) >> 1;
+                        if (P.items[mid].chunk_begin <= sm.ticket) lo = mid;
+                        else hi = mid;
+                    }
+                    it = lo;
                 }
-                it = lo;
             }
             sm.item = it;
         }

@@ -11,10 +11,10 @@ cudaError_t launch_wscan(const Launch& P, unsigned grid, cudaStream_t s)
 }
 
 cudaError_t launch_tile_map(const Item* items, unsigned n_items, unsigned total_tiles,
-                            unsigned* map, cudaStream_t s)
+                            unsigned* map, cudaStream_t s, bool by_chunk)
 {
-    k_tile_map<<<(total_tiles + NTHREADS - 1) / NTHREADS, NTHREADS, 0, s>>>(items, n_items,
-                                                                           total_tiles, map);
+    k_tile_map<<<(total_tiles + NTHREADS - 1) / NTHREADS, NTHREADS, 0, s>>>(
+        items, n_items, total_tiles, map, by_chunk ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -44,8 +44,9 @@ cudaError_t launch_batch_u(const Launch& P, unsigned grid, cudaStream_t s);
 
 cudaError_t launch_wscan(const Launch& P, unsigned grid, cudaStream_t s);
 cudaError_t launch_decompress(const Launch& P, unsigned grid, cudaStream_t s);
+// Item of every tile (by_chunk: of every width-scan chunk) of a multi-item launch.
 cudaError_t launch_tile_map(const Item* items, unsigned n_items, unsigned total_tiles,
-                            unsigned* map, cudaStream_t s);
+                            unsigned* map, cudaStream_t s, bool by_chunk = false);
 // Grouped batches: first tickets of every item by block size (rewrites the
 // items' tile_begin) and the ticket -> item map; `part` holds 5 u32 per 256 items.
 cudaError_t launch_group(Item* items, unsigned n_items, unsigned* part, unsigned* map,
