@@ -819,7 +819,7 @@ int zc_plan_decompress_batch(zc_batch* plan, int n_msgs, const zc_message* h_msg
         it.tile_begin = (unsigned)tile;
         it.ntiles = (unsigned)tiles_for(m.n, DEC_U);
         it.chunk_begin = (unsigned)chunk;
-        it.nchunks = (unsigned)chunks_for(it.ntiles);
+        it.nchunks = it.ntiles <= DEC_LOCAL_TILES ? 0u : (unsigned)chunks_for(it.ntiles);
         it.x_dtype = m.dtype;
         it.out_dtype = m.dtype;
         tile += it.ntiles;
@@ -868,7 +868,7 @@ int zc_plan_decompress_streams(zc_batch* plan, int n_msgs, const void* const* h_
         it.tile_begin = (unsigned)tile;
         it.ntiles = (unsigned)tiles_for(m.n, DEC_U);
         it.chunk_begin = (unsigned)chunk;
-        it.nchunks = (unsigned)chunks_for(it.ntiles);
+        it.nchunks = it.ntiles <= DEC_LOCAL_TILES ? 0u : (unsigned)chunks_for(it.ntiles);
         it.x_dtype = m.dtype;
         it.out_dtype = m.dtype;
         tile += it.ntiles;
@@ -904,16 +904,18 @@ int zc_decompress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_st
     P.in_cap = plan->packed_cap;
     P.grouped = plan->grouped;
     P.total_tiles = (unsigned)plan->total_chunks;
-    if (plan->n_msgs > 1) {
-        // chunk -> item map for the width scan (the tile map below reuses its space)
-        if (launch_tile_map(P.items, P.n_items, P.total_tiles, w.tile_map, (cudaStream_t)s,
-                            true) != cudaSuccess)
+    if (plan->total_chunks > 0) {  // none when every item is small (offsets found by the decoder)
+        if (plan->n_msgs > 1) {
+            // chunk -> item map for the width scan (the tile map below reuses its space)
+            if (launch_tile_map(P.items, P.n_items, P.total_tiles, w.tile_map, (cudaStream_t)s,
+                                true) != cudaSuccess)
+                return ZC_ERR_CUDA;
+            P.tile_map = w.tile_map;
+        }
+        if (launch_wscan(P, (unsigned)plan->total_chunks, (cudaStream_t)s) != cudaSuccess)
             return ZC_ERR_CUDA;
-        P.tile_map = w.tile_map;
+        P.tile_map = nullptr;
     }
-    if (launch_wscan(P, (unsigned)plan->total_chunks, (cudaStream_t)s) != cudaSuccess)
-        return ZC_ERR_CUDA;
-    P.tile_map = nullptr;
     P.total_tiles = (unsigned)plan->total_tiles;
     if (plan->n_msgs > 1) {
         if (launch_tile_map(P.items, P.n_items, P.total_tiles, w.tile_map, (cudaStream_t)s) !=

@@ -37,6 +37,9 @@ namespace zc {
 constexpr int GR = 8;                  // rows held in registers at a time
 constexpr int WSCAN = NTHREADS;        // warp units per width-scan chunk
 constexpr int DEC_U = 64;              // rows per warp unit of the decompressor
+// Batched decompression: items of at most this many decode tiles get no
+// width-scan chunks; their decoder CTAs find the unit offsets themselves.
+constexpr unsigned DEC_LOCAL_TILES = 4;
 
 // Rows per warp unit of an encoder tile of `chunks` 2048-element chunks.
 __host__ __device__ constexpr int unit_rows(int chunks) { return chunks * 8; }
@@ -283,10 +286,13 @@ __device__ __forceinline__ float pair_half_f(uint32_t half, uint32_t kbits)
 // meta[b] = (planes, byte offset from the unit's payload start) for the
 // unit's blocks.  Returns the unit's payload start in the stream; a unit whose
 // planes would lie beyond cin_cap is reported and gets zero planes.
+// off_local >= 0: the unit's payload offset found by the caller (a small
+// item's decoder CTA), in place of the width scan's P.offs[slot].
 template <int LOG2L, int U, bool HEADS = false>
 __device__ __forceinline__ unsigned long long unit_meta(const Launch& P, const Item& it,
                                                         unsigned slot, unsigned long long ue0,
-                                                        int2* meta, bool& narrow, bool& narrow11)
+                                                        int2* meta, bool& narrow, bool& narrow11,
+                                                        long long off_local = -1)
 {
     constexpr int L = 1 << LOG2L;
     constexpr int PB = L / 8;
@@ -337,9 +343,10 @@ __device__ __forceinline__ unsigned long long unit_meta(const Launch& P, const I
     }
     int tot;
     int off = warp_excl_scan(sum, lane, tot);
-    const bool slot_ok = dcheck(P.ctl, slot < P.ws_cap, slot);
-    const unsigned long long base =
-        32ull + ceil16(nb) + (HEADS ? ceil16(3ull * nb) : 0ull) + (slot_ok ? P.offs[slot] : 0ull);
+    const bool slot_ok = off_local >= 0 || dcheck(P.ctl, slot < P.ws_cap, slot);
+    const unsigned long long uoff =
+        off_local >= 0 ? (unsigned long long)off_local : (slot_ok ? P.offs[slot] : 0ull);
+    const unsigned long long base = 32ull + ceil16(nb) + (HEADS ? ceil16(3ull * nb) : 0ull) + uoff;
     const bool ok = slot_ok && base + (unsigned long long)tot <= it.cin_cap;
     if (!ok && lane == 0) fail(P.ctl, ZC_ERR_FORMAT, slot);
     if (DEBUG_BUILD && mine && lane == (BU >= 32 ? 31 : BU - 1))
@@ -1948,14 +1955,15 @@ __device__ __forceinline__ void unit_raw_copy(const Item& it, int src_dtype, uns
 
 template <int LOG2L, typename TO, bool HEADS = false>
 __device__ __forceinline__ void unit_decode(const Launch& P, const Item& it, unsigned slot,
-                                            unsigned long long ue0, float two_eb, int2* meta)
+                                            unsigned long long ue0, float two_eb, int2* meta,
+                                            long long off_local)
 {
     const int lane = threadIdx.x & 31;
     const TpC tc = tp_consts(lane);
     bool narrow;
     bool narrow11;
-    const uint8_t* src =
-        it.cin + unit_meta<LOG2L, DEC_U, HEADS>(P, it, slot, ue0, meta, narrow, narrow11);
+    const uint8_t* src = it.cin + unit_meta<LOG2L, DEC_U, HEADS>(P, it, slot, ue0, meta, narrow,
+                                                                 narrow11, off_local);
     const uint8_t* hsrc = nullptr;  // heads apart: the heads of this unit's blocks
     if (HEADS) {
         const unsigned long long nb = (it.n + (1ull << LOG2L) - 1) >> LOG2L;
@@ -1989,6 +1997,56 @@ __device__ __forceinline__ void unit_decode(const Launch& P, const Item& it, uns
     }
 }
 
+// Items of at most DEC_LOCAL_TILES decode tiles (planned with no width-scan
+// chunks) need no width scan: the decoder CTA of tile t sums the plane bytes
+// of the item's blocks before its tile itself (at most DEC_LOCAL_TILES - 1
+// tiles' width bytes) and its warps' units (one value per warp), which gives
+// every warp its unit's payload offset; the item's last tile checks the total
+// against the header's payload size, as the width scan does.  Called by every
+// thread of the CTA (coded streams only: lg >= 4).
+__device__ __forceinline__ unsigned long long local_unit_offset(const Item& it, int lg, unsigned t,
+                                                                Ctl* ctl, unsigned item_idx)
+{
+    __shared__ unsigned long long s_pre[NWARPS], s_own[NWARPS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lgb = lg & 7;
+    const unsigned long long PB = (1ull << lgb) / 8;
+    const unsigned long long nb = (it.n + (1ull << lgb) - 1) >> lgb;
+    const unsigned long long bpu = (unsigned long long)(DEC_U * 32) >> lgb;  // blocks per unit
+    const uint8_t* w = it.cin + 32;
+    auto bytes_of = [&](unsigned long long b) -> unsigned long long {
+        const int wv = __ldg(w + b);
+        return wv > ZC_MAX_WIDTH ? 0ull : (unsigned long long)planes_of(wv) * PB;
+    };
+    const unsigned long long pre_end = min((unsigned long long)t * NWARPS * bpu, nb);
+    unsigned long long pre = 0ull;
+    for (unsigned long long b = tid; b < pre_end; b += NTHREADS) pre += bytes_of(b);
+    const unsigned long long u_lo = ((unsigned long long)t * NWARPS + warp) * bpu;
+    const unsigned long long u_hi = min(u_lo + bpu, nb);
+    unsigned long long own = 0ull;
+    for (unsigned long long b = u_lo + lane; b < u_hi; b += 32) own += bytes_of(b);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        pre += __shfl_xor_sync(FULL, pre, o);
+        own += __shfl_xor_sync(FULL, own, o);
+    }
+    if (lane == 0) {
+        s_pre[warp] = pre;
+        s_own[warp] = own;
+    }
+    __syncthreads();
+    unsigned long long off = 0ull, total = 0ull;
+#pragma unroll
+    for (int v = 0; v < NWARPS; ++v) {
+        off += s_pre[v] + (v < warp ? s_own[v] : 0ull);
+        total += s_pre[v] + s_own[v];
+    }
+    if (t + 1 == it.ntiles && tid == 0 &&
+        total != __ldg((const unsigned long long*)it.cin + 3))
+        fail(ctl, ZC_ERR_FORMAT, item_idx);
+    return off;
+}
+
 // NWARPS warp units per CTA, one per warp, independent of each other; the
 // block size comes from the stream's header.
 // 5 CTAs per SM (48 registers): the decoder waits on its plane loads, and the
@@ -2018,30 +2076,33 @@ __global__ void __launch_bounds__(NTHREADS, 5) k_decompress(const Launch P)
     const unsigned slot = tile * NWARPS + warp;
     float eb_in;
     const int lg = check_header(it, P.ctl, idx, -1, eb_in, threadIdx.x == 0 && t == 0);
+    long long loff = -1;  // the unit's payload offset, when this CTA finds it
+    if (P.items != nullptr && it.nchunks == 0 && lg >= 4)  // uniform in the CTA
+        loff = (long long)local_unit_offset(it, lg, t, P.ctl, idx);
     if (ue0 >= it.n) return;
     const float two = __fadd_rn(eb_in, eb_in);
     if (it.out_dtype == ZC_F32) {
         switch (lg) {
-        case 4: unit_decode<4, float>(P, it, slot, ue0, two, meta[warp]); return;
-        case 5: unit_decode<5, float>(P, it, slot, ue0, two, meta[warp]); return;
-        case 6: unit_decode<6, float>(P, it, slot, ue0, two, meta[warp]); return;
-        case 7: unit_decode<7, float>(P, it, slot, ue0, two, meta[warp]); return;
-        case 12: unit_decode<4, float, true>(P, it, slot, ue0, two, meta[warp]); return;
-        case 13: unit_decode<5, float, true>(P, it, slot, ue0, two, meta[warp]); return;
-        case 14: unit_decode<6, float, true>(P, it, slot, ue0, two, meta[warp]); return;
-        case 15: unit_decode<7, float, true>(P, it, slot, ue0, two, meta[warp]); return;
+        case 4: unit_decode<4, float>(P, it, slot, ue0, two, meta[warp], loff); return;
+        case 5: unit_decode<5, float>(P, it, slot, ue0, two, meta[warp], loff); return;
+        case 6: unit_decode<6, float>(P, it, slot, ue0, two, meta[warp], loff); return;
+        case 7: unit_decode<7, float>(P, it, slot, ue0, two, meta[warp], loff); return;
+        case 12: unit_decode<4, float, true>(P, it, slot, ue0, two, meta[warp], loff); return;
+        case 13: unit_decode<5, float, true>(P, it, slot, ue0, two, meta[warp], loff); return;
+        case 14: unit_decode<6, float, true>(P, it, slot, ue0, two, meta[warp], loff); return;
+        case 15: unit_decode<7, float, true>(P, it, slot, ue0, two, meta[warp], loff); return;
         default: break;
         }
     } else {
         switch (lg) {
-        case 4: unit_decode<4, uint16_t>(P, it, slot, ue0, two, meta[warp]); return;
-        case 5: unit_decode<5, uint16_t>(P, it, slot, ue0, two, meta[warp]); return;
-        case 6: unit_decode<6, uint16_t>(P, it, slot, ue0, two, meta[warp]); return;
-        case 7: unit_decode<7, uint16_t>(P, it, slot, ue0, two, meta[warp]); return;
-        case 12: unit_decode<4, uint16_t, true>(P, it, slot, ue0, two, meta[warp]); return;
-        case 13: unit_decode<5, uint16_t, true>(P, it, slot, ue0, two, meta[warp]); return;
-        case 14: unit_decode<6, uint16_t, true>(P, it, slot, ue0, two, meta[warp]); return;
-        case 15: unit_decode<7, uint16_t, true>(P, it, slot, ue0, two, meta[warp]); return;
+        case 4: unit_decode<4, uint16_t>(P, it, slot, ue0, two, meta[warp], loff); return;
+        case 5: unit_decode<5, uint16_t>(P, it, slot, ue0, two, meta[warp], loff); return;
+        case 6: unit_decode<6, uint16_t>(P, it, slot, ue0, two, meta[warp], loff); return;
+        case 7: unit_decode<7, uint16_t>(P, it, slot, ue0, two, meta[warp], loff); return;
+        case 12: unit_decode<4, uint16_t, true>(P, it, slot, ue0, two, meta[warp], loff); return;
+        case 13: unit_decode<5, uint16_t, true>(P, it, slot, ue0, two, meta[warp], loff); return;
+        case 14: unit_decode<6, uint16_t, true>(P, it, slot, ue0, two, meta[warp], loff); return;
+        case 15: unit_decode<7, uint16_t, true>(P, it, slot, ue0, two, meta[warp], loff); return;
         default: break;
         }
     }

@@ -287,3 +287,46 @@ def test_grouped_batch_follows_block_sizes_changed_on_the_device(zc):
         ref = oracle_stream(x, blk, eb)
         assert buf[off[i]:off[i] + len(ref)] == ref, i
     assert off[-1] == sum(len(oracle_stream(x, blk, eb)) for x, blk, eb in zip(xs, new_blocks, ebs))
+
+
+@pytest.mark.parametrize("block", [16, 32, 64, 128])
+def test_batch_decompress_small_and_large_items(zc, block):
+    """Items of up to four decode tiles (16384 elements each) are decoded
+    without the width scan, larger ones with it: both sides of that boundary,
+    every block size, FP32 and BF16, bit-identical to the oracle."""
+    sizes = [1, 31, 16383, 16384, 16385, 32768 + 7, 49152, 65535, 65536, 65537, 81920, 81921,
+             3, 40000]
+    xs, _, ebs = mixed_messages(7, sizes)
+    blocks = [block] * len(sizes)
+    b = zc.BatchCompress([x.cuda() for x in xs], blocks, ebs)
+    b.run()
+    check_against_oracle(b, xs, blocks, ebs)
+    outs = [torch.empty(x.numel(), dtype=x.dtype, device="cuda") for x in xs]
+    d = zc.BatchDecompress(b.packed, b.msg_off, outs)
+    for _ in range(2):  # the second run reuses the workspace
+        d.run()
+        assert d.ws.status()[0] == 0, d.ws.status()
+        for i, (x, eb) in enumerate(zip(xs, ebs)):
+            s = oracle_stream(x, block, eb)
+            code = 0 if x.dtype == torch.float32 else 1
+            np.testing.assert_array_equal(np_of(outs[i]), oracle.decompress(s, x.numel(), code))
+
+
+@pytest.mark.parametrize("n", [5000, 60000, 100000])
+def test_batch_decompress_payload_size_mismatch_is_a_format_error(zc, n):
+    """A header whose payload size disagrees with the width bytes is caught
+    whether the item's offsets come from the width scan (100000 elements) or
+    from its decoder CTAs (5000, 60000)."""
+    xs, _, ebs = mixed_messages(8, [3000, n])
+    b = zc.BatchCompress([x.cuda() for x in xs], [32, 32], ebs)
+    b.run()
+    off = b.msg_off.cpu().tolist()
+    hdr = b.packed[off[1]:off[1] + 32].cpu().numpy().copy()
+    pl = int(hdr[24:32].view(np.uint64)[0])
+    assert pl >= 32
+    hdr[24:32] = np.array([pl - 16], dtype=np.uint64).view(np.uint8)
+    b.packed[off[1]:off[1] + 32] = torch.from_numpy(hdr).cuda()
+    outs = [torch.empty(x.numel(), dtype=x.dtype, device="cuda") for x in xs]
+    d = zc.BatchDecompress(b.packed, b.msg_off, outs)
+    d.run()
+    assert d.ws.status()[0] == zc.ERR_FORMAT
