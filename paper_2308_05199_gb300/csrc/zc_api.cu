@@ -137,6 +137,10 @@ int ws_view(void* ws, size_t bytes, WsView& v)
     return ZC_OK;
 }
 
+// Width scans over at least this many items find a chunk's item in a map
+// (one extra launch); fewer items are searched (at most 8 dependent loads).
+constexpr int CHUNK_MAP_ITEMS = 256;
+
 // SM count of the current device (queried once per device).
 int sm_count()
 {
@@ -582,7 +586,7 @@ int zc_reduce_step_batch(const zc_plan* plan, void* d_ws, size_t ws_bytes, zc_st
     P.urows = unit_rows(C);
     if (plan->has_input) {
         P.total_tiles = (unsigned)plan->total_chunks;
-        if (plan->n_items > 1) {
+        if (plan->n_items >= CHUNK_MAP_ITEMS) {
             // chunk -> item map for the width scan (the tile map below reuses its space)
             if (launch_tile_map(P.items, P.n_items, P.total_tiles, w.tile_map, (cudaStream_t)s,
                                 true) != cudaSuccess)
@@ -905,7 +909,7 @@ int zc_decompress_batch(const zc_batch* plan, void* d_ws, size_t ws_bytes, zc_st
     P.grouped = plan->grouped;
     P.total_tiles = (unsigned)plan->total_chunks;
     if (plan->total_chunks > 0) {  // none when every item is small (offsets found by the decoder)
-        if (plan->n_msgs > 1) {
+        if (plan->n_msgs >= CHUNK_MAP_ITEMS) {
             // chunk -> item map for the width scan (the tile map below reuses its space)
             if (launch_tile_map(P.items, P.n_items, P.total_tiles, w.tile_map, (cudaStream_t)s,
                                 true) != cudaSuccess)
