@@ -2052,6 +2052,10 @@ __device__ __forceinline__ unsigned long long local_unit_offset(const Item& it, 
 // 5 CTAs per SM (48 registers): the decoder waits on its plane loads, and the
 // extra warps hide more of that than the few spilled values cost (measured on
 // the 512^3 field: 0.166 ms at 5 CTAs per SM, 0.175 ms at 4, 0.168 ms at 6)
+// BATCH: a multi-item launch (items may find their own unit offsets); the
+// single-stream decoder is compiled without that path, which would cost it
+// registers.
+template <bool BATCH>
 __global__ void __launch_bounds__(NTHREADS, 5) k_decompress(const Launch P)
 {
     __shared__ __align__(16) int2 meta[NWARPS][DEC_U * 2];
@@ -2077,7 +2081,7 @@ __global__ void __launch_bounds__(NTHREADS, 5) k_decompress(const Launch P)
     float eb_in;
     const int lg = check_header(it, P.ctl, idx, -1, eb_in, threadIdx.x == 0 && t == 0);
     long long loff = -1;  // the unit's payload offset, when this CTA finds it
-    if (P.items != nullptr && it.nchunks == 0 && lg >= 4)  // uniform in the CTA
+    if (BATCH && it.nchunks == 0 && lg >= 4)  // uniform in the CTA
         loff = (long long)local_unit_offset(it, lg, t, P.ctl, idx);
     if (ue0 >= it.n) return;
     const float two = __fadd_rn(eb_in, eb_in);

@@ -30,7 +30,8 @@ cudaError_t launch_group(Item* items, unsigned n_items, unsigned* part, unsigned
 
 cudaError_t launch_decompress(const Launch& P, unsigned grid, cudaStream_t s)
 {
-    k_decompress<<<grid, NTHREADS, 0, s>>>(P);
+    if (P.items != nullptr) k_decompress<true><<<grid, NTHREADS, 0, s>>>(P);
+    else k_decompress<false><<<grid, NTHREADS, 0, s>>>(P);
     return cudaGetLastError();
 }
 
