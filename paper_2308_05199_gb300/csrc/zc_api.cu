@@ -212,7 +212,8 @@ unsigned range_grid(uint64_t n)
 {
     uint64_t g = (n + 256 * 32 - 1) / (256 * 32);
     if (g < 1) g = 1;
-    if (g > 1216) g = 1216;  // 8 CTAs per SM on 152 SMs
+    const uint64_t cap = (uint64_t)sm_count() * 4;  // 4 CTAs of 256 per SM: the fastest measured
+    if (g > cap) g = cap;
     return (unsigned)g;
 }
 
