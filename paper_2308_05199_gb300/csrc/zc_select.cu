@@ -6,6 +6,7 @@
 // comment of zc.h (zc_batch_chunk_stats .. zc_batch_select).  Everything runs
 // on the device; nothing is read back, so a whole select-then-compress
 // sequence can be captured in one CUDA graph.
+#include <cstddef>
 #include <cstring>
 
 #include "zc_launch.h"
@@ -287,17 +288,27 @@ __global__ void __launch_bounds__(256, 4) k_chunk_stats(const Item* items, unsig
 // Shared memory of an MLP CTA (floats): the parameters with padded row
 // strides (no bank conflicts), the normalised inputs, both layers'
 // activations (after the ReLU), one 64 x 64 gradient buffer and the outputs.
+// Rows that the forward pass reads four at a time (W2, W3, X, A1, A2) have
+// strides of a multiple of 4 floats: 16-byte loads, and at stride 68 the 8
+// rows of a quarter warp fall in distinct bank groups.
+constexpr int NHP = NH + 4, NIP = NI + 4;
 struct MlpSmem {
     float W1[NH][NI + 1], b1[NH];
-    float W2[NH][NH + 1], b2[NH];
-    float W3[NO][NH + 1], b3[NO];
-    float X[TB][NI + 1];
-    float A1[TB][NH + 1];
-    float A2[TB][NH + 1];  // later: dA1
-    float D[TB][NH + 1];   // dA2
-    float Y[TB][NO];       // outputs, later dY
+    alignas(16) float W2[NH][NHP];
+    float b2[NH];
+    alignas(16) float W3[NO][NHP];
+    float b3[NO];
+    alignas(16) float X[TB][NIP];
+    alignas(16) float A1[TB][NHP];
+    alignas(16) float A2[TB][NHP];  // later: dA1
+    float D[TB][NH + 1];            // dA2
+    float Y[TB][NO];                // outputs, later dY
     float red[MT / 32];
 };
+static_assert(offsetof(MlpSmem, W2) % 16 == 0 && offsetof(MlpSmem, W3) % 16 == 0 &&
+                  offsetof(MlpSmem, X) % 16 == 0 && offsetof(MlpSmem, A1) % 16 == 0 &&
+                  offsetof(MlpSmem, A2) % 16 == 0,
+              "16-byte rows");
 
 __device__ __forceinline__ float relu(float v) { return v > 0.0f ? v : 0.0f; }
 
@@ -356,7 +367,13 @@ __device__ __forceinline__ void mlp_forward_tile(MlpSmem& sm)
             const int s = g * (TB / 4) + i;
             float a = sm.b1[j];
 #pragma unroll
-            for (int k = 0; k < NI; ++k) a = __fmaf_rn(w[k], sm.X[s][k], a);
+            for (int k = 0; k < NI; k += 4) {
+                const float4 x = *reinterpret_cast<const float4*>(&sm.X[s][k]);
+                a = __fmaf_rn(w[k], x.x, a);
+                a = __fmaf_rn(w[k + 1], x.y, a);
+                a = __fmaf_rn(w[k + 2], x.z, a);
+                a = __fmaf_rn(w[k + 3], x.w, a);
+            }
             sm.A1[s][j] = relu(a);
         }
     }
@@ -365,12 +382,17 @@ __device__ __forceinline__ void mlp_forward_tile(MlpSmem& sm)
         float acc[TB / 4];
 #pragma unroll
         for (int i = 0; i < TB / 4; ++i) acc[i] = sm.b2[j];
-#pragma unroll 4
-        for (int k = 0; k < NH; ++k) {
-            const float w = sm.W2[j][k];
+#pragma unroll 2
+        for (int k = 0; k < NH; k += 4) {
+            const float4 w = *reinterpret_cast<const float4*>(&sm.W2[j][k]);
 #pragma unroll
-            for (int i = 0; i < TB / 4; ++i)
-                acc[i] = __fmaf_rn(w, sm.A1[g * (TB / 4) + i][k], acc[i]);
+            for (int i = 0; i < TB / 4; ++i) {
+                const float4 a = *reinterpret_cast<const float4*>(&sm.A1[g * (TB / 4) + i][k]);
+                acc[i] = __fmaf_rn(w.x, a.x, acc[i]);
+                acc[i] = __fmaf_rn(w.y, a.y, acc[i]);
+                acc[i] = __fmaf_rn(w.z, a.z, acc[i]);
+                acc[i] = __fmaf_rn(w.w, a.w, acc[i]);
+            }
         }
 #pragma unroll
         for (int i = 0; i < TB / 4; ++i) sm.A2[g * (TB / 4) + i][j] = relu(acc[i]);
@@ -379,8 +401,15 @@ __device__ __forceinline__ void mlp_forward_tile(MlpSmem& sm)
     {
         const int s = t >> 2, o = t & 3;
         float y = sm.b3[o];
-#pragma unroll 8
-        for (int k = 0; k < NH; ++k) y = __fmaf_rn(sm.W3[o][k], sm.A2[s][k], y);
+#pragma unroll 4
+        for (int k = 0; k < NH; k += 4) {
+            const float4 w = *reinterpret_cast<const float4*>(&sm.W3[o][k]);
+            const float4 a = *reinterpret_cast<const float4*>(&sm.A2[s][k]);
+            y = __fmaf_rn(w.x, a.x, y);
+            y = __fmaf_rn(w.y, a.y, y);
+            y = __fmaf_rn(w.z, a.z, y);
+            y = __fmaf_rn(w.w, a.w, y);
+        }
         sm.Y[s][o] = y;
     }
     __syncthreads();

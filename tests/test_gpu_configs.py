@@ -187,27 +187,33 @@ def test_ring_64x8192sq_full_size(zc):
 
 def test_selector_heldout_streams_from_graph(zc):
     """Held-out chunks of the four workload kinds through the learned
-    selector path captured in a CUDA graph: sampled streams byte-equal to the
-    oracle's at the chosen block size (or raw), decoded chunks bit-equal."""
+    selector path (bits and time networks, as the bench runs it) captured in
+    a CUDA graph: sampled streams byte-equal to the oracle's at the chosen
+    block size (or raw), decoded chunks bit-equal."""
     from paper_2308_05199_gb300 import selector as S
     tv, te, _ = S.mixed_chunks(2000, seed=1, scale=64)
     tr = S.ChunkBatch(tv, te)
     cfg = tr.cost_model(link_gbs=12.5, reps=2)
-    X, T, _, _ = S.dataset(tr)
+    X, T, keep, bits = S.dataset(tr)
     mlp = S.Mlp(seed=0)
     mlp.set_norm(X)
     mlp.fit(X, T, epochs=10, batch=256, lr=0.02, momentum=0.9, seed=0)
+    rates, _ = S.time_labels(tv, te, bits, groups=4)
+    tmlp = S.Mlp(seed=1)
+    tmlp.set_norm(X)
+    tmlp.fit(X, torch.from_numpy(np.log2(rates[keep]).astype(np.float32)).cuda(), epochs=10,
+             batch=256, lr=0.02, momentum=0.9, seed=1)
     del tr
     xs, ebs, _ = S.mixed_messages(96 << 20, seed=7, device="cuda", scale=64)
     hv, he = S.split_chunks(xs, ebs)
     st = torch.cuda.Stream()
     torch.cuda.synchronize()
     cb = S.ChunkBatch(hv, he, stream=st)
-    cb.run_selected(cfg, mlp)
+    cb.run_selected(cfg, mlp, tmlp)
     st.synchronize()
     g = zc.Graph(st)
     with g.capture():
-        cb.run_selected(cfg, mlp)
+        cb.run_selected(cfg, mlp, tmlp)
         cb.dec.run(st)
     cb.batch.packed.zero_()
     for o in cb.outs:
