@@ -1135,15 +1135,22 @@ def e2e_ours(torch, W, args, step_bytes, world):
     for _ in range(2):
         one()
     torch.cuda.synchronize()
+    walls = []
     t = time.perf_counter()
     for _ in range(K):
-        one()
+        t1 = time.perf_counter()
+        one()  # ends with a device synchronize
+        walls.append(time.perf_counter() - t1)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t) / K
     h2d = sum(h.numel() * h.element_size() for h in host_in)
     return {"value": round(step_bytes * world / dt / 1e9, 1), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": stats["d2h"],
-            "ms_per_step": round(dt * 1e3, 3), "steps": K}
+            "ms_per_step": round(dt * 1e3, 3), "steps": K,
+            # the mean above is the reported value; the median and the range of
+            # the single steps show how the host link varies between steps
+            "ms_per_step_median": round(statistics.median(walls) * 1e3, 3),
+            "ms_per_step_min_max": [round(min(walls) * 1e3, 3), round(max(walls) * 1e3, 3)]}
 
 
 # ---------------------------------------------------------------------------
