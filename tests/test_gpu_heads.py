@@ -107,3 +107,24 @@ def test_heads_capacity_covers_heads_area(zc):
                               ob.data_ptr(), ws.ptr, ws.nbytes,
                               torch.cuda.current_stream().cuda_stream)
     assert st == zc.ERR_CAPACITY
+
+
+@pytest.mark.parametrize("block", [16, 32, 64, 128])
+@pytest.mark.parametrize("kind", ["offset_walk", "tdist", "tdist_wide"])
+def test_decompress_heads_narrow_and_wide_units(zc, block, kind):
+    """Heads-apart streams whose units have at most 11 planes per block
+    (decoded two rows per integer scan, the heads added after it) and wider
+    ones (one row per scan), and streams that mix both, decode bit for bit
+    as the oracle does."""
+    for n in (2048 * 8 + 3, 100003):
+        x = signal("tdist" if kind == "tdist_wide" else kind, n, n + block)
+        if kind == "tdist_wide":
+            x = x * 300.0  # deltas beyond 1023 levels in most units
+        a = np_of(x)
+        s = oracle.compress_heads(a, 1e-3, int(math.log2(block)))
+        cmp = torch.frombuffer(bytearray(s), dtype=torch.uint8).cuda()
+        for out_dtype, code in ((torch.float32, 0), (torch.bfloat16, 1)):
+            ws = zc.Workspace(n, 1)
+            y = zc.decompress(cmp, n, out_dtype, ws=ws)
+            assert ws.status()[0] == 0
+            np.testing.assert_array_equal(np_of(y), oracle.decompress(s, n, code))
