@@ -451,7 +451,7 @@ int zc_decompress(const void* d_cmp, size_t cmp_cap, void* d_out, uint64_t n, in
     P.total_tiles = (unsigned)chunks;
     if (launch_wscan(P, (unsigned)chunks, (cudaStream_t)s) != cudaSuccess) return ZC_ERR_CUDA;
     P.total_tiles = (unsigned)tiles;
-    return cuda_status(launch_decompress(P, (unsigned)tiles, (cudaStream_t)s));
+    return cuda_status(launch_decompress(P, (unsigned)tiles, (cudaStream_t)s, true));
 }
 
 int zc_reduce_step(const void* d_cmp_in, size_t cmp_in_cap, const float* d_local, uint64_t n,

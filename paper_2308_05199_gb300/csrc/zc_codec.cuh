@@ -1830,6 +1830,7 @@ __global__ void __launch_bounds__(NTHREADS) k_wscan(const Launch P)
 {
     __shared__ Smem sm;
     __shared__ int wsum[NWARPS];
+    grid_dep_launch();  // the decoder after it may be launched now (it waits for the offsets)
     if (threadIdx.x == 0) {
         sm.E = ld_volatile_u32(&P.ctl->epoch) + 1u;
         sm.abort = ld_volatile_u32(&P.ctl->magic) != WS_MAGIC;
@@ -2056,7 +2057,7 @@ __device__ __forceinline__ unsigned long long local_unit_offset(const Item& it, 
 // single-stream decoder is compiled without that path, which would cost it
 // registers.
 template <bool BATCH>
-__global__ void __launch_bounds__(NTHREADS, 5) k_decompress(const Launch P)
+__device__ __forceinline__ void decompress_tile(const Launch& P)
 {
     __shared__ __align__(16) int2 meta[NWARPS][DEC_U * 2];
     const unsigned tile = blockIdx.x;
@@ -2083,6 +2084,12 @@ __global__ void __launch_bounds__(NTHREADS, 5) k_decompress(const Launch P)
     long long loff = -1;  // the unit's payload offset, when this CTA finds it
     if (BATCH && it.nchunks == 0 && lg >= 4)  // uniform in the CTA
         loff = (long long)local_unit_offset(it, lg, t, P.ctl, idx);
+    // the width scan's offsets are read from here on: a single-stream decoder
+    // launched dependent on the scan has looked up its tile and checked the
+    // header while the scan ran, and waits for it now.  Every thread passes
+    // this wait, so the decoder never completes before the scan (later
+    // launches on the stream find the scan finished).
+    if (!BATCH) grid_dep_wait();
     if (ue0 >= it.n) return;
     const float two = __fadd_rn(eb_in, eb_in);
     if (it.out_dtype == ZC_F32) {
@@ -2112,6 +2119,12 @@ __global__ void __launch_bounds__(NTHREADS, 5) k_decompress(const Launch P)
     }
     if (lg == -2) unit_raw_copy(it, ZC_F32, ue0);
     else if (lg == -3) unit_raw_copy(it, ZC_BF16, ue0);
+}
+
+template <bool BATCH>
+__global__ void __launch_bounds__(NTHREADS, 5) k_decompress(const Launch P)
+{
+    decompress_tile<BATCH>(P);
 }
 
 #endif  // ZC_DECODE_KERNELS

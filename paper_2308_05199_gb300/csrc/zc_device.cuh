@@ -155,6 +155,14 @@ __device__ __forceinline__ uint32_t tpose(uint32_t u, const TpC& c)
     return u;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while the kernel before it on the stream still
+// runs; grid_dep_wait() blocks until that kernel has completed and its memory
+// operations are visible (it returns at once in a kernel launched without
+// the attribute).  grid_dep_launch() lets the dependent kernel start early.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Inclusive prefix sum over segments of W lanes, using the in-range predicate
 // of shfl.up so each step is one shuffle and one predicated add.
 template <int W>

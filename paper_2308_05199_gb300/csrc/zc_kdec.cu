@@ -28,11 +28,29 @@ cudaError_t launch_group(Item* items, unsigned n_items, unsigned* part, unsigned
     return cudaGetLastError();
 }
 
-cudaError_t launch_decompress(const Launch& P, unsigned grid, cudaStream_t s)
+cudaError_t launch_decompress(const Launch& P, unsigned grid, cudaStream_t s, bool after_wscan)
 {
-    if (P.items != nullptr) k_decompress<true><<<grid, NTHREADS, 0, s>>>(P);
-    else k_decompress<false><<<grid, NTHREADS, 0, s>>>(P);
-    return cudaGetLastError();
+    if (P.items != nullptr) {
+        k_decompress<true><<<grid, NTHREADS, 0, s>>>(P);
+        return cudaGetLastError();
+    }
+    if (!after_wscan) {
+        k_decompress<false><<<grid, NTHREADS, 0, s>>>(P);
+        return cudaGetLastError();
+    }
+    // launched dependent on the width scan just before it on the stream: its
+    // CTAs read their headers and width bytes while the scan still runs
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_decompress<false>, P);
 }
 
 }  // namespace zc

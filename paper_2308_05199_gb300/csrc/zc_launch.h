@@ -43,7 +43,10 @@ template <int U>
 cudaError_t launch_batch_u(const Launch& P, unsigned grid, cudaStream_t s);
 
 cudaError_t launch_wscan(const Launch& P, unsigned grid, cudaStream_t s);
-cudaError_t launch_decompress(const Launch& P, unsigned grid, cudaStream_t s);
+// after_wscan (single streams): the width scan was the launch just before on
+// `s`; the decoder is launched dependent on it (programmatic serialisation).
+cudaError_t launch_decompress(const Launch& P, unsigned grid, cudaStream_t s,
+                              bool after_wscan = false);
 // Item of every tile (by_chunk: of every width-scan chunk) of a multi-item launch.
 cudaError_t launch_tile_map(const Item* items, unsigned n_items, unsigned total_tiles,
                             unsigned* map, cudaStream_t s, bool by_chunk = false);
