@@ -1489,6 +1489,10 @@ __device__ __forceinline__ void enc_pipeline(const Launch& P, const Src& src, En
     extern __shared__ __align__(16) uint8_t dsm[];  // width bytes [slot][warp][2U] (, stages)
     __shared__ __align__(16) uint8_t stage_static[SINGLE ? 1 : NWARPS][SINGLE ? 16 : stage_bytes(32)];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // a relative bound comes from the range kernel launched just before: an
+    // encoder launched dependent on it waits here for it to complete (every
+    // thread: the bound is read below and in every tile)
+    if (P.eb_from_ctl) grid_dep_wait();
     if (tid == 0) {
         es.E = ld_volatile_u32(&P.ctl->epoch) + 1u;
         int a = ld_volatile_u32(&P.ctl->magic) != WS_MAGIC;

@@ -11,6 +11,27 @@
 
 namespace zc {
 
+// One encoder launch; `after_range`: the range kernel that resolves the
+// relative bound was the launch just before on `s`, and this one is launched
+// dependent on it (programmatic serialisation): its CTAs become resident
+// while the range kernel finishes and wait for it before reading the bound.
+template <typename... A>
+static cudaError_t launch_enc(void (*k)(A...), unsigned grid, int smem, cudaStream_t s,
+                              bool after_range, const A&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(ENC_THREADS);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = after_range ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <auto K, auto K16>
 static cudaError_t launch_typed(int x_dtype, int smem, unsigned grid, cudaStream_t s,
                                 const Launch& P)
@@ -18,9 +39,9 @@ static cudaError_t launch_typed(int x_dtype, int smem, unsigned grid, cudaStream
     const cudaError_t e32 = smem_limit<K>(smem);
     const cudaError_t e16 = smem_limit<K16>(smem);
     if (e32 != cudaSuccess || e16 != cudaSuccess) return e32 != cudaSuccess ? e32 : e16;
-    if (x_dtype == ZC_F32) K<<<grid, ENC_THREADS, smem, s>>>(P);
-    else K16<<<grid, ENC_THREADS, smem, s>>>(P);
-    return cudaGetLastError();
+    const bool after_range = P.eb_from_ctl != 0;
+    return x_dtype == ZC_F32 ? launch_enc(K, grid, smem, s, after_range, P)
+                             : launch_enc(K16, grid, smem, s, after_range, P);
 }
 
 template <int LG>
@@ -57,9 +78,10 @@ static cudaError_t scatter_u(int x_dtype, const Launch& P, const ScatterParams& 
     const cudaError_t e32 = smem_limit<k_scatter<LG, U, float>>(smem);
     const cudaError_t e16 = smem_limit<k_scatter<LG, U, uint16_t>>(smem);
     if (e32 != cudaSuccess || e16 != cudaSuccess) return e32 != cudaSuccess ? e32 : e16;
-    if (x_dtype == ZC_F32) k_scatter<LG, U, float><<<grid, ENC_THREADS, smem, s>>>(P, SP);
-    else k_scatter<LG, U, uint16_t><<<grid, ENC_THREADS, smem, s>>>(P, SP);
-    return cudaGetLastError();
+    const bool after_range = P.eb_from_ctl != 0;
+    return x_dtype == ZC_F32
+               ? launch_enc(k_scatter<LG, U, float>, grid, smem, s, after_range, P, SP)
+               : launch_enc(k_scatter<LG, U, uint16_t>, grid, smem, s, after_range, P, SP);
 }
 
 template <int LG>

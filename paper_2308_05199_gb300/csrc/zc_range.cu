@@ -176,6 +176,7 @@ __device__ void range_finish(const RangeLaunch& P, Acc a)
 template <typename TX>
 __global__ void __launch_bounds__(256) k_range_one(const RangeLaunch P)
 {
+    grid_dep_launch();  // the compressor after it may be launched now (it waits for the bound)
     Acc a{FLT_MAX, -FLT_MAX, false};
     const unsigned long long gtid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long gstride = (unsigned long long)gridDim.x * blockDim.x;
@@ -186,6 +187,7 @@ __global__ void __launch_bounds__(256) k_range_one(const RangeLaunch P)
 template <typename TX>
 __global__ void __launch_bounds__(256) k_range_multi(const RangeLaunch P, const RangeSegs S)
 {
+    grid_dep_launch();  // the scatter pack after it may be launched now (it waits for the bound)
     Acc a{FLT_MAX, -FLT_MAX, false};
     const unsigned long long gtid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned long long gstride = (unsigned long long)gridDim.x * blockDim.x;
