@@ -599,14 +599,20 @@ int zc_reduce_step_batch(const zc_plan* plan, void* d_ws, size_t ws_bytes, zc_st
         P.tile_map = nullptr;
     }
     P.total_tiles = (unsigned)plan->total_tiles;
-    if (plan->n_items > 1) {
-        if (launch_tile_map(P.items, P.n_items, P.total_tiles, w.tile_map, (cudaStream_t)s) !=
-            cudaSuccess)
-            return ZC_ERR_CUDA;
-        P.tile_map = w.tile_map;
-    }
     const uint64_t grid = enc_grid(plan->total_tiles, unit_rows(C), w);
     if (grid == 0) return ZC_ERR_WORKSPACE;
+    // each launch of the step is dependent on the one before it: the tile
+    // map is built while the width scan runs, the fused kernel's CTAs become
+    // resident while the map finishes (both wait for their inputs)
+    if (plan->n_items > 1) {
+        if (launch_tile_map(P.items, P.n_items, P.total_tiles, w.tile_map, (cudaStream_t)s,
+                            false, plan->has_input != 0) != cudaSuccess)
+            return ZC_ERR_CUDA;
+        P.tile_map = w.tile_map;
+        P.dep = 1;
+    } else {
+        P.dep = plan->has_input != 0;
+    }
     return cuda_status(launch_reduce_any(lg, C, P, (unsigned)grid, (cudaStream_t)s));
 }
 

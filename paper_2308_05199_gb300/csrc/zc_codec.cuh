@@ -90,6 +90,10 @@ struct Launch {
     // order, so seg_off[i] is only item i's start and seg_off[n_items] the
     // packed total; a decoder bounds a stream by seg_off[n_items]
     int grouped;
+    // encoder launches: launched dependent on the kernel just before on the
+    // stream (programmatic serialisation), whose results the CTAs wait for
+    // in their prologue (a relative bound, eb_from_ctl, implies it)
+    int dep;
 };
 
 struct Smem {
@@ -1489,10 +1493,11 @@ __device__ __forceinline__ void enc_pipeline(const Launch& P, const Src& src, En
     extern __shared__ __align__(16) uint8_t dsm[];  // width bytes [slot][warp][2U] (, stages)
     __shared__ __align__(16) uint8_t stage_static[SINGLE ? 1 : NWARPS][SINGLE ? 16 : stage_bytes(32)];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // a relative bound comes from the range kernel launched just before: an
-    // encoder launched dependent on it waits here for it to complete (every
-    // thread: the bound is read below and in every tile)
-    if (P.eb_from_ctl) grid_dep_wait();
+    // a relative bound comes from the range kernel launched just before, the
+    // fused ring step's offsets and tile map from the kernels before it: an
+    // encoder launched dependent on them waits here for them to complete
+    // (every thread: their results are read below and in every tile)
+    if (P.eb_from_ctl || P.dep) grid_dep_wait();
     if (tid == 0) {
         es.E = ld_volatile_u32(&P.ctl->epoch) + 1u;
         int a = ld_volatile_u32(&P.ctl->magic) != WS_MAGIC;
@@ -1690,10 +1695,15 @@ __device__ __forceinline__ void resolve_packed(const Launch& P, Item& it, unsign
 // Item of every encoder tile (by_chunk: of every width-scan chunk) of a
 // multi-item launch, so that a CTA finds its ticket's item with one load
 // instead of a binary search of dependent loads.
+// Launched dependent on a width scan (the fused ring step), the map is
+// built while the scan runs; the kernel then waits for the scan, so that it
+// never completes before it (the step launched dependent on the map reads
+// the scan's offsets too).  Thread 0 always reaches the wait.
 __global__ void __launch_bounds__(NTHREADS) k_tile_map(const Item* items, unsigned n_items,
                                                       unsigned total_tiles, unsigned* map,
                                                       int by_chunk)
 {
+    grid_dep_launch();
     const unsigned g = blockIdx.x * NTHREADS + threadIdx.x;
     if (g >= total_tiles) return;
     unsigned lo = 0, hi = n_items;
@@ -1704,6 +1714,7 @@ __global__ void __launch_bounds__(NTHREADS) k_tile_map(const Item* items, unsign
         else hi = mid;
     }
     map[g] = lo;
+    grid_dep_wait();
 }
 
 // ---- grouped batches ------------------------------------------------------------

@@ -11,11 +11,20 @@ cudaError_t launch_wscan(const Launch& P, unsigned grid, cudaStream_t s)
 }
 
 cudaError_t launch_tile_map(const Item* items, unsigned n_items, unsigned total_tiles,
-                            unsigned* map, cudaStream_t s, bool by_chunk)
+                            unsigned* map, cudaStream_t s, bool by_chunk, bool dependent)
 {
-    k_tile_map<<<(total_tiles + NTHREADS - 1) / NTHREADS, NTHREADS, 0, s>>>(
-        items, n_items, total_tiles, map, by_chunk ? 1 : 0);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((total_tiles + NTHREADS - 1) / NTHREADS);
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = dependent ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_tile_map, items, n_items, total_tiles, map,
+                              by_chunk ? 1 : 0);
 }
 
 cudaError_t launch_group(Item* items, unsigned n_items, unsigned* part, unsigned* map,

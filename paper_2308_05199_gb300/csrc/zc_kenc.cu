@@ -11,10 +11,11 @@
 
 namespace zc {
 
-// One encoder launch; `after_range`: the range kernel that resolves the
-// relative bound was the launch just before on `s`, and this one is launched
-// dependent on it (programmatic serialisation): its CTAs become resident
-// while the range kernel finishes and wait for it before reading the bound.
+// One encoder launch; `after_range`: the kernel this one waits for (the range
+// kernel of a relative bound, the fused step's width scan or tile map) was
+// the launch just before on `s`, and this one is launched dependent on it
+// (programmatic serialisation): its CTAs become resident while that kernel
+// finishes and wait for it in their prologue.
 template <typename... A>
 static cudaError_t launch_enc(void (*k)(A...), unsigned grid, int smem, cudaStream_t s,
                               bool after_range, const A&... args)
@@ -39,7 +40,7 @@ static cudaError_t launch_typed(int x_dtype, int smem, unsigned grid, cudaStream
     const cudaError_t e32 = smem_limit<K>(smem);
     const cudaError_t e16 = smem_limit<K16>(smem);
     if (e32 != cudaSuccess || e16 != cudaSuccess) return e32 != cudaSuccess ? e32 : e16;
-    const bool after_range = P.eb_from_ctl != 0;
+    const bool after_range = P.eb_from_ctl != 0 || P.dep != 0;
     return x_dtype == ZC_F32 ? launch_enc(K, grid, smem, s, after_range, P)
                              : launch_enc(K16, grid, smem, s, after_range, P);
 }
@@ -78,7 +79,7 @@ static cudaError_t scatter_u(int x_dtype, const Launch& P, const ScatterParams& 
     const cudaError_t e32 = smem_limit<k_scatter<LG, U, float>>(smem);
     const cudaError_t e16 = smem_limit<k_scatter<LG, U, uint16_t>>(smem);
     if (e32 != cudaSuccess || e16 != cudaSuccess) return e32 != cudaSuccess ? e32 : e16;
-    const bool after_range = P.eb_from_ctl != 0;
+    const bool after_range = P.eb_from_ctl != 0 || P.dep != 0;
     return x_dtype == ZC_F32
                ? launch_enc(k_scatter<LG, U, float>, grid, smem, s, after_range, P, SP)
                : launch_enc(k_scatter<LG, U, uint16_t>, grid, smem, s, after_range, P, SP);
@@ -101,8 +102,7 @@ static cudaError_t reduce_u(const Launch& P, unsigned grid, cudaStream_t s)
 {
     const cudaError_t e = smem_limit<k_reduce<LG, U>>(enc_smem_bytes(U));
     if (e != cudaSuccess) return e;
-    k_reduce<LG, U><<<grid, ENC_THREADS, enc_smem_bytes(U), s>>>(P);
-    return cudaGetLastError();
+    return launch_enc(k_reduce<LG, U>, grid, enc_smem_bytes(U), s, P.dep != 0, P);
 }
 
 template <int LG>

@@ -47,9 +47,11 @@ cudaError_t launch_wscan(const Launch& P, unsigned grid, cudaStream_t s);
 // `s`; the decoder is launched dependent on it (programmatic serialisation).
 cudaError_t launch_decompress(const Launch& P, unsigned grid, cudaStream_t s,
                               bool after_wscan = false);
-// Item of every tile (by_chunk: of every width-scan chunk) of a multi-item launch.
+// Item of every tile (by_chunk: of every width-scan chunk) of a multi-item
+// launch; `dependent`: launched dependent on the width scan just before it.
 cudaError_t launch_tile_map(const Item* items, unsigned n_items, unsigned total_tiles,
-                            unsigned* map, cudaStream_t s, bool by_chunk = false);
+                            unsigned* map, cudaStream_t s, bool by_chunk = false,
+                            bool dependent = false);
 // Grouped batches: first tickets of every item by block size (rewrites the
 // items' tile_begin) and the ticket -> item map; `part` holds 5 u32 per 256 items.
 cudaError_t launch_group(Item* items, unsigned n_items, unsigned* part, unsigned* map,
